@@ -1,0 +1,482 @@
+/*
+ * ngdbf_oracle.c -- reference NGDBF decoder.  TEST INFRASTRUCTURE ONLY.
+ *
+ * This file is the plain, slow, step-by-step statement of Noisy Gradient
+ * Descent Bit-Flip decoding (Sundararajan, Winstead, Boutillon, "Noisy
+ * Gradient Descent Bit-Flip Decoding for LDPC Codes", IEEE Trans. Commun.
+ * 2014).  Only the test suite, the smoke check and the CPU-baseline leg of
+ * the benchmark may load it.  It shares no code with the CUDA decoder.
+ *
+ * Paper sections followed:
+ *   Sec. III-A  notation: H, N(i), M(k), x(0) = sign(y), bipolar syndromes
+ *   Sec. III-B  GDBF Steps 1-4 (Step 1 syndrome + stop, Step 3b multi-bit flip)
+ *   Sec. III-C  NGDBF Step 2: E_k = x_k y_k + w sum_{i in M(k)} s_i + q_k,
+ *               q_k ~ N(0, eta^2 N0/2)
+ *   Sec. III-D  threshold adaptation Steps 0 and 3b (theta_k <- theta_k lambda
+ *               when not flipped), in the counter form of Sec. V-A,
+ *               theta_k = theta lambda^{u_k} (Eqs. 11-12)
+ *   Sec. III-E  output smoothing, Eq. 7: X_k(t+1) = X_k(t) + x_k(t) over
+ *               t = T-W .. T, output sign(X_k) when T is reached
+ *   Sec. IV-E   quantizer g(.) (Eq. 8)
+ *   Sec. V-A    quantized threshold adaptation events (Eq. 13, Table II)
+ *
+ * Readings where the paper is silent (each also listed in the design notes):
+ *   - sign(0) = +1; samples are clamped to [-Y_max, Y_max] first (Sec. IV-A).
+ *   - Step 1 precedes Step 2; a frame valid at t reports iters = t, pass = 1;
+ *     T flip phases at most, iters = T and pass = 0 when T is reached.
+ *   - Flooding schedule: every E_k of iteration t uses the syndromes of t.
+ *   - Strict E_k < theta_k flips; a tie adapts (u_k += 1).
+ *   - The smoothing sum covers x(t) for t = max(0, T-W) .. T; a zero sum keeps
+ *     x_k(T).
+ *   - Perturbation std = eta * sigma with sigma the channel std (N0/2 = sigma^2).
+ *   - The quantizer's level index saturates at 2^(Q-1) - 1 (needed to
+ *     reproduce Table II).
+ *
+ * The perturbation q_k is drawn by a counter-based generator (the paper's own
+ * hardware used one Gaussian RNG and a shift-register chain, Sec. V-B):
+ *   Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), key = (seed_lo,
+ *   seed_hi), counter = (k/4, t, frame_lo, frame_hi);  r -> a = r >> 9,
+ *   u = (a + 1/2) 2^-23;  Box-Muller (1958): outputs (r0,r1) give symbols
+ *   4g, 4g+1 as rho cos(2 pi u1), rho sin(2 pi u1) with rho = sqrt(-2 ln u0);
+ *   (r2,r3) give 4g+2, 4g+3 the same way.
+ * The FP32 form evaluates ln and sin/cos with its own series (below) so that
+ * the same definition can be evaluated bit-identically elsewhere; the FP64
+ * form uses the C library's log/sin/cos on the same uniforms.
+ */
+#include <math.h>
+#include <pthread.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_ADAPT 1
+#define ORC_SMOOTH 2
+
+typedef struct {
+    float w, theta, eta, lambda, y_max;
+    int32_t t_max, smooth_window, variant, precision, q_bits;
+} orc_params;
+
+/* ------------------------------------------------------------------------ */
+/* Philox4x32-10                                                             */
+/* ------------------------------------------------------------------------ */
+
+void oracle_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+    const uint32_t mul0 = 0xD2511F53u, mul1 = 0xCD9E8D57u;   /* round multipliers */
+    const uint32_t bump0 = 0x9E3779B9u, bump1 = 0xBB67AE85u; /* Weyl key increments */
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; ++round) {
+        uint64_t p0 = (uint64_t)mul0 * c0;
+        uint64_t p1 = (uint64_t)mul1 * c2;
+        uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ k0;
+        uint32_t n1 = (uint32_t)p1;
+        uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ k1;
+        uint32_t n3 = (uint32_t)p0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+        k0 += bump0; k1 += bump1;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* ------------------------------------------------------------------------ */
+/* FP32 elementary functions used by the Gaussian generator                  */
+/* ------------------------------------------------------------------------ */
+
+/* Series coefficients computed from their definitions (not fitted):
+ *   ln:  ln m = 2 atanh(s), s = (m-1)/(m+1), atanh s = sum s^(2j+1)/(2j+1)
+ *   sin/cos(h xi), h = pi/2:  a_n = (-1)^((n-1)/2) h^n / n!  (odd n),
+ *                             b_n = (-1)^(n/2) h^n / n!      (even n)
+ * with h^n/n! formed in double as t_n = (t_{n-1} * h) / n, t_0 = 1. */
+static float inv_odd[12];       /* inv_odd[n] = fl32(1/n) for odd n */
+static float sin_c[12], cos_c[13];
+static pthread_once_t coef_once = PTHREAD_ONCE_INIT;
+
+static void coef_init(void) {
+    for (int n = 1; n < 12; n += 2) inv_odd[n] = 1.0f / (float)n;
+    const double h = 1.5707963267948966;  /* pi/2 */
+    double t = 1.0;
+    for (int n = 1; n <= 12; ++n) {
+        t = (t * h) / (double)n;
+        if (n & 1) sin_c[n] = (float)((((n - 1) / 2) & 1) ? -t : t);
+        else cos_c[n] = (float)(((n / 2) & 1) ? -t : t);
+    }
+}
+
+/* Natural log for a positive normal float.  u = m 2^e with m in (1/sqrt2, sqrt2]. */
+float oracle_ln_f32(float u) {
+    pthread_once(&coef_once, coef_init);
+    uint32_t bits;
+    memcpy(&bits, &u, 4);
+    int32_t e = (int32_t)((bits >> 23) & 0xFFu) - 127;
+    uint32_t mb = (bits & 0x007FFFFFu) | 0x3F800000u;
+    float m;
+    memcpy(&m, &mb, 4);
+    if (m > 1.41421354f) { m = m * 0.5f; e = e + 1; }
+    float s = (m - 1.0f) / (m + 1.0f);
+    float z = s * s;
+    float p = inv_odd[11];
+    p = fmaf(p, z, inv_odd[9]);
+    p = fmaf(p, z, inv_odd[7]);
+    p = fmaf(p, z, inv_odd[5]);
+    p = fmaf(p, z, inv_odd[3]);
+    float r = fmaf(s * z, p, s);            /* atanh(s) */
+    return fmaf((float)e, 0.693147182f, 2.0f * r);
+}
+
+/* sin and cos of 2 pi u for u = (a + 1/2) 2^-23, a a 23-bit integer.
+ * 4u = quadrant + xi with xi in [-1/2, 1/2], exact in FP32. */
+void oracle_sincos2pi_f32(uint32_t a, float* sin_out, float* cos_out) {
+    pthread_once(&coef_once, coef_init);
+    uint32_t quadrant = (a >> 21) & 3u;
+    int32_t rem = (int32_t)(a & 0x1FFFFFu);
+    if (rem >= (1 << 20)) { rem -= (1 << 21); quadrant = (quadrant + 1u) & 3u; }
+    float xi = ((float)rem + 0.5f) * 0x1.0p-21f;
+    float zz = xi * xi;
+    float ps = sin_c[11];
+    ps = fmaf(ps, zz, sin_c[9]);
+    ps = fmaf(ps, zz, sin_c[7]);
+    ps = fmaf(ps, zz, sin_c[5]);
+    ps = fmaf(ps, zz, sin_c[3]);
+    ps = fmaf(ps, zz, sin_c[1]);
+    float S = xi * ps;                       /* sin(pi xi / 2) */
+    float pc = cos_c[12];
+    pc = fmaf(pc, zz, cos_c[10]);
+    pc = fmaf(pc, zz, cos_c[8]);
+    pc = fmaf(pc, zz, cos_c[6]);
+    pc = fmaf(pc, zz, cos_c[4]);
+    pc = fmaf(pc, zz, cos_c[2]);
+    float C = fmaf(zz, pc, 1.0f);            /* cos(pi xi / 2) */
+    switch (quadrant) {
+        case 0: *sin_out = S; *cos_out = C; break;
+        case 1: *sin_out = C; *cos_out = -S; break;
+        case 2: *sin_out = -S; *cos_out = -C; break;
+        default: *sin_out = -C; *cos_out = S; break;
+    }
+}
+
+static inline float uniform_f32(uint32_t r) { return ((float)(r >> 9) + 0.5f) * 0x1.0p-23f; }
+
+/* Four standard normals for (seed, frame, t, symbol group g): symbols 4g..4g+3. */
+void oracle_gauss4_f32(uint64_t seed, uint64_t frame, uint32_t t, uint32_t g, float z[4]) {
+    uint32_t ctr[4] = {g, t, (uint32_t)frame, (uint32_t)(frame >> 32)};
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t r[4];
+    oracle_philox4x32_10(ctr, key, r);
+    for (int h = 0; h < 2; ++h) {
+        float rho = sqrtf(-2.0f * oracle_ln_f32(uniform_f32(r[2 * h])));
+        float sn, cs;
+        oracle_sincos2pi_f32(r[2 * h + 1] >> 9, &sn, &cs);
+        z[2 * h] = rho * cs;
+        z[2 * h + 1] = rho * sn;
+    }
+}
+
+void oracle_gauss4_f64(uint64_t seed, uint64_t frame, uint32_t t, uint32_t g, double z[4]) {
+    uint32_t ctr[4] = {g, t, (uint32_t)frame, (uint32_t)(frame >> 32)};
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t r[4];
+    oracle_philox4x32_10(ctr, key, r);
+    for (int h = 0; h < 2; ++h) {
+        double u0 = ((double)(r[2 * h] >> 9) + 0.5) * 0x1.0p-23;
+        double u1 = ((double)(r[2 * h + 1] >> 9) + 0.5) * 0x1.0p-23;
+        double rho = sqrt(-2.0 * log(u0));
+        z[2 * h] = rho * cos(6.283185307179586 * u1);
+        z[2 * h + 1] = rho * sin(6.283185307179586 * u1);
+    }
+}
+
+/* Standard deviation of q_k: eta * sigma (Sec. III-C, variance eta^2 N0/2 with
+ * N0/2 = sigma^2 the channel variance), formed in double, rounded to FP32. */
+static float noise_scale_f32(float eta, float sigma) { return (float)((double)eta * (double)sigma); }
+
+/* The perturbation q_k the FP32 decoder adds for (seed, frame, t, k). */
+float oracle_noise_f32(uint64_t seed, uint64_t frame, uint32_t t, uint32_t k, float eta, float sigma) {
+    float z[4];
+    oracle_gauss4_f32(seed, frame, t, k >> 2, z);
+    return noise_scale_f32(eta, sigma) * z[k & 3];
+}
+
+/* ------------------------------------------------------------------------ */
+/* Thresholds and the inversion function                                     */
+/* ------------------------------------------------------------------------ */
+
+/* theta_k = theta lambda^u (Sec. V-A, Eq. 12), tabulated for u = 0..t_max:
+ * p_0 = 1, p_{u+1} = p_u * lambda in double; thr[u] = fl32(theta * p_u). */
+void oracle_threshold_table_f32(float theta, float lambda, int32_t t_max, float* thr) {
+    double p = 1.0;
+    for (int32_t u = 0; u <= t_max; ++u) {
+        thr[u] = (float)((double)theta * p);
+        p = p * (double)lambda;
+    }
+}
+
+/* Step 2 of Sec. III-C in FP32 with a fixed order: ((x*y) + w*S) + q. */
+float oracle_metric_f32(int x, float ys, int S, float w, float q) {
+    float xy = x > 0 ? ys : -ys;
+    float ws = w * (float)S;
+    float e = xy + ws;
+    return e + q;
+}
+
+double oracle_metric_f64(int x, double ys, int S, double w, double q) {
+    return (x > 0 ? ys : -ys) + w * (double)S + q;
+}
+
+/* g(v) of Sec. IV-E, Eq. 8, with the level index saturated at 2^(Q-1)-1. */
+double oracle_quantize(double v, int32_t q_bits, double y_max) {
+    const double nq = ldexp(1.0, q_bits);
+    double k = floor(fabs(v) * nq / (2.0 * y_max));
+    const double kmax = nq / 2.0 - 1.0;
+    if (k > kmax) k = kmax;
+    const double s = v >= 0.0 ? 1.0 : -1.0;
+    return s * (k + 0.5) * (2.0 * y_max / nq);
+}
+
+/* Adaptation events (theta~, tau~) of Sec. V-A: tau where g(theta lambda^u)
+ * changes, for u = 0..t_max (Table II).  Returns the event count. */
+int32_t oracle_threshold_events(double theta, double lambda, int32_t t_max, int32_t q_bits,
+                                double y_max, double* thr_out, int32_t* tau_out, int32_t cap) {
+    int32_t count = 0;
+    double prev = 0.0;
+    for (int32_t u = 0; u <= t_max; ++u) {
+        double th = oracle_quantize(theta * pow(lambda, (double)u), q_bits, y_max);
+        if (u == 0 || th != prev) {
+            if (count < cap) { thr_out[count] = th; tau_out[count] = u; }
+            ++count;
+            prev = th;
+        }
+    }
+    return count;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Decoder                                                                   */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    int32_t n, m;
+    const int32_t* row_ptr;   /* N(i) = col_idx[row_ptr[i] .. row_ptr[i+1]) */
+    const int32_t* col_idx;
+    int32_t* sym_ptr;         /* M(k) = chk_idx[sym_ptr[k] .. sym_ptr[k+1]) */
+    int32_t* chk_idx;
+} orc_code;
+
+static int code_init(orc_code* C, int32_t n, int32_t m, const int32_t* row_ptr, const int32_t* col_idx) {
+    C->n = n; C->m = m; C->row_ptr = row_ptr; C->col_idx = col_idx;
+    int32_t nnz = row_ptr[m];
+    C->sym_ptr = (int32_t*)calloc((size_t)n + 1, sizeof(int32_t));
+    C->chk_idx = (int32_t*)malloc(sizeof(int32_t) * (size_t)(nnz > 0 ? nnz : 1));
+    if (!C->sym_ptr || !C->chk_idx) return -1;
+    for (int32_t e = 0; e < nnz; ++e) C->sym_ptr[col_idx[e] + 1]++;
+    for (int32_t k = 0; k < n; ++k) C->sym_ptr[k + 1] += C->sym_ptr[k];
+    int32_t* fill = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
+    if (!fill) return -1;
+    memcpy(fill, C->sym_ptr, sizeof(int32_t) * (size_t)n);
+    for (int32_t i = 0; i < m; ++i)
+        for (int32_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) C->chk_idx[fill[col_idx[e]]++] = i;
+    free(fill);
+    return 0;
+}
+
+static void code_free(orc_code* C) { free(C->sym_ptr); free(C->chk_idx); }
+
+/* Writes x (bit 1 <=> x_k = -1, LSB-first) into out[ceil(n/8)]. */
+static void pack_bits(const int8_t* x, int32_t n, uint8_t* out) {
+    memset(out, 0, (size_t)(n + 7) / 8);
+    for (int32_t k = 0; k < n; ++k)
+        if (x[k] < 0) out[k >> 3] |= (uint8_t)(1u << (k & 7));
+}
+
+typedef struct {
+    const orc_code* C;
+    const orc_params* P;
+    int use_f64;
+    float scale32;            /* fl32(eta * sigma) */
+    double scale64;           /* eta * sigma */
+    const float* thr32;       /* [t_max + 1] */
+    const double* thr64;
+    uint64_t seed;
+    const float* q_in;        /* optional [t_max][n] perturbations for one frame */
+} orc_ctx;
+
+/* Decodes one frame.  ws must hold 4n + m + 16 int32 words. */
+static void decode_frame(const orc_ctx* X, const float* y, uint64_t frame_id,
+                         uint8_t* bits, int32_t* iters, uint8_t* pass, int32_t* ws) {
+    const orc_code* C = X->C;
+    const orc_params* P = X->P;
+    const int32_t n = C->n, m = C->m, T = P->t_max;
+    const int adapt = (P->variant & ORC_ADAPT) != 0;
+    const int smooth = (P->variant & ORC_SMOOTH) != 0;
+    int8_t* x = (int8_t*)ws;                       /* n bytes */
+    int8_t* s = (int8_t*)(ws + (n + 3) / 4);       /* m bytes */
+    int32_t* u = ws + (n + 3) / 4 + (m + 3) / 4;   /* n */
+    int32_t* Xs = u + n;                           /* n */
+    float* ys32 = (float*)(Xs + n);                /* n */
+    double* ys64 = (double*)malloc(sizeof(double) * (size_t)n);
+    const int clamp = P->y_max > 0.0f && isfinite(P->y_max);
+
+    /* Step 0 and x(0) = sign(y) on saturated samples (Sec. III-A, IV-A). */
+    for (int32_t k = 0; k < n; ++k) {
+        float v = y[k];
+        if (clamp) { if (v > P->y_max) v = P->y_max; if (v < -P->y_max) v = -P->y_max; }
+        ys32[k] = v;
+        ys64[k] = (double)v;
+        x[k] = v >= 0.0f ? 1 : -1;
+        u[k] = 0;
+        Xs[k] = 0;
+    }
+    const int32_t t_smooth = smooth ? (T - P->smooth_window > 0 ? T - P->smooth_window : 0) : T + 1;
+    float z32[4] = {0, 0, 0, 0};
+    double z64[4] = {0, 0, 0, 0};
+
+    for (int32_t t = 0; t <= T; ++t) {
+        /* Step 1: syndromes and the stopping test. */
+        int all_satisfied = 1;
+        for (int32_t i = 0; i < m; ++i) {
+            int prod = 1;
+            for (int32_t e = C->row_ptr[i]; e < C->row_ptr[i + 1]; ++e) prod *= x[C->col_idx[e]];
+            s[i] = (int8_t)prod;
+            if (prod < 0) all_satisfied = 0;
+        }
+        if (all_satisfied) {
+            pack_bits(x, n, bits);
+            *iters = t;
+            *pass = 1;
+            free(ys64);
+            return;
+        }
+        /* Eq. 7: the up/down counter sums x(t) over the smoothing window. */
+        if (t >= t_smooth)
+            for (int32_t k = 0; k < n; ++k) Xs[k] += x[k];
+        if (t == T) break;
+        /* Step 2 (noisy inversion function) and Step 3b (flip / adapt). */
+        for (int32_t k = 0; k < n; ++k) {
+            int S = 0;
+            for (int32_t e = C->sym_ptr[k]; e < C->sym_ptr[k + 1]; ++e) S += s[C->chk_idx[e]];
+            int flip;
+            if (X->use_f64) {
+                if ((k & 3) == 0) oracle_gauss4_f64(X->seed, frame_id, (uint32_t)t, (uint32_t)(k >> 2), z64);
+                double q = X->scale64 * z64[k & 3];
+                double E = oracle_metric_f64(x[k], ys64[k], S, (double)P->w, q);
+                flip = E < X->thr64[u[k]];
+            } else {
+                float q;
+                if (X->q_in) {
+                    q = X->q_in[(size_t)t * n + k];
+                } else {
+                    if ((k & 3) == 0) oracle_gauss4_f32(X->seed, frame_id, (uint32_t)t, (uint32_t)(k >> 2), z32);
+                    q = X->scale32 * z32[k & 3];
+                }
+                float E = oracle_metric_f32(x[k], ys32[k], S, P->w, q);
+                flip = E < X->thr32[u[k]];
+            }
+            if (flip) x[k] = (int8_t)-x[k];
+            else if (adapt) u[k] += 1;
+        }
+    }
+    /* T reached: smoothed decision sign(X_k) (Sec. III-E), zero keeps x_k(T). */
+    if (smooth)
+        for (int32_t k = 0; k < n; ++k) x[k] = Xs[k] > 0 ? 1 : (Xs[k] < 0 ? -1 : x[k]);
+    pack_bits(x, n, bits);
+    *iters = T;
+    *pass = 0;
+    free(ys64);
+}
+
+typedef struct {
+    const orc_ctx* X;
+    const float* y;
+    int64_t f0, f1;
+    uint64_t frame_offset;
+    uint8_t* bits;
+    int32_t* iters;
+    uint8_t* pass;
+    int status;
+} orc_job;
+
+static void* decode_worker(void* arg) {
+    orc_job* J = (orc_job*)arg;
+    const orc_code* C = J->X->C;
+    const int32_t n = C->n, nb = (C->n + 7) / 8;
+    int32_t* ws = (int32_t*)malloc(sizeof(int32_t) * (size_t)(4 * n + C->m + 16));
+    if (!ws) { J->status = -1; return NULL; }
+    for (int64_t f = J->f0; f < J->f1; ++f)
+        decode_frame(J->X, J->y + f * (int64_t)n, J->frame_offset + (uint64_t)f,
+                     J->bits + f * (int64_t)nb, J->iters + f, J->pass + f, ws);
+    free(ws);
+    J->status = 0;
+    return NULL;
+}
+
+static int check_args(int32_t n, int32_t m, const int32_t* row_ptr, const int32_t* col_idx,
+                      const orc_params* P) {
+    if (n <= 0 || m <= 0 || !row_ptr || !col_idx || !P) return -1;
+    if (row_ptr[0] != 0) return -1;
+    for (int32_t i = 0; i < m; ++i) if (row_ptr[i + 1] < row_ptr[i]) return -1;
+    for (int32_t e = 0; e < row_ptr[m]; ++e) if (col_idx[e] < 0 || col_idx[e] >= n) return -1;
+    if (P->t_max < 0 || P->smooth_window < 0) return -1;
+    return 0;
+}
+
+static int run(int use_f64, int32_t n, int32_t m, const int32_t* row_ptr, const int32_t* col_idx,
+               const float* y, int64_t n_frames, float sigma, const orc_params* P, uint64_t seed,
+               uint64_t frame_offset, const float* q_in, uint8_t* bits, int32_t* iters,
+               uint8_t* pass, int32_t n_threads) {
+    if (check_args(n, m, row_ptr, col_idx, P) != 0 || n_frames < 0) return -1;
+    if (n_frames == 0) return 0;
+    orc_code C;
+    if (code_init(&C, n, m, row_ptr, col_idx) != 0) { code_free(&C); return -1; }
+    float* thr32 = (float*)malloc(sizeof(float) * (size_t)(P->t_max + 1));
+    double* thr64 = (double*)malloc(sizeof(double) * (size_t)(P->t_max + 1));
+    oracle_threshold_table_f32(P->theta, P->lambda, P->t_max, thr32);
+    for (int32_t u = 0; u <= P->t_max; ++u) thr64[u] = (double)P->theta * pow((double)P->lambda, (double)u);
+    orc_ctx X;
+    X.C = &C; X.P = P; X.use_f64 = use_f64;
+    X.scale32 = noise_scale_f32(P->eta, sigma);
+    X.scale64 = (double)P->eta * (double)sigma;
+    X.thr32 = thr32; X.thr64 = thr64; X.seed = seed; X.q_in = q_in;
+    if (n_threads <= 0) n_threads = 1;
+    if (n_threads > 512) n_threads = 512;
+    if (n_frames < n_threads) n_threads = (int32_t)n_frames;
+    pthread_t th[512];
+    orc_job jobs[512];
+    for (int32_t i = 0; i < n_threads; ++i) {
+        jobs[i].X = &X; jobs[i].y = y;
+        jobs[i].f0 = n_frames * i / n_threads; jobs[i].f1 = n_frames * (i + 1) / n_threads;
+        jobs[i].frame_offset = frame_offset;
+        jobs[i].bits = bits; jobs[i].iters = iters; jobs[i].pass = pass; jobs[i].status = 0;
+    }
+    for (int32_t i = 1; i < n_threads; ++i) pthread_create(&th[i], NULL, decode_worker, &jobs[i]);
+    decode_worker(&jobs[0]);
+    int status = jobs[0].status;
+    for (int32_t i = 1; i < n_threads; ++i) { pthread_join(th[i], NULL); status |= jobs[i].status; }
+    free(thr32); free(thr64);
+    code_free(&C);
+    return status;
+}
+
+/* FP32 decoder with a fixed operation order: the bit-exact reference. */
+int oracle_decode_f32(int32_t n, int32_t m, const int32_t* row_ptr, const int32_t* col_idx,
+                      const float* y, int64_t n_frames, float sigma, const orc_params* P,
+                      uint64_t seed, uint64_t frame_offset, uint8_t* bits, int32_t* iters,
+                      uint8_t* pass, int32_t n_threads) {
+    return run(0, n, m, row_ptr, col_idx, y, n_frames, sigma, P, seed, frame_offset, NULL,
+               bits, iters, pass, n_threads);
+}
+
+/* FP64 decoder on the same uniforms: the statistical reference. */
+int oracle_decode_f64(int32_t n, int32_t m, const int32_t* row_ptr, const int32_t* col_idx,
+                      const float* y, int64_t n_frames, float sigma, const orc_params* P,
+                      uint64_t seed, uint64_t frame_offset, uint8_t* bits, int32_t* iters,
+                      uint8_t* pass, int32_t n_threads) {
+    return run(1, n, m, row_ptr, col_idx, y, n_frames, sigma, P, seed, frame_offset, NULL,
+               bits, iters, pass, n_threads);
+}
+
+/* FP32 decoder of ONE frame with the perturbations given: q[t][k], t < t_max. */
+int oracle_decode_f32_qin(int32_t n, int32_t m, const int32_t* row_ptr, const int32_t* col_idx,
+                          const float* y, const orc_params* P, const float* q,
+                          uint8_t* bits, int32_t* iters, uint8_t* pass) {
+    return run(0, n, m, row_ptr, col_idx, y, 1, 0.0f, P, 0, 0, q, bits, iters, pass, 1);
+}

@@ -1,0 +1,433 @@
+"""Pins of the reference (oracle) decoder to facts outside the oracle itself.
+
+Each ``pin_*`` function takes an ``oracle.Oracle`` and raises AssertionError
+when the oracle disagrees with the paper (Sundararajan, Winstead, Boutillon
+2014), with a closed form, with a library routine evaluating a textbook
+definition, with an invariant, or with a trace worked out by hand.  The
+test modules run every pin on the real oracle, and run the whole battery
+on oracles with planted mistakes, each of which must fail at least one pin.
+"""
+from __future__ import annotations
+
+import math
+import os
+
+import numpy as np
+
+import oracle as oracle_pkg
+from paper_1402_2773_gb300 import workload as wl
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def _golden_lines(name):
+    with open(os.path.join(GOLDEN, name)) as f:
+        return [ln.split() for ln in f if ln.strip() and not ln.startswith("#")]
+
+
+# ---------------------------------------------------------------------------
+# tiny codes
+# ---------------------------------------------------------------------------
+
+# Hamming (7,4): N(0) = {0,1,3,4}, N(1) = {0,2,3,5}, N(2) = {1,2,3,6};
+# M(0) = {0,1}, M(1) = {0,2}, M(2) = {1,2}, M(3) = {0,1,2}, M(4..6) = {0},{1},{2}.
+HAMMING_H = np.array([[1, 1, 0, 1, 1, 0, 0],
+                      [1, 0, 1, 1, 0, 1, 0],
+                      [0, 1, 1, 1, 0, 0, 1]], dtype=np.uint8)
+
+
+def hamming_code():
+    return wl.code_from_dense(HAMMING_H, name="hamming74")
+
+
+def _bits_byte(bits):
+    return int(bits[0])
+
+
+# ---------------------------------------------------------------------------
+# generator
+# ---------------------------------------------------------------------------
+
+def pin_philox_kat(O):
+    """Philox4x32-10 against the authors' published known-answer vectors."""
+    for row in _golden_lines("philox4x32_10_kat.txt"):
+        v = [int(h, 16) for h in row]
+        got = O.philox(v[0:4], v[4:6])
+        assert list(got) == v[6:10], f"philox KAT mismatch: {got} vs {v[6:10]}"
+
+
+def pin_ln_f32(O):
+    """FP32 ln of the generator's uniforms within 2 ulp of the C library's double log."""
+    a = np.concatenate([np.arange(0, 4096), np.arange((1 << 23) - 4096, 1 << 23),
+                        np.linspace(0, (1 << 23) - 1, 6000).astype(np.int64),
+                        # around the sqrt(2) mantissa boundary of each binade
+                        np.array([int(math.sqrt(2) * 2 ** (23 - j)) - 1 + d for j in range(1, 20)
+                                  for d in range(3)])])
+    for ai in a:
+        u = np.float32((float(ai) + 0.5) * 2.0 ** -23)
+        got = float(O.ln_f32(float(u)))
+        ref = math.log(float(u))
+        ulp = float(np.spacing(np.float32(abs(ref))))
+        assert abs(got - ref) <= 2.0 * ulp, f"ln({u}) = {got}, libm {ref}"
+
+
+def pin_sincos_f32(O):
+    """FP32 sin/cos(2 pi u) within 2^-23 of the C library and exactly quarter-turn symmetric."""
+    rng = np.random.default_rng(5)
+    a = np.concatenate([np.arange(0, 64), rng.integers(0, 1 << 23, 4000),
+                        np.array([(q << 21) + d for q in range(4) for d in (-2, -1, 0, 1, (1 << 20) - 1,
+                                                                            1 << 20)]) % (1 << 23)])
+    for ai in a:
+        ai = int(ai)
+        s, c = O.sincos2pi_f32(ai)
+        u = (ai + 0.5) * 2.0 ** -23
+        assert abs(float(s) - math.sin(2 * math.pi * u)) <= 2.0 ** -23, f"sin(2pi {u})"
+        assert abs(float(c) - math.cos(2 * math.pi * u)) <= 2.0 ** -23, f"cos(2pi {u})"
+        # a quarter turn (a + 2^21) rotates (sin, cos) -> (cos, -sin) exactly
+        s2, c2 = O.sincos2pi_f32((ai + (1 << 21)) % (1 << 23))
+        assert s2 == c and c2 == -s, "quarter-turn symmetry"
+
+
+def pin_gauss_f32_vs_library(O):
+    """FP32 Box-Muller pairs agree with the C library's double evaluation of the same uniforms."""
+    worst = 0.0
+    for f in range(8):
+        for t in (0, 1, 299):
+            for g in range(0, 600, 7):
+                z32 = O.gauss4_f32(12345, f, t, g).astype(np.float64)
+                z64 = O.gauss4_f64(12345, f, t, g)
+                worst = max(worst, float(np.max(np.abs(z32 - z64) / (1.0 + np.abs(z64)))))
+    assert worst < 4e-6, f"FP32 Gaussian deviates from the library evaluation by {worst}"
+
+
+def pin_gauss_statistics(O):
+    """z ~ N(0,1): Kolmogorov-Smirnov, first moments, pair independence, radial law."""
+    from scipy import stats
+    z = np.array([O.gauss4_f64(7, f, t, g) for f in range(16) for t in range(8) for g in range(64)])
+    zz = z.reshape(-1)
+    assert stats.kstest(zz, "norm").pvalue > 1e-4, "Gaussian KS test"
+    assert abs(zz.mean()) < 0.02 and abs(zz.var() - 1.0) < 0.03
+    assert abs(np.corrcoef(z[:, 0], z[:, 1])[0, 1]) < 0.03
+    r2 = z[:, 0] ** 2 + z[:, 1] ** 2          # chi-square with 2 dof: exponential, mean 2
+    assert stats.kstest(r2, "expon", args=(0, 2)).pvalue > 1e-4
+    z32 = np.array([O.gauss4_f32(7, f, t, g) for f in range(16) for t in range(8) for g in range(64)],
+                   dtype=np.float64).reshape(-1)
+    assert stats.kstest(z32, "norm").pvalue > 1e-4
+
+
+def pin_noise_variance(O):
+    """q_k has standard deviation eta * sigma (Sec. III-C; N0/2 = sigma^2)."""
+    eta, sigma = 0.7, 0.6
+    q = np.array([O.noise_f32(3, f, t, k, eta, sigma) for f in range(4) for t in range(16)
+                  for k in range(256)], dtype=np.float64)
+    sd = q.std()
+    assert abs(sd - eta * sigma) < 0.02 * eta * sigma, f"perturbation std {sd}"
+    assert abs(q.mean()) < 0.02
+
+
+# ---------------------------------------------------------------------------
+# thresholds, quantizer, inversion function
+# ---------------------------------------------------------------------------
+
+def pin_threshold_table(O):
+    """theta_k = theta lambda^u (Sec. V-A, Eq. 12): within 1 FP32 ulp of the closed form."""
+    for theta, lam, T in ((-0.9, 0.99, 300), (-0.7, 0.993, 300), (-0.6, 1.0, 50), (-0.9, 0.9, 100)):
+        thr = O.threshold_table_f32(theta, lam, T)
+        ref = float(np.float32(theta)) * float(np.float32(lam)) ** np.arange(T + 1, dtype=np.float64)
+        err = np.abs(thr.astype(np.float64) - ref) / np.spacing(np.abs(ref).astype(np.float32))
+        assert err.max() <= 1.0, f"threshold table off by {err.max()} ulp"
+
+
+def pin_table2(O):
+    """Quantized adaptation events reproduce Table II of Sec. V-A exactly."""
+    want = {}
+    for q, i, th, tau in _golden_lines("table2_threshold_events.txt"):
+        want.setdefault(int(q), []).append((float(th), int(tau)))
+    for q, events in want.items():
+        got = O.threshold_events(-0.9, 0.99, 300, q, 2.5)
+        assert len(got) == len(events), f"Q={q}: {got}"
+        for (gth, gtau), (wth, wtau) in zip(got, events):
+            assert gtau == wtau and round(gth, 4) == wth, f"Q={q}: {got} vs {events}"
+
+
+def pin_fig20(O):
+    """Weighted-GDBF flip matrices of Fig. 20 (Sec. VII) from the oracle's inversion function."""
+    lines = _golden_lines("fig20_weighted_flip_matrices.txt")
+    mats, cur = {}, None
+    for ln in lines:
+        if ln[0] == "theta":
+            cur = float(ln[1])
+            mats[cur] = []
+        else:
+            mats[cur].append([int(v) for v in ln])
+    nq = 16
+    rows = [O.quantize((k + 0.5) * 3.0 / nq, 4, 1.5) for k in range(nq // 2 - 1, -1, -1)]
+    assert rows[0] == 1.40625 and rows[-1] == 0.09375
+    for theta, want in mats.items():
+        for r, ys in enumerate(rows):
+            for c, S in enumerate((3, 1, -1, -3)):
+                e = O.metric_f32(+1, ys, S, 0.5, 0.0)
+                got = -1 if e < np.float32(theta) else 1
+                assert got == want[r][c], f"theta={theta} row {r} col {c}"
+                e64 = O.metric_f64(+1, ys, S, 0.5, 0.0)
+                assert (-1 if e64 < theta else 1) == want[r][c]
+
+
+def pin_quantizer(O):
+    """g(.) of Eq. 8: odd multiples of Delta/2, saturating at +-(N_Q - 1) Delta / 2."""
+    for q in (3, 4, 5, 8):
+        d = 2 * 2.5 / 2 ** q
+        for v in np.linspace(-4, 4, 801):
+            g = O.quantize(float(v), q, 2.5)
+            k = (abs(g) / d) - 0.5
+            assert abs(k - round(k)) < 1e-9 and 0 <= round(k) <= 2 ** (q - 1) - 1
+            if abs(v) < 2.5 - 1e-9:
+                assert abs(g - v) <= d / 2 + 1e-12
+            assert (g > 0) == (v >= 0)
+
+
+# ---------------------------------------------------------------------------
+# decoder: hand-worked traces on the Hamming (7,4) code
+# ---------------------------------------------------------------------------
+
+Y_A = np.array([0.8, 0.9, 1.1, -0.2, 0.7, 1.0, 0.6], dtype=np.float32)
+
+
+def pin_trace_gdbf(O):
+    """Case A: s = (-1,-1,-1) at t = 0; with w = 0.5, theta = -0.6:
+    E = (-0.2, -0.1, 0.1, -1.3, 0.2, 0.5, 0.1) so only x_3 flips; t = 1 is valid."""
+    C = hamming_code()
+    p = oracle_pkg.make_params(w=0.5, theta=-0.6, eta=0.0, lam=1.0, y_max=2.5, t_max=10)
+    bits, it, ps = O.decode_f32_qin(C, Y_A, p, np.zeros((10, 7), np.float32))
+    assert (_bits_byte(bits), it, ps) == (0, 1, 1)
+    # T = 1 still allows the single flip phase; T = 0 tests x(0) only
+    p1 = oracle_pkg.make_params(w=0.5, theta=-0.6, eta=0.0, lam=1.0, y_max=2.5, t_max=1)
+    assert (lambda r: (_bits_byte(r[0]), r[1], r[2]))(O.decode_f32_qin(C, Y_A, p1, np.zeros((1, 7), np.float32))) == (0, 1, 1)
+    p0 = oracle_pkg.make_params(w=0.5, theta=-0.6, eta=0.0, lam=1.0, y_max=2.5, t_max=0)
+    bits, it, ps = O.decode_f32_qin(C, Y_A, p0, np.zeros((0, 7), np.float32))
+    assert (_bits_byte(bits), it, ps) == (0x08, 0, 0)
+
+
+def pin_trace_injected_noise(O):
+    """Case B: q_4(0) = -1 pushes E_4 = 0.2 - 1.0 = -0.8 below theta: x_3 and x_4 flip at t = 0.
+    At t = 1, s = (-1, +1, +1), E_4 = -0.7 - 0.5 = -1.2 flips x_4 back; t = 2 is valid."""
+    C = hamming_code()
+    p = oracle_pkg.make_params(w=0.5, theta=-0.6, eta=0.0, lam=1.0, y_max=2.5, t_max=10)
+    q = np.zeros((10, 7), np.float32)
+    q[0, 4] = -1.0
+    bits, it, ps = O.decode_f32_qin(C, Y_A, p, q)
+    assert (_bits_byte(bits), it, ps) == (0, 2, 1)
+    # With q_4(0) = -0.1 instead, E_4 = 0.1 > theta: the trace of case A.
+    q[0, 4] = -0.1
+    bits, it, ps = O.decode_f32_qin(C, Y_A, p, q)
+    assert (_bits_byte(bits), it, ps) == (0, 1, 1)
+
+
+def pin_trace_adaptation(O):
+    """Case C: y_3 = -0.1, w = 0.2, theta = -0.6.  t = 0: E_3 = 0.1 - 0.6 = -0.5 >= -0.6, no flip,
+    every u_k = 1.  With lambda = 0.5 the threshold becomes -0.3 and E_3 = -0.5 flips at t = 1,
+    so t = 2 is valid.  Without adaptation x never changes: T is reached with x_3 = -1."""
+    C = hamming_code()
+    y = Y_A.copy()
+    y[3] = -0.1
+    pa = oracle_pkg.make_params(w=0.2, theta=-0.6, eta=0.0, lam=0.5, y_max=2.5, t_max=6,
+                                variant=oracle_pkg.ADAPT)
+    bits, it, ps = O.decode_f32_qin(C, y, pa, np.zeros((6, 7), np.float32))
+    assert (_bits_byte(bits), it, ps) == (0, 2, 1)
+    pn = oracle_pkg.make_params(w=0.2, theta=-0.6, eta=0.0, lam=0.5, y_max=2.5, t_max=6, variant=0)
+    bits, it, ps = O.decode_f32_qin(C, y, pn, np.zeros((6, 7), np.float32))
+    assert (_bits_byte(bits), it, ps) == (0x08, 6, 0)
+
+
+def pin_trace_smoothing(O):
+    """Case D: T = 4, W = 3 (window t = 1..4), q = -5 forces a flip and +5 forbids one.
+    Flips: t=1 {3,4}, t=2 {5}, t=3 {0,3}.  x(1) = (+,+,+,-,+,+,+), x(2) = (+,+,+,+,-,+,+),
+    x(3) = (+,+,+,+,-,-,+), x(4) = (-,+,+,-,-,-,+); no x(t) satisfies all checks.
+    Window sums X = (2,4,4,0,-2,0,4): smoothed output (+,+,+,-,-,-,+) (zeros keep x(4)),
+    bits 3,4,5 -> 0x38; unsmoothed output x(4) -> 0x39."""
+    C = hamming_code()
+    q = np.full((4, 7), 5.0, np.float32)
+    for t, k in ((1, 3), (1, 4), (2, 5), (3, 3), (3, 0)):
+        q[t, k] = -5.0
+    ps_ = oracle_pkg.make_params(w=0.5, theta=-0.6, eta=0.0, lam=1.0, y_max=2.5, t_max=4,
+                                 smooth_window=3, variant=oracle_pkg.SMOOTH)
+    bits, it, ps = O.decode_f32_qin(C, Y_A, ps_, q)
+    assert (_bits_byte(bits), it, ps) == (0x38, 4, 0)
+    pn = oracle_pkg.make_params(w=0.5, theta=-0.6, eta=0.0, lam=1.0, y_max=2.5, t_max=4,
+                                smooth_window=3, variant=0)
+    bits, it, ps = O.decode_f32_qin(C, Y_A, pn, q)
+    assert (_bits_byte(bits), it, ps) == (0x39, 4, 0)
+
+
+def pin_trace_clamp_sign_tie(O):
+    """Case F: saturation at Y_max = 2 turns E_3 = 2.8 - 3 = -0.2 into 2 - 3 = -1 < -0.6 (w = 1).
+    Case G: y_3 = 0 gives x_3 = +1 and the all-(+1) word is valid at t = 0.
+    Case H: y_3 = -0.25, w = 0.25, theta = -0.5: E_3 = 0.25 - 0.75 = -0.5 = theta exactly, no flip."""
+    C = hamming_code()
+    y = np.array([2.0, 2.0, 2.0, -2.8, 0.7, 1.0, 0.6], np.float32)
+    p = oracle_pkg.make_params(w=1.0, theta=-0.6, eta=0.0, lam=1.0, y_max=2.0, t_max=5)
+    bits, it, ps = O.decode_f32_qin(C, y, p, np.zeros((5, 7), np.float32))
+    assert (_bits_byte(bits), it, ps) == (0, 1, 1)
+    p_noclamp = oracle_pkg.make_params(w=1.0, theta=-0.6, eta=0.0, lam=1.0, y_max=math.inf, t_max=5)
+    bits, it, ps = O.decode_f32_qin(C, y, p_noclamp, np.zeros((5, 7), np.float32))
+    assert (_bits_byte(bits), it, ps) == (0x08, 5, 0)
+    y0 = Y_A.copy()
+    y0[3] = 0.0
+    p = oracle_pkg.make_params(w=0.5, theta=-0.6, eta=0.0, lam=1.0, y_max=2.5, t_max=5)
+    bits, it, ps = O.decode_f32_qin(C, y0, p, np.zeros((5, 7), np.float32))
+    assert (_bits_byte(bits), it, ps) == (0, 0, 1)
+    yt = Y_A.copy()
+    yt[3] = -0.25
+    p = oracle_pkg.make_params(w=0.25, theta=-0.5, eta=0.0, lam=1.0, y_max=2.5, t_max=3)
+    bits, it, ps = O.decode_f32_qin(C, yt, p, np.zeros((3, 7), np.float32))
+    assert (_bits_byte(bits), it, ps) == (0x08, 3, 0)
+
+
+# ---------------------------------------------------------------------------
+# decoder: invariants and special cases on seeded codes
+# ---------------------------------------------------------------------------
+
+def _pin_code():
+    return wl.peg_code(96, 48, 3, seed=11)
+
+
+def pin_noiseless(O):
+    """A transmitted codeword (y = 1 - 2c) satisfies every check: iters = 0, pass = 1, output c."""
+    C = _pin_code()
+    y, cw, _ = wl.frames(C, 16, None, seed=3)
+    for variant in (0, 1, 3):
+        p = oracle_pkg.make_params(variant=variant, t_max=20, smooth_window=8)
+        for dec in (O.decode_f32, O.decode_f64):
+            bits, it, ps = dec(C, y, 0.5, p, seed=1)
+            assert (it == 0).all() and (ps == 1).all() and (bits == cw).all()
+
+
+def _mgdbf_dense(H, y, w, theta, lam, T, y_max, adapt):
+    """Textbook M-GDBF / AT-GDBF (Wadayama et al. 2010; Ismail et al. 2013) on a dense H, FP64."""
+    ys = np.clip(y.astype(np.float64), -y_max, y_max)
+    x = np.where(ys >= 0, 1, -1)
+    thr = np.full(H.shape[1], theta, dtype=np.float64)
+    Hi = H.astype(np.int64)
+    for t in range(T + 1):
+        s = 1 - 2 * ((Hi @ (x < 0).astype(np.int64)) % 2)
+        if (s == 1).all():
+            return x, t, 1
+        if t == T:
+            break
+        E = x * ys + w * (Hi.T @ s)
+        flip = E < thr
+        x = np.where(flip, -x, x)
+        if adapt:
+            thr = np.where(flip, thr, thr * lam)
+    return x, T, 0
+
+
+def pin_eta0_is_gdbf(O):
+    """eta = 0 removes the perturbation: the oracle equals textbook M-GDBF (lambda = 1) and
+    AT-GDBF (lambda < 1) evaluated densely."""
+    C = _pin_code()
+    H = C.dense()
+    y, _, sig = wl.frames(C, 60, 2.5, seed=9)
+    for lam, adapt, w, theta in ((1.0, 0, 0.75, -0.9), (0.9, 1, 0.5, -0.7), (0.97, 1, 1.0, -1.2)):
+        p = oracle_pkg.make_params(w=w, theta=theta, eta=0.0, lam=lam, y_max=2.5, t_max=40,
+                                   variant=oracle_pkg.ADAPT if adapt else 0)
+        bits, it, ps = O.decode_f64(C, y, sig, p, seed=1)
+        b32, it32, ps32 = O.decode_f32(C, y, sig, p, seed=1)
+        xs = wl.unpack_bits(bits, C.n)
+        same = 0
+        for f in range(y.shape[0]):
+            x, t, pa = _mgdbf_dense(H, y[f], float(np.float32(w)), float(np.float32(theta)),
+                                    float(np.float32(lam)), 40, 2.5, adapt)
+            ok = (it[f] == t and ps[f] == pa and (xs[f] == (x < 0)).all())
+            same += ok
+        assert same == y.shape[0], f"eta=0 oracle differs from textbook GDBF on {y.shape[0] - same} frames"
+        assert (it32 == it).mean() > 0.95
+
+
+def pin_codeword_and_ml(O):
+    """N = 24 brute force: a passing output is a codeword (dense H x = 0); NGDBF cannot beat ML."""
+    C = wl.peg_code(24, 12, 3, seed=2)
+    H = C.dense().astype(np.int64)
+    enc = C.encoder()
+    K = enc.k
+    infos = ((np.arange(2 ** K)[:, None] >> np.arange(K)[None, :]) & 1).astype(np.uint8)
+    cws = np.zeros((2 ** K, C.n), np.uint8)
+    cws[:, enc.info_pos] = infos
+    pm = wl.unpack_bits(enc.pmask.view(np.uint8).reshape(enc.rank, -1), enc.pmask.shape[1] * 64)[:, :K]
+    cws[:, enc.pivot_pos] = (infos.astype(np.int64) @ pm.T.astype(np.int64)) % 2
+    assert ((cws.astype(np.int64) @ H.T) % 2 == 0).all()
+    y, cw, sig = wl.frames(C, 400, 3.0, seed=4)
+    p = oracle_pkg.make_params(w=0.75, theta=-0.9, eta=0.96, lam=0.95, t_max=60, variant=oracle_pkg.ADAPT)
+    bits, it, ps = O.decode_f32(C, y, sig, p, seed=8)
+    out = wl.unpack_bits(bits, C.n).astype(np.int64)
+    synd = (out @ H.T) % 2
+    assert (synd[ps == 1] == 0).all(), "a passing frame is not a codeword"
+    assert synd[ps == 0].any(axis=1).all(), "a failing (unsmoothed) frame satisfies every check"
+    bip = 1.0 - 2.0 * cws.astype(np.float64)
+    ml = np.argmax(y.astype(np.float64) @ bip.T, axis=1)
+    tx = wl.unpack_bits(cw, C.n)
+    ml_err = (cws[ml] != tx).any(axis=1).mean()
+    dec_err = (out != tx).any(axis=1).mean()
+    n = y.shape[0]
+    assert dec_err >= ml_err - 3 * math.sqrt(max(ml_err, 1.0 / n) / n), (dec_err, ml_err)
+    corr = (1.0 - 2.0 * out) @ y.T.astype(np.float64)
+    corr_ml = np.max(y.astype(np.float64) @ bip.T, axis=1)
+    assert (np.diag(corr)[ps == 1] <= corr_ml[ps == 1] + 1e-9).all()
+
+
+def pin_f32_matches_injected_noise(O):
+    """The FP32 decoder adds exactly q_k = noise(seed, frame, t, k) each iteration."""
+    C = hamming_code()
+    y = np.array([0.3, -0.2, 0.5, 0.1, -0.4, 0.9, -0.05], np.float32)
+    for variant, lam in ((0, 1.0), (3, 0.9)):
+        p = oracle_pkg.make_params(w=0.5, theta=-0.3, eta=0.9, lam=lam, t_max=12, smooth_window=5,
+                                   variant=variant)
+        sigma = 0.7
+        for fid in range(6):
+            q = np.array([[O.noise_f32(99, fid, t, k, 0.9, sigma) for k in range(7)] for t in range(12)],
+                         np.float32)
+            b1, it1, ps1 = O.decode_f32_qin(C, y, p, q)
+            b2, it2, ps2 = O.decode_f32(C, y[None, :], sigma, p, seed=99, frame_offset=fid)
+            assert (b1 == b2[0]).all() and it1 == it2[0] and ps1 == ps2[0]
+    # frames of a batch are keyed by frame_offset + index, at low SNR where the noise decides
+    C = _pin_code()
+    y, _, sig = wl.frames(C, 6, 1.0, seed=12)
+    p = oracle_pkg.make_params(w=0.75, theta=-0.9, eta=0.96, lam=0.97, t_max=25, variant=1)
+    b2, it2, ps2 = O.decode_f32(C, y, sig, p, seed=5, frame_offset=40)
+    for f in range(6):
+        q = np.array([[O.noise_f32(5, 40 + f, t, k, 0.96, sig) for k in range(C.n)] for t in range(25)],
+                     np.float32)
+        b1, it1, ps1 = O.decode_f32_qin(C, y[f], p, q)
+        assert (b1 == b2[f]).all() and it1 == it2[f] and ps1 == ps2[f], f"frame {f}"
+
+
+def pin_frame_independence(O):
+    """A frame's result depends only on (y, seed, frame id): not on batch position or threads."""
+    C = _pin_code()
+    y, _, sig = wl.frames(C, 40, 2.0, seed=5)
+    p = oracle_pkg.make_params(variant=3, t_max=30, smooth_window=10, lam=0.95)
+    b, it, ps = O.decode_f32(C, y, sig, p, seed=4, frame_offset=100, threads=1)
+    b2, it2, ps2 = O.decode_f32(C, y[10:20], sig, p, seed=4, frame_offset=110, threads=3)
+    assert (b[10:20] == b2).all() and (it[10:20] == it2).all() and (ps[10:20] == ps2).all()
+    b3, it3, ps3 = O.decode_f32(C, y, sig, p, seed=4, frame_offset=100, threads=7)
+    assert (b == b3).all() and (it == it3).all()
+
+
+def pin_f32_f64_statistics(O):
+    """FP32 and FP64 forms decode the same frames to statistically equal results."""
+    C = _pin_code()
+    y, cw, sig = wl.frames(C, 300, 3.0, seed=6)
+    p = oracle_pkg.make_params(w=0.75, theta=-0.9, eta=0.9, lam=0.95, t_max=50, variant=1)
+    b32, it32, ps32 = O.decode_f32(C, y, sig, p, seed=2)
+    b64, it64, ps64 = O.decode_f64(C, y, sig, p, seed=2)
+    assert (it32 == it64).mean() > 0.8
+    assert abs(ps32.mean() - ps64.mean()) < 0.05
+
+
+ALL_PINS = [
+    pin_philox_kat, pin_ln_f32, pin_sincos_f32, pin_gauss_f32_vs_library, pin_gauss_statistics,
+    pin_noise_variance, pin_threshold_table, pin_table2, pin_fig20, pin_quantizer,
+    pin_trace_gdbf, pin_trace_injected_noise, pin_trace_adaptation, pin_trace_smoothing,
+    pin_trace_clamp_sign_tie, pin_noiseless, pin_eta0_is_gdbf, pin_codeword_and_ml,
+    pin_f32_matches_injected_noise, pin_frame_independence, pin_f32_f64_statistics,
+]

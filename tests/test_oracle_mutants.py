@@ -1,0 +1,89 @@
+"""Every plausible mistake planted in the oracle must be caught by at least one pin.
+
+Each mutant is a one-line edit of a copy of ``oracle/ngdbf_oracle.c`` (a
+dropped term, a wrong sign or index, a transposed operand, an off-by-one),
+compiled into a temporary library; the pin battery of ``oracle_pins`` then
+runs against it in a child process and must fail.
+"""
+import os
+import subprocess
+import sys
+
+import pytest
+
+import oracle as oracle_pkg
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+
+MUTANTS = [
+    ("philox key word", "^ c1 ^ k0;", "^ c1 ^ k1;"),
+    ("philox multiplier", "mul0 = 0xD2511F53u", "mul0 = 0xD2511F57u"),
+    ("philox rounds", "round < 10;", "round < 9;"),
+    ("ln series term", "p = fmaf(p, z, inv_odd[3]);", "p = fmaf(p, z, inv_odd[5]);"),
+    ("ln exponent", "fmaf((float)e, 0.693147182f, 2.0f * r)", "fmaf((float)e, 0.693147182f, r)"),
+    ("sincos quadrant", "case 1: *sin_out = C; *cos_out = -S;", "case 1: *sin_out = -C; *cos_out = S;"),
+    ("sin series sign", "sin_c[n] = (float)((((n - 1) / 2) & 1) ? -t : t);", "sin_c[n] = (float)t;"),
+    ("box-muller swap", "z[2 * h] = rho * cs;\n        z[2 * h + 1] = rho * sn;",
+     "z[2 * h] = rho * sn;\n        z[2 * h + 1] = rho * cs;"),
+    ("uniform offset", "((float)(r >> 9) + 0.5f) * 0x1.0p-23f", "((float)(r >> 9) + 1.0f) * 0x1.0p-23f"),
+    ("counter transposed", "uint32_t ctr[4] = {g, t, (uint32_t)frame, (uint32_t)(frame >> 32)};\n    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};\n    uint32_t r[4];\n    oracle_philox4x32_10(ctr, key, r);\n    for (int h = 0; h < 2; ++h) {\n        float rho",
+     "uint32_t ctr[4] = {t, g, (uint32_t)frame, (uint32_t)(frame >> 32)};\n    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};\n    uint32_t r[4];\n    oracle_philox4x32_10(ctr, key, r);\n    for (int h = 0; h < 2; ++h) {\n        float rho"),
+    ("noise scale", "return (float)((double)eta * (double)sigma);", "return (float)((double)eta * (double)sigma * (double)sigma);"),
+    ("metric sign", "float e = xy + ws;", "float e = xy - ws;"),
+    ("metric drops w", "float ws = w * (float)S;", "float ws = (float)S;"),
+    ("metric drops x", "float xy = x > 0 ? ys : -ys;", "float xy = ys;"),
+    ("metric64 sign", "return (x > 0 ? ys : -ys) + w * (double)S + q;", "return (x > 0 ? ys : -ys) - w * (double)S + q;"),
+    ("flip tie", "flip = E < X->thr32[u[k]];", "flip = E <= X->thr32[u[k]];"),
+    ("flip direction", "flip = E < X->thr64[u[k]];", "flip = E > X->thr64[u[k]];"),
+    ("adapt on flips", "else if (adapt) u[k] += 1;", "if (adapt) u[k] += 1;"),
+    ("threshold power", "thr[u] = (float)((double)theta * p);", "thr[u] = (float)((double)theta * p * (double)lambda);"),
+    ("quantizer saturation", "if (k > kmax) k = kmax;", ""),
+    ("quantizer half level", "return s * (k + 0.5) * (2.0 * y_max / nq);", "return s * k * (2.0 * y_max / nq);"),
+    ("smoothing start", "T - P->smooth_window > 0 ? T - P->smooth_window : 0", "T - P->smooth_window + 1 > 0 ? T - P->smooth_window + 1 : 0"),
+    ("smoothing tie", "(Xs[k] < 0 ? -1 : x[k])", "(Xs[k] < 0 ? -1 : 1)"),
+    ("smoothing skips x(T)", "if (t >= t_smooth)\n", "if (t >= t_smooth && t < T)\n"),
+    ("no final test", "for (int32_t t = 0; t <= T; ++t) {", "for (int32_t t = 0; t < T; ++t) {"),
+    ("iteration count", "*iters = t;", "*iters = t + 1;"),
+    ("sign of zero", "x[k] = v >= 0.0f ? 1 : -1;", "x[k] = v > 0.0f ? 1 : -1;"),
+    ("no clamp", "if (clamp) { if", "if (0) { if"),
+    ("penalty drops a check", "for (int32_t e = C->sym_ptr[k]; e < C->sym_ptr[k + 1]; ++e) S += s[C->chk_idx[e]];",
+     "for (int32_t e = C->sym_ptr[k]; e + 1 < C->sym_ptr[k + 1]; ++e) S += s[C->chk_idx[e]];"),
+    ("syndrome drops a symbol", "for (int32_t e = C->row_ptr[i]; e < C->row_ptr[i + 1]; ++e) prod *= x[C->col_idx[e]];",
+     "for (int32_t e = C->row_ptr[i]; e + 1 < C->row_ptr[i + 1]; ++e) prod *= x[C->col_idx[e]];"),
+    ("csc transposed", "C->chk_idx[fill[col_idx[e]]++] = i;", "C->chk_idx[fill[col_idx[e]]++] = col_idx[e] % m;"),
+    ("sequential update", "if (flip) x[k] = (int8_t)-x[k];",
+     "if (flip) { x[k] = (int8_t)-x[k]; for (int32_t e = C->sym_ptr[k]; e < C->sym_ptr[k + 1]; ++e) s[C->chk_idx[e]] = (int8_t)-s[C->chk_idx[e]]; }"),
+    ("frame id offset", "J->frame_offset + (uint64_t)f,", "J->frame_offset + (uint64_t)f + 1,"),
+]
+
+RUNNER = r"""
+import sys
+sys.path.insert(0, {root!r}); sys.path.insert(0, {tests!r})
+import oracle, oracle_pins
+O = oracle.Oracle({lib!r})
+for pin in oracle_pins.ALL_PINS:
+    try:
+        pin(O)
+    except AssertionError as e:
+        print("CAUGHT", pin.__name__, str(e)[:200])
+        sys.exit(0)
+print("NOT CAUGHT")
+sys.exit(3)
+"""
+
+
+@pytest.mark.parametrize("name,old,new", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_mutant_is_caught(tmp_path, name, old, new):
+    src = open(oracle_pkg.SRC).read()
+    assert src.count(old) == 1, f"mutation site for '{name}' must be unique"
+    mutated = src.replace(old, new)
+    path = tmp_path / "mutant.c"
+    path.write_text(mutated)
+    lib = str(tmp_path / "libmutant.so")
+    oracle_pkg.compile_lib(str(path), lib)
+    code = RUNNER.format(root=ROOT, tests=HERE, lib=lib)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=300)
+    assert r.returncode != 3, f"mutant '{name}' passed every pin:\n{r.stdout}\n{r.stderr}"
+    # a crash or a caught assertion both count as detection
+    assert "CAUGHT" in r.stdout or r.returncode != 0, r.stdout + r.stderr
