@@ -1,0 +1,391 @@
+#!/usr/bin/env python
+"""Throughput of the GB300 NGDBF decoder on the smoothed, adaptive high-rate workload.
+
+Workload: a seeded progressive-edge-growth (6,32)-regular code, N=2048, M=384
+(rank 383, rate 1665/2048), 10^6 frames of random information words at each
+of Eb/N0 = 3.5, 4.0 and 4.5 dB (BPSK 0 -> +1, AWGN, FP32 samples), decoded by
+SM-NGDBF with threshold adaptation and output smoothing: T = 300, W = 64,
+theta = -0.7, eta = 0.65, lambda = 0.993, Y_max = 2.0, w = 0.1875 (the high-
+rate parameter set of Fig. 5).  One step decodes the three 10^6-frame batches.
+
+Reported: decoded frames/s (value), information Gbit/s, the ALU roofline
+fraction of the decode kernel, clocks seen during the timed region, an
+end-to-end number through the host-buffer C-ABI call (copies included), and
+the FP32 reference decoder timed on the host cores on a bounded sample.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import signal
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1402_2773_gb300 import workload as wl  # noqa: E402
+
+FRAMES_PER_POINT = 1_000_000
+EBN0_DB = (3.5, 4.0, 4.5)
+PARAMS = dict(w=0.1875, theta=-0.7, eta=0.65, lam=0.993, y_max=2.0, t_max=300, smooth_window=64,
+              variant=3)
+DATA_SEED = 2014          # information bits and channel noise
+DECODER_SEED = 1          # Philox key of the perturbation
+# Algorithmic lane operations per (symbol, iteration) of the FP32 path: Philox 20 + uniforms 4
+# + ln 10.5 + sqrt 1 + sin/cos 13.5 + Box-Muller products 1 + perturbation 1 + inversion
+# function 5 + decision bit 1 + penalty sum (2 d_v + 2) + threshold, adaptation, window and
+# ballot 4 = 63 + 2 d_v, i.e. 75 for d_v = 6 (breakdown in the design doc).
+OPS_PER_SYMBOL_ITER = 75
+
+
+def env_rank():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
+        int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def shard(rank: int, world: int, frames_per_gpu: int):
+    """Frame ids of a rank: a disjoint range per rank (weak scaling, no data exchange)."""
+    return rank * frames_per_gpu, frames_per_gpu
+
+
+def make_inputs(code, frames, rank, world, pinned=False):
+    import torch
+    off, F = shard(rank, world, frames)
+    ys, cws, sigmas = [], [], []
+    for j, eb in enumerate(EBN0_DB):
+        buf = torch.empty((F, code.n), dtype=torch.float32, pin_memory=pinned) if pinned else None
+        y, cw, sig = wl.frames(code, F, eb, seed=DATA_SEED + j, frame_offset=off,
+                               out=None if buf is None else buf.numpy())
+        ys.append(buf if buf is not None else y)
+        cws.append(cw)
+        sigmas.append(sig)
+    return off, ys, cws, sigmas
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region (read only; changes no setting)."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.send_signal(signal.SIGTERM)
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            for ln in open(self.path):
+                p = [x.strip() for x in ln.split(",")]
+                if len(p) >= 9:
+                    rows.append(p)
+        except OSError:
+            pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        pw = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows), "power_w_max": max(pw) if pw else None}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def cpu_baseline(code, ys, cws, sigmas, gpu_outs, target_s=15.0):
+    """FP32 reference decoder on all host cores, on a bounded sample of the same frames;
+    also checks that the GPU decoded those frames identically."""
+    import oracle
+    O = oracle.load()
+    op = oracle.make_params(**PARAMS)
+    cores = os.cpu_count() or 1
+    # calibrate on a small slice, then size the sample for about target_s seconds
+    probe = max(cores, 64)
+    t0 = time.perf_counter()
+    O.decode_f32(code, np.asarray(ys[1][:probe]), sigmas[1], op, seed=DECODER_SEED + 1, threads=cores)
+    per_frame = (time.perf_counter() - t0) / probe
+    per_point = int(max(cores, min(20000, target_s / max(per_frame, 1e-7) / len(EBN0_DB))))
+    total, secs, mism = 0, 0.0, 0
+    for j in range(len(EBN0_DB)):
+        y = np.ascontiguousarray(np.asarray(ys[j][:per_point]))
+        t0 = time.perf_counter()
+        b, it, ps = O.decode_f32(code, y, sigmas[j], op, seed=DECODER_SEED + j, frame_offset=0, threads=cores)
+        secs += time.perf_counter() - t0
+        total += per_point
+        if gpu_outs is not None:
+            gb, gi, gp = gpu_outs[j]
+            mism += int(((gb[:per_point] != b).any(axis=1) | (gi[:per_point] != it) | (gp[:per_point] != ps)).sum())
+    fps = total / secs
+    return {"value": fps, "unit": "frames/s", "cores": cores, "kind": "oracle",
+            "sample": f"first {per_point} frames of each of the {len(EBN0_DB)} Eb/N0 batches "
+                      f"({total} frames, FP32 reference decoder, {cores} threads)",
+            "info_gbit_s": fps * code.k / 1e9, "seconds": secs,
+            "parity": {"frames": total, "mismatches": mism}}
+
+
+def error_rates(code, outs, cws):
+    res = {}
+    info = code.encoder().info_pos
+    for j, eb in enumerate(EBN0_DB):
+        b, it, ps = outs[j]
+        fe = (b != cws[j]).any(axis=1)
+        xb = wl.unpack_bits(b, code.n)[:, info]
+        tb = wl.unpack_bits(cws[j], code.n)[:, info]
+        be = (xb != tb)
+        n = b.shape[0]
+        fer = float(fe.mean())
+        half = 1.96 * math.sqrt(max(fer * (1 - fer), 1.0 / n) / n)
+        res[str(eb)] = {"frames": n, "fer": fer, "fer_ci95": [max(0.0, fer - half), fer + half],
+                        "ber_info": float(be.mean()), "avg_iters": float(it.mean()),
+                        "pass_rate": float(ps.mean())}
+    return res
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    from paper_1402_2773_gb300 import ngdbf
+
+    rank, world, local = env_rank()
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    ngdbf.load()
+    code = wl.code_c2()
+    off, ys_host, cws, sigmas = make_inputs(code, args.frames_per_point, rank, world, pinned=True)
+    dc = ngdbf.DeviceCode.from_code(code)
+    gp = ngdbf.make_params(**PARAMS)
+    ys = [y.cuda(non_blocking=False) for y in ys_host]
+    F = args.frames_per_point
+    nb = (code.n + 7) // 8
+    outs = [(torch.empty((F, nb), dtype=torch.uint8, device="cuda"),
+             torch.empty(F, dtype=torch.int32, device="cuda"),
+             torch.empty(F, dtype=torch.uint8, device="cuda")) for _ in EBN0_DB]
+    stream = torch.cuda.current_stream()
+
+    def step(evs=None):
+        for j in range(len(EBN0_DB)):
+            if evs is not None:
+                evs[j][0].record(stream)
+            dc.decode(ys[j], sigmas[j], gp, seed=DECODER_SEED + j, frame_offset=off, out=outs[j], stream=stream)
+            if evs is not None:
+                evs[j][1].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    launch = ngdbf.ngdbf_last_launch()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    evs = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+            for _ in EBN0_DB] for _ in range(args.steps)]
+    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        t_start.record(stream)
+        for s in range(args.steps):
+            step(evs[s])
+        t_end.record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    elapsed = t_start.elapsed_time(t_end) / 1e3
+    kernel_ms = [evs[s][j][0].elapsed_time(evs[s][j][1]) for s in range(args.steps) for j in range(len(EBN0_DB))]
+    if world > 1:
+        t = torch.tensor([elapsed], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+    frames_total = F * len(EBN0_DB) * args.steps * world
+    fps = frames_total / elapsed
+
+    host_outs = [(b.cpu().numpy(), i.cpu().numpy(), p.cpu().numpy()) for b, i, p in outs]
+    rates = error_rates(code, host_outs, cws)
+    # roofline: algorithmic lane-ops of the iterations the frames needed, per launch
+    sym_iters = [float(o[1].astype(np.int64).sum()) * code.n for o in host_outs]
+    mean_launch_s = float(np.mean(kernel_ms)) / 1e3
+    ops_per_launch = float(np.mean(sym_iters)) * OPS_PER_SYMBOL_ITER
+    clocks = clk.summary()
+    peak_mhz = clocks.get("sm_max_mhz") or measured_peaks().get("sm_max_mhz") or 2070.0
+    sm_count = launch.get("sm_count") or 152
+    peak_ops = sm_count * 128 * peak_mhz * 1e6      # 4 schedulers x 32 lanes issue per SM-clock
+    achieved = ops_per_launch / mean_launch_s
+    traffic = None
+    rl = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12, "unit": "Tlane-op/s",
+          "frac": achieved / peak_ops, "traffic": traffic,
+          "kernel": "ngdbf_persistent_kernel<ADAPT,SMOOTH,state in smem>",
+          "ops_per_symbol_iter": OPS_PER_SYMBOL_ITER,
+          "symbol_iters_per_launch": float(np.mean(sym_iters)), "mean_launch_ms": mean_launch_s * 1e3,
+          "peak_basis": f"{sm_count} SMs x 128 lanes x {peak_mhz:.0f} MHz (max SM clock)"}
+
+    # end to end through the host-buffer C-ABI call: copies inside the timed region
+    e2e_steps = max(1, min(args.steps, 2))
+    bits_h = [np.empty((F, nb), np.uint8) for _ in EBN0_DB]
+    it_h = [np.empty(F, np.int32) for _ in EBN0_DB]
+    ps_h = [np.empty(F, np.uint8) for _ in EBN0_DB]
+    bits_p = [torch.empty((F, nb), dtype=torch.uint8, pin_memory=True) for _ in EBN0_DB]
+    it_p = [torch.empty(F, dtype=torch.int32, pin_memory=True) for _ in EBN0_DB]
+    ps_p = [torch.empty(F, dtype=torch.uint8, pin_memory=True) for _ in EBN0_DB]
+    del bits_h, it_h, ps_h
+    dc.decode_host(ys_host[0][:4096], sigmas[0], gp, seed=DECODER_SEED, frame_offset=off,
+                   out=(bits_p[0][:4096], it_p[0][:4096], ps_p[0][:4096]))
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        for j in range(len(EBN0_DB)):
+            dc.decode_host(ys_host[j], sigmas[j], gp, seed=DECODER_SEED + j, frame_offset=off,
+                           out=(bits_p[j], it_p[j], ps_p[j]))
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_ok = all(np.array_equal(bits_p[j].numpy(), host_outs[j][0]) for j in range(len(EBN0_DB)))
+    e2e = {"value": F * len(EBN0_DB) * e2e_steps * world / e2e_s, "unit": "frames/s",
+           "h2d_bytes_per_step": F * code.n * 4 * len(EBN0_DB),
+           "d2h_bytes_per_step": F * (nb + 4 + 1) * len(EBN0_DB), "steps": e2e_steps,
+           "matches_device_run": bool(e2e_ok)}
+
+    base = None
+    if rank == 0 and not args.no_cpu_baseline:
+        base = cpu_baseline(code, [y.numpy() for y in ys_host], cws, sigmas, host_outs)
+
+    if rank == 0:
+        line = {
+            "metric": "decoded frames/s", "value": fps, "unit": "frames/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded PEG code, random information words, AWGN)",
+            "config": {"workload": "SM-NGDBF (adaptive, smoothed), PEG (6,32) N=2048 M=384 rate 1665/2048, "
+                                   "10^6 frames at each of Eb/N0 3.5/4.0/4.5 dB per step",
+                       "code": "peg(6,32) N=2048 M=384 seed 1", "frames_per_point": F,
+                       "ebn0_db": list(EBN0_DB), "params": PARAMS, "decoder_seed": DECODER_SEED,
+                       "l2": "inputs larger than L2 (8.2 GB of samples per batch)",
+                       "parallelism": f"replicas x{world} (disjoint frame ranges)"},
+            "info_gbit_s": fps * code.k / 1e9,
+            "roofline": rl,
+            "error_rates": rates,
+            "launch": launch,
+            "gpu_launches": len(EBN0_DB) * args.steps,
+            "clocks": clocks,
+            "e2e": e2e,
+            "cpu_baseline": base,
+        }
+        print(json.dumps(line))
+    dc.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def run_reference(args):
+    """The FP32 reference decoder on the host cores: same workload, metric and unit."""
+    rank, world, _ = env_rank()
+    if rank != 0:
+        return
+    import oracle
+    O = oracle.load()
+    code = wl.code_c2()
+    cores = os.cpu_count() or 1
+    op = oracle.make_params(**PARAMS)
+    # per step: a bounded sample of each Eb/N0 batch, sized so the run ends within minutes
+    per_point = max(cores, int(os.environ.get("NGDBF_REF_FRAMES", "0")) or 0)
+    ys, sig = [], []
+    if not per_point:
+        y, _, s = wl.frames(code, 4 * cores, 4.0, seed=DATA_SEED + 1)
+        t0 = time.perf_counter()
+        O.decode_f32(code, y, s, op, seed=DECODER_SEED + 1, threads=cores)
+        per_frame = (time.perf_counter() - t0) / (4 * cores)
+        per_point = int(max(cores, min(5000, 6.0 / max(per_frame, 1e-7) / len(EBN0_DB))))
+    for j, eb in enumerate(EBN0_DB):
+        y, _, s = wl.frames(code, per_point, eb, seed=DATA_SEED + j)
+        ys.append(y)
+        sig.append(s)
+
+    def step():
+        for j in range(len(EBN0_DB)):
+            O.decode_f32(code, ys[j], sig[j], op, seed=DECODER_SEED + j, threads=cores)
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    secs = time.perf_counter() - t0
+    fps = per_point * len(EBN0_DB) * args.steps / secs
+    sample = (f"first {per_point} frames of each of the {len(EBN0_DB)} Eb/N0 batches per step, "
+              f"FP32 reference decoder, {cores} threads")
+    print(json.dumps({
+        "impl": "reference", "metric": "decoded frames/s", "value": fps, "unit": "frames/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": secs / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded PEG code, random information words, AWGN)",
+        "config": {"workload": "SM-NGDBF (adaptive, smoothed), PEG (6,32) N=2048 M=384 rate 1665/2048, "
+                               "10^6 frames at each of Eb/N0 3.5/4.0/4.5 dB per step",
+                   "code": "peg(6,32) N=2048 M=384 seed 1", "frames_per_point": per_point,
+                   "ebn0_db": list(EBN0_DB), "params": PARAMS},
+        "info_gbit_s": fps * code.k / 1e9,
+        "cpu_baseline": {"value": fps, "unit": "frames/s", "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": fps, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+    }))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--frames-per-point", type=int, default=FRAMES_PER_POINT,
+                    help="frames per Eb/N0 batch (the benchmark workload is 10^6; smaller only for profiling)")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,170 @@
+/*
+ * ngdbf.h -- C ABI of the GB300 Noisy Gradient Descent Bit-Flip (NGDBF)
+ * LDPC decoder.
+ *
+ * Method: Sundararajan, Winstead, Boutillon, "Noisy Gradient Descent
+ * Bit-Flip Decoding for LDPC Codes", IEEE Trans. Commun. 62(10), 2014.
+ *   Sec. III-A  code, channel and notation: H (m x n, n > m >= 1), bipolar
+ *               codewords 1 - 2c, y = c^ + z with var(z) = N0/2,
+ *               x(0) = sign(y), N(i), M(k), s_i = prod_{j in N(i)} x_j
+ *   Sec. III-B  Step 1 (syndromes, stop when all s_i = +1), Step 3b
+ *               (multi-bit flip when E_k < theta), Step 4 (repeat to T)
+ *   Sec. III-C  Step 2: E_k = x_k y_k + w sum_{i in M(k)} s_i + q_k,
+ *               q_k ~ N(0, eta^2 N0/2)
+ *   Sec. III-D  threshold adaptation: theta_k <- theta_k lambda when x_k is
+ *               not flipped (implemented as theta lambda^{u_k}, Sec. V-A,
+ *               Eqs. 11-12, u_k = number of non-flips)
+ *   Sec. III-E  output smoothing, Eq. 7: up/down counter X_k over
+ *               t = T-W .. T, output sign(X_k) when T is reached
+ *
+ * Conventions shared by every entry point:
+ *   - Bits: bit k of frame f is byte f*ceil(n/8) + k/8, bit k%8 (LSB
+ *     first); bit 1 <=> x_k = -1 <=> c_k = 1.
+ *   - Samples are saturated to [-y_max, y_max] first (Sec. IV-A), sign(0)
+ *     is +1.  Decisions E_k < theta_k flip; a tie does not flip.
+ *   - iters[f] = iteration t at which all checks were satisfied (0 for a
+ *     valid input), or t_max when the limit was reached; pass[f] = 1 iff
+ *     all checks were satisfied (the smoothed output is not re-checked).
+ *   - q_k is drawn by Philox4x32-10 (Salmon et al., SC'11) keyed by
+ *     (seed_lo, seed_hi) with counter (k/4, t, frame_lo, frame_hi), where
+ *     frame = frame_offset + index of the frame in the call, and mapped by
+ *     Box-Muller: u = ((r >> 9) + 1/2) 2^-23; symbols 4g, 4g+1 take
+ *     rho cos(2 pi u1), rho sin(2 pi u1), rho = sqrt(-2 ln u0), from outputs
+ *     (r0, r1); symbols 4g+2, 4g+3 take the same from (r2, r3).  ln, sin and
+ *     cos are evaluated in FP32 from their series (atanh series of ln;
+ *     Taylor series of sin/cos of (pi/2) xi, |xi| <= 1/2, after an exact
+ *     quadrant split); the perturbation is fl32(eta * sigma) * z.  A frame's
+ *     result therefore depends only on (y, sigma, params, seed, frame id):
+ *     never on the other frames of the call or on the launch shape.
+ *   - Errors: every function returns a status and never aborts;
+ *     ngdbf_last_error() gives a message for the calling thread.  CUDA
+ *     errors raised by earlier asynchronous work may surface on a later call.
+ */
+#ifndef NGDBF_H
+#define NGDBF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    NGDBF_OK = 0,
+    NGDBF_ERR_INVALID_ARG = 1,   /* bad pointer, size, index or parameter */
+    NGDBF_ERR_OOM = 2,           /* device or host allocation failed */
+    NGDBF_ERR_CUDA = 3,          /* a CUDA runtime call failed */
+    NGDBF_ERR_UNSUPPORTED = 4    /* valid input outside this build's limits */
+} ngdbf_status;
+
+/* Variant bits (Sec. III-C/D/E).  0 = plain M-NGDBF with one threshold. */
+enum { NGDBF_ADAPT = 1, NGDBF_SMOOTH = 2 };
+
+/* Arithmetic of the inversion function.  Only FP32 is implemented here. */
+enum { NGDBF_FP32 = 0 };
+
+/* Limits of this build. */
+enum {
+    NGDBF_MAX_T = 511,            /* t_max */
+    NGDBF_MAX_WINDOW = 126,       /* smooth_window */
+    NGDBF_MAX_N = 65535,          /* symbols */
+    NGDBF_MAX_DEGREE = 64         /* symbol and check degree */
+};
+
+typedef struct ngdbf_params {
+    float w;              /* syndrome weight w > 0 (Sec. III-C) */
+    float theta;          /* initial inversion threshold (Sec. III-B), finite */
+    float eta;            /* noise scale, 0 <= eta <= 1; 0 gives plain GDBF (Sec. III-C) */
+    float lambda;         /* adaptation factor, 0 < lambda <= 1 (Sec. III-D) */
+    float y_max;          /* saturation magnitude; <= 0 or +inf disables (Sec. IV-A) */
+    int32_t t_max;        /* T: at most T flip phases, 0 <= T <= NGDBF_MAX_T */
+    int32_t smooth_window;/* W: X_k sums x(t) for t = max(0, T-W) .. T, 0 <= W <= 126 */
+    int32_t variant;      /* OR of NGDBF_ADAPT, NGDBF_SMOOTH */
+    int32_t precision;    /* NGDBF_FP32 */
+    int32_t q_bits;       /* reserved, must be 0 */
+} ngdbf_params;
+
+typedef struct ngdbf_code ngdbf_code_t;   /* opaque; owned by the library */
+
+/*
+ * Builds the device-resident tables of a parity-check matrix H (Sec. III-A).
+ *   n, m      symbols and checks, n > m >= 1, n <= NGDBF_MAX_N
+ *   row_ptr   HOST int32[m+1], row_ptr[0] = 0, non-decreasing
+ *   col_idx   HOST int32[row_ptr[m]]: N(i) = col_idx[row_ptr[i] .. row_ptr[i+1])
+ * Every check must have degree >= 1 and every symbol degree >= 1; degrees
+ * are at most NGDBF_MAX_DEGREE; no column may repeat within a row.
+ * The arrays are copied; the caller keeps ownership.  On success *out
+ * receives a handle that must be released with ngdbf_code_destroy.  The
+ * tables live on the device that is current at this call.
+ * Errors: INVALID_ARG (bad structure), UNSUPPORTED (limits), OOM, CUDA.
+ */
+ngdbf_status ngdbf_code_create(int32_t n, int32_t m, const int32_t* row_ptr,
+                               const int32_t* col_idx, ngdbf_code_t** out);
+
+/* Releases a code handle (NULL is accepted).  The caller must ensure no
+ * decode using it is still running on the device. */
+ngdbf_status ngdbf_code_destroy(ngdbf_code_t* code);
+
+/* Reports n, m, maximum symbol degree and maximum check degree. */
+ngdbf_status ngdbf_code_info(const ngdbf_code_t* code, int32_t* n, int32_t* m,
+                             int32_t* dv_max, int32_t* dc_max);
+
+/*
+ * Decodes a batch of frames on the GPU (Steps 0-4 of Sec. III-B with Step 2
+ * of Sec. III-C, adaptation of Sec. III-D and smoothing of Sec. III-E as
+ * selected by params->variant).
+ *   y            DEVICE float[n_frames][n], frame-major channel samples
+ *   n_frames     >= 0 (0 returns immediately)
+ *   sigma        channel noise standard deviation (N0/2 = sigma^2), >= 0
+ *   seed         Philox key of the perturbation
+ *   frame_offset frame id of y[0] for the perturbation counter
+ *   bits         DEVICE uint8[n_frames][ceil(n/8)] decoded words (written)
+ *   iters        DEVICE int32[n_frames] (written)
+ *   pass         DEVICE uint8[n_frames] (written)
+ *   stream       cudaStream_t to run on (NULL = legacy default stream)
+ * Asynchronous: returns after enqueueing; outputs are valid once the stream
+ * reaches this point.  Temporary device memory (per-slot sample copies and
+ * a work counter, about 160 * n bytes per 32 concurrently decoded frames)
+ * is taken from a library-owned stream-ordered pool and returned on the
+ * same stream.  All pointers must be device memory of the current device.
+ * Errors: INVALID_ARG, UNSUPPORTED, OOM, CUDA.
+ */
+ngdbf_status ngdbf_decode(const ngdbf_code_t* code, const float* y, int64_t n_frames,
+                          float sigma, const ngdbf_params* params, uint64_t seed,
+                          uint64_t frame_offset, uint8_t* bits, int32_t* iters,
+                          uint8_t* pass, void* stream);
+
+/*
+ * Same decode with HOST buffers, synchronous: copies y to the device in
+ * chunks on two streams, decodes each chunk as soon as it has arrived while
+ * the next chunk is copied, copies the outputs back, and returns when the
+ * host outputs are written.  Page-locked host buffers give overlapped
+ * copies; pageable ones work but serialize.  Same layouts as ngdbf_decode.
+ * chunk_frames <= 0 picks a chunk size automatically.
+ */
+ngdbf_status ngdbf_decode_host(const ngdbf_code_t* code, const float* y_host, int64_t n_frames,
+                               float sigma, const ngdbf_params* params, uint64_t seed,
+                               uint64_t frame_offset, uint8_t* bits_host, int32_t* iters_host,
+                               uint8_t* pass_host, int64_t chunk_frames);
+
+/* Launch shape of the most recent ngdbf_decode on the calling thread. */
+typedef struct ngdbf_launch_info {
+    int32_t grid;            /* CTAs (each owns 32 frame slots) */
+    int32_t block;           /* threads per CTA */
+    int32_t smem_bytes;      /* dynamic shared memory per CTA */
+    int32_t state_in_smem;   /* 1 if per-(symbol, slot) counters live in shared memory */
+    int32_t kernels;         /* kernels launched by the call */
+    int32_t sm_count;        /* SMs of the device */
+} ngdbf_launch_info;
+
+ngdbf_status ngdbf_last_launch(ngdbf_launch_info* out);
+
+/* Message for the last error on the calling thread ("" if none). */
+const char* ngdbf_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NGDBF_H */

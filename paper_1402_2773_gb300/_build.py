@@ -1,0 +1,52 @@
+"""In-tree build of the decoder library (nvcc, sm_103a) and the workload helper (gcc)."""
+from __future__ import annotations
+
+import os
+import subprocess
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(PKG)
+CSRC = os.path.join(PKG, "csrc")
+LIB_PATH = os.path.join(PKG, "libngdbf.so")
+SOURCES = [os.path.join(CSRC, "ngdbf_decode.cu")]
+DEPS = SOURCES + [os.path.join(CSRC, "ngdbf_device.cuh"), os.path.join(ROOT, "include", "ngdbf.h")]
+
+NVCC_FLAGS = [
+    "-std=c++17", "-O3", "-lineinfo",
+    "-gencode", "arch=compute_103a,code=sm_103a",
+    # every FP32 operation of the method is an explicitly rounded intrinsic;
+    # no contraction elsewhere either
+    "--fmad=false",
+    "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
+    "-shared",
+]
+
+
+def nvcc() -> str:
+    for cand in (os.environ.get("NVCC"), "/usr/local/cuda/bin/nvcc", "nvcc"):
+        if cand and (os.path.isabs(cand) and os.path.exists(cand) or not os.path.isabs(cand)):
+            return cand
+    return "nvcc"
+
+
+def stale(target: str, deps: list[str]) -> bool:
+    if not os.path.exists(target):
+        return True
+    t = os.path.getmtime(target)
+    return any(os.path.getmtime(d) > t for d in deps)
+
+
+def build_cuda(force: bool = False, verbose: bool = False) -> str:
+    """Compiles libngdbf.so next to this file; returns its path."""
+    if force or stale(LIB_PATH, DEPS):
+        tmp = LIB_PATH + ".tmp"
+        cmd = [nvcc(), *NVCC_FLAGS, *(["-Xptxas", "-v"] if verbose else []), "-o", tmp, *SOURCES]
+        subprocess.check_call(cmd)
+        os.replace(tmp, LIB_PATH)
+    return LIB_PATH
+
+
+def build_all(force: bool = False) -> None:
+    from . import workload
+    workload.build(force)
+    build_cuda(force)

@@ -1,0 +1,210 @@
+"""ctypes binding of the C ABI declared in include/ngdbf.h.
+
+The functions keep the C names and only marshal arguments; every step of the
+decode runs in the CUDA library ``libngdbf.so``.  There is no CPU fallback:
+loading fails loudly when the library has not been built, and the decode
+functions need CUDA device pointers (torch tensors on the GPU work).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+from ._build import LIB_PATH, ROOT
+
+NGDBF_OK = 0
+NGDBF_ERR_INVALID_ARG = 1
+NGDBF_ERR_OOM = 2
+NGDBF_ERR_CUDA = 3
+NGDBF_ERR_UNSUPPORTED = 4
+NGDBF_ADAPT = 1
+NGDBF_SMOOTH = 2
+NGDBF_FP32 = 0
+NGDBF_MAX_T = 511
+NGDBF_MAX_WINDOW = 126
+
+HEADER = os.path.join(ROOT, "include", "ngdbf.h")
+
+
+class NgdbfError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"ngdbf status {status}: {message}")
+        self.status = status
+
+
+class ngdbf_params(ctypes.Structure):
+    _fields_ = [("w", ctypes.c_float), ("theta", ctypes.c_float), ("eta", ctypes.c_float),
+                ("lambda_", ctypes.c_float), ("y_max", ctypes.c_float),
+                ("t_max", ctypes.c_int32), ("smooth_window", ctypes.c_int32),
+                ("variant", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("q_bits", ctypes.c_int32)]
+
+
+class ngdbf_launch_info(ctypes.Structure):
+    _fields_ = [("grid", ctypes.c_int32), ("block", ctypes.c_int32), ("smem_bytes", ctypes.c_int32),
+                ("state_in_smem", ctypes.c_int32), ("kernels", ctypes.c_int32),
+                ("sm_count", ctypes.c_int32)]
+
+
+def make_params(w=0.75, theta=-0.9, eta=0.96, lam=1.0, y_max=2.5, t_max=100, smooth_window=64,
+                variant=0) -> ngdbf_params:
+    return ngdbf_params(w, theta, eta, lam, y_max, t_max, smooth_window, variant, NGDBF_FP32, 0)
+
+
+_lib = None
+
+
+def load(path: str | None = None) -> ctypes.CDLL:
+    """Loads libngdbf.so; raises if it is missing (no fallback exists)."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError(f"CUDA decoder library not built: {p} is missing "
+                           "(run __graft_entry__.build() or paper_1402_2773_gb300._build.build_cuda())")
+    lib = ctypes.CDLL(p)
+    vp = ctypes.c_void_p
+    i32p = ctypes.POINTER(ctypes.c_int32)
+    lib.ngdbf_code_create.argtypes = [ctypes.c_int32, ctypes.c_int32, i32p, i32p, ctypes.POINTER(vp)]
+    lib.ngdbf_code_destroy.argtypes = [vp]
+    lib.ngdbf_code_info.argtypes = [vp, i32p, i32p, i32p, i32p]
+    lib.ngdbf_decode.argtypes = [vp, vp, ctypes.c_int64, ctypes.c_float, ctypes.POINTER(ngdbf_params),
+                                 ctypes.c_uint64, ctypes.c_uint64, vp, vp, vp, vp]
+    lib.ngdbf_decode_host.argtypes = [vp, vp, ctypes.c_int64, ctypes.c_float,
+                                      ctypes.POINTER(ngdbf_params), ctypes.c_uint64, ctypes.c_uint64,
+                                      vp, vp, vp, ctypes.c_int64]
+    lib.ngdbf_last_launch.argtypes = [ctypes.POINTER(ngdbf_launch_info)]
+    lib.ngdbf_last_error.argtypes = []
+    lib.ngdbf_last_error.restype = ctypes.c_char_p
+    for fn in ("ngdbf_code_create", "ngdbf_code_destroy", "ngdbf_code_info", "ngdbf_decode",
+               "ngdbf_decode_host", "ngdbf_last_launch"):
+        getattr(lib, fn).restype = ctypes.c_int
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def declared_functions() -> list[str]:
+    """Names of the functions include/ngdbf.h declares."""
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(ngdbf_[a-z_0-9]+)\s*\(", src)))
+
+
+def _check(lib, status: int) -> None:
+    if status != NGDBF_OK:
+        raise NgdbfError(status, lib.ngdbf_last_error().decode())
+
+
+# --- C-named entry points (argument marshalling only) --------------------------------------------
+
+def ngdbf_last_error() -> str:
+    return load().ngdbf_last_error().decode()
+
+
+def ngdbf_code_create(n: int, m: int, row_ptr, col_idx) -> int:
+    lib = load()
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int32)
+    ci = np.ascontiguousarray(col_idx, dtype=np.int32)
+    h = ctypes.c_void_p()
+    _check(lib, lib.ngdbf_code_create(n, m, rp.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                      ci.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), ctypes.byref(h)))
+    return h.value
+
+
+def ngdbf_code_destroy(code: int) -> None:
+    lib = load()
+    _check(lib, lib.ngdbf_code_destroy(code))
+
+
+def ngdbf_code_info(code: int):
+    lib = load()
+    v = [ctypes.c_int32() for _ in range(4)]
+    _check(lib, lib.ngdbf_code_info(code, *[ctypes.byref(x) for x in v]))
+    return tuple(x.value for x in v)
+
+
+def ngdbf_decode(code: int, y_ptr: int, n_frames: int, sigma: float, params: ngdbf_params, seed: int,
+                 frame_offset: int, bits_ptr: int, iters_ptr: int, pass_ptr: int, stream: int = 0) -> None:
+    lib = load()
+    _check(lib, lib.ngdbf_decode(code, y_ptr, n_frames, sigma, ctypes.byref(params), seed, frame_offset,
+                                 bits_ptr, iters_ptr, pass_ptr, stream))
+
+
+def ngdbf_decode_host(code: int, y_ptr: int, n_frames: int, sigma: float, params: ngdbf_params, seed: int,
+                      frame_offset: int, bits_ptr: int, iters_ptr: int, pass_ptr: int,
+                      chunk_frames: int = 0) -> None:
+    lib = load()
+    _check(lib, lib.ngdbf_decode_host(code, y_ptr, n_frames, sigma, ctypes.byref(params), seed,
+                                      frame_offset, bits_ptr, iters_ptr, pass_ptr, chunk_frames))
+
+
+def ngdbf_last_launch() -> dict:
+    lib = load()
+    info = ngdbf_launch_info()
+    _check(lib, lib.ngdbf_last_launch(ctypes.byref(info)))
+    return {f: getattr(info, f) for f, _ in info._fields_}
+
+
+# --- convenience over torch device memory -----------------------------------------------------------
+
+class DeviceCode:
+    """A parity-check matrix resident on the current CUDA device."""
+
+    def __init__(self, n: int, m: int, row_ptr, col_idx):
+        self.n, self.m = int(n), int(m)
+        self.handle = ngdbf_code_create(self.n, self.m, row_ptr, col_idx)
+
+    @classmethod
+    def from_code(cls, code) -> "DeviceCode":
+        return cls(code.n, code.m, code.row_ptr, code.col_idx)
+
+    def close(self) -> None:
+        if self.handle:
+            ngdbf_code_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def decode(self, y, sigma: float, params: ngdbf_params, seed: int = 1, frame_offset: int = 0,
+               out=None, stream=None):
+        """y: float32 CUDA tensor [F, n].  Returns (bits uint8 [F, ceil(n/8)], iters int32 [F],
+        pass uint8 [F]) as CUDA tensors, enqueued on ``stream`` (default: torch's current stream)."""
+        import torch
+        assert y.is_cuda and y.dtype == torch.float32 and y.is_contiguous() and y.shape[-1] == self.n
+        F = y.shape[0]
+        if out is None:
+            bits = torch.empty((F, (self.n + 7) // 8), dtype=torch.uint8, device=y.device)
+            iters = torch.empty(F, dtype=torch.int32, device=y.device)
+            pas = torch.empty(F, dtype=torch.uint8, device=y.device)
+        else:
+            bits, iters, pas = out
+        s = stream if stream is not None else torch.cuda.current_stream(y.device)
+        ngdbf_decode(self.handle, y.data_ptr(), F, float(sigma), params, int(seed), int(frame_offset),
+                     bits.data_ptr(), iters.data_ptr(), pas.data_ptr(), s.cuda_stream)
+        return bits, iters, pas
+
+    def decode_host(self, y: np.ndarray, sigma: float, params: ngdbf_params, seed: int = 1,
+                    frame_offset: int = 0, out=None, chunk_frames: int = 0):
+        """Host arrays in and out (numpy or pinned CPU torch tensors)."""
+        F = y.shape[0]
+        if out is None:
+            bits = np.empty((F, (self.n + 7) // 8), dtype=np.uint8)
+            iters = np.empty(F, dtype=np.int32)
+            pas = np.empty(F, dtype=np.uint8)
+        else:
+            bits, iters, pas = out
+
+        def ptr(a):
+            return a.ctypes.data if isinstance(a, np.ndarray) else a.data_ptr()
+        ngdbf_decode_host(self.handle, ptr(y), F, float(sigma), params, int(seed), int(frame_offset),
+                          ptr(bits), ptr(iters), ptr(pas), chunk_frames)
+        return bits, iters, pas

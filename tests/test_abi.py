@@ -1,0 +1,64 @@
+"""C ABI: the library builds, loads and exports what include/ngdbf.h declares (no GPU needed)."""
+import ctypes
+import re
+
+import numpy as np
+import pytest
+
+from paper_1402_2773_gb300 import _build, ngdbf
+
+
+@pytest.fixture(scope="module")
+def lib():
+    _build.build_cuda()
+    return ngdbf.load()
+
+
+def test_header_declares_the_boundary():
+    names = ngdbf.declared_functions()
+    for want in ("ngdbf_code_create", "ngdbf_code_destroy", "ngdbf_decode", "ngdbf_decode_host",
+                 "ngdbf_last_error", "ngdbf_code_info", "ngdbf_last_launch"):
+        assert want in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for name in ngdbf.declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_params_struct_matches_header():
+    src = open(ngdbf.HEADER).read()
+    body = re.search(r"typedef struct ngdbf_params \{(.*?)\} ngdbf_params;", src, re.S).group(1)
+    fields = re.findall(r"\b(float|int32_t)\s+([a-z_]+);", body)
+    assert [f for _, f in fields] == ["w", "theta", "eta", "lambda", "y_max", "t_max", "smooth_window",
+                                      "variant", "precision", "q_bits"]
+    assert ctypes.sizeof(ngdbf.ngdbf_params) == 4 * len(fields)
+
+
+def test_host_validation_without_a_device(lib):
+    """Structural errors are reported before any CUDA call, with a message."""
+    h = ctypes.c_void_p()
+    i32p = ctypes.POINTER(ctypes.c_int32)
+
+    def create(n, m, rp, ci):
+        rp = np.ascontiguousarray(rp, np.int32)
+        ci = np.ascontiguousarray(ci, np.int32)
+        return lib.ngdbf_code_create(n, m, rp.ctypes.data_as(i32p), ci.ctypes.data_as(i32p), ctypes.byref(h))
+
+    assert create(4, 4, [0, 1, 2, 3, 4], [0, 1, 2, 3]) == ngdbf.NGDBF_ERR_INVALID_ARG      # n > m
+    assert create(4, 2, [0, 2, 4], [0, 5, 1, 2]) == ngdbf.NGDBF_ERR_INVALID_ARG            # index
+    assert "range" in lib.ngdbf_last_error().decode()
+    assert create(4, 2, [0, 2, 4], [0, 0, 1, 2]) == ngdbf.NGDBF_ERR_INVALID_ARG            # repeat
+    assert create(4, 2, [0, 2, 2], [0, 1]) == ngdbf.NGDBF_ERR_INVALID_ARG                  # empty row
+    assert create(4, 2, [0, 2, 3], [0, 1, 2]) == ngdbf.NGDBF_ERR_INVALID_ARG               # symbol 3 unused
+    assert create(70000, 2, [0, 1, 2], [0, 1]) == ngdbf.NGDBF_ERR_UNSUPPORTED              # n too large
+    p = ngdbf.make_params()
+    assert lib.ngdbf_decode(None, None, 1, 0.5, ctypes.byref(p), 1, 0, None, None, None, None) == \
+        ngdbf.NGDBF_ERR_INVALID_ARG
+    assert lib.ngdbf_decode_host(None, None, 1, 0.5, ctypes.byref(p), 1, 0, None, None, None, 0) == \
+        ngdbf.NGDBF_ERR_INVALID_ARG
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    with pytest.raises(RuntimeError, match="not built"):
+        ngdbf.load(str(tmp_path / "absent.so"))
