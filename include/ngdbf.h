@@ -69,7 +69,8 @@ enum {
     NGDBF_MAX_T = 511,            /* t_max */
     NGDBF_MAX_WINDOW = 126,       /* smooth_window */
     NGDBF_MAX_N = 65535,          /* symbols */
-    NGDBF_MAX_DEGREE = 64         /* symbol and check degree */
+    NGDBF_MAX_DEGREE = 64,        /* symbol and check degree */
+    NGDBF_NOALLOC_SCRATCH_BYTES = 40 << 20   /* static scratch of ngdbf_decode_noalloc */
 };
 
 typedef struct ngdbf_params {
@@ -147,6 +148,35 @@ ngdbf_status ngdbf_decode_host(const ngdbf_code_t* code, const float* y_host, in
                                float sigma, const ngdbf_params* params, uint64_t seed,
                                uint64_t frame_offset, uint8_t* bits_host, int32_t* iters_host,
                                uint8_t* pass_host, int64_t chunk_frames);
+
+/*
+ * ngdbf_decode_noalloc -- ngdbf_decode that allocates no device memory.
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate while they decode, for example a receiver with a fixed
+ * memory plan that forbids allocation after start-up (cudaMalloc may
+ * synchronize the device and its latency is unbounded), or a host
+ * application whose own allocator already owns the device memory.
+ *
+ * Same arguments, layouts and results as ngdbf_decode; the caller still
+ * provides y, bits, iters and pass as device memory.  Instead of taking
+ * scratch from a pool, the call uses one static device array of
+ * NGDBF_NOALLOC_SCRATCH_BYTES that every GPU loading this library holds
+ * until the process exits.  Consequences:
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - Every call shares the array and its work counter (the call clears the
+ *     counter on its stream before the kernel).  Calls that overlap on the
+ *     GPU race and give wrong results: serialize them, e.g. on one stream.
+ *   - When the per-CTA scratch of a full launch does not fit, the launch
+ *     uses fewer CTAs (slower, same results); a code whose single CTA needs
+ *     more than the array holds is rejected with NGDBF_ERR_UNSUPPORTED.
+ * Calls no cudaMalloc, cudaFree or allocating library routine.
+ */
+ngdbf_status ngdbf_decode_noalloc(const ngdbf_code_t* code, const float* y, int64_t n_frames,
+                                  float sigma, const ngdbf_params* params, uint64_t seed,
+                                  uint64_t frame_offset, uint8_t* bits, int32_t* iters,
+                                  uint8_t* pass, void* stream);
 
 /* Launch shape of the most recent ngdbf_decode on the calling thread. */
 typedef struct ngdbf_launch_info {

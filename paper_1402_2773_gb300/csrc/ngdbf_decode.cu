@@ -761,4 +761,116 @@ ngdbf_status ngdbf_decode_host(const ngdbf_code_t* C, const float* y_host, int64
     return rs;
 }
 
+// ---------------------------------------------------------------------------
+// ngdbf_decode_noalloc: the same decode with its scratch in a static device
+// array instead of pool memory, for callers that cannot allocate.
+// ---------------------------------------------------------------------------
+
 }  // extern "C"
+
+namespace {
+
+// Work counter (first 256 bytes), then per-slot samples [grid][n][32] and, when
+// the per-slot state does not fit shared memory, the state words [grid][n][32].
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NGDBF_NOALLOC_SCRATCH_BYTES];
+
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[64] = {};
+
+// Device address of g_noalloc_scratch on the current device, looked up once per device.
+ngdbf_status noalloc_scratch(int dev, unsigned char** out) {
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (dev < 0 || dev >= 64) return fail(NGDBF_ERR_UNSUPPORTED, "device index out of range");
+    if (!g_noalloc_addr[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) return cuda_fail(e, "cudaGetSymbolAddress(static scratch)");
+        g_noalloc_addr[dev] = p;
+    }
+    *out = static_cast<unsigned char*>(g_noalloc_addr[dev]);
+    return NGDBF_OK;
+}
+
+}  // namespace
+
+extern "C" ngdbf_status ngdbf_decode_noalloc(const ngdbf_code_t* C, const float* y, int64_t n_frames,
+                                             float sigma, const ngdbf_params* P, uint64_t seed,
+                                             uint64_t frame_offset, uint8_t* bits, int32_t* iters,
+                                             uint8_t* pass, void* stream_ptr) {
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_ptr);
+    if (!C) return fail(NGDBF_ERR_INVALID_ARG, "code is NULL");
+    ngdbf_status s = check_params(P, sigma);
+    if (s != NGDBF_OK) return s;
+    if (n_frames < 0) return fail(NGDBF_ERR_INVALID_ARG, "n_frames < 0");
+    g_last_launch = {0, 0, 0, 0, 0, 0};
+    if (n_frames == 0) return NGDBF_OK;
+    if (!y || !bits || !iters || !pass) return fail(NGDBF_ERR_INVALID_ARG, "NULL buffer");
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev != C->device) return fail(NGDBF_ERR_INVALID_ARG, "code tables belong to another device");
+    for (const void* p : {(const void*)y, (const void*)bits, (const void*)iters, (const void*)pass}) {
+        cudaPointerAttributes a;
+        e = cudaPointerGetAttributes(&a, p);
+        if (e != cudaSuccess || !(a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged)) {
+            cudaGetLastError();
+            return fail(NGDBF_ERR_INVALID_ARG, "y, bits, iters and pass must be device memory");
+        }
+    }
+    unsigned char* base = nullptr;
+    s = noalloc_scratch(dev, &base);
+    if (s != NGDBF_OK) return s;
+    LaunchPlan plan;
+    KernelFn fn;
+    int sm_count = 0;
+    s = plan_launch(C, P, n_frames, dev, &plan, &fn, &sm_count);
+    if (s != NGDBF_OK) return s;
+
+    // Fit the launch into the static array: fewer CTAs when a full grid does not fit.
+    const bool state = (P->variant & 3) != 0;
+    const size_t per_cta_y = (size_t)C->n * kSlots * 4;
+    const size_t per_cta_st = (state && !plan.st_smem) ? (size_t)C->n * kSlots * 2 : 0;
+    const size_t avail = (size_t)NGDBF_NOALLOC_SCRATCH_BYTES - 256 - 256;   // counter + alignment
+    const size_t max_grid = avail / (per_cta_y + per_cta_st);
+    if (max_grid < 1)
+        return fail(NGDBF_ERR_UNSUPPORTED, "code needs more per-CTA scratch (" +
+                    std::to_string(per_cta_y + per_cta_st) + " bytes) than the static array holds (" +
+                    std::to_string((long long)NGDBF_NOALLOC_SCRATCH_BYTES) + " bytes)");
+    const int grid = (int)std::min<size_t>((size_t)plan.grid, max_grid);
+    const size_t bytes_y = ((size_t)grid * per_cta_y + 255) / 256 * 256;
+
+    DecodeArgs A;
+    std::memset(&A, 0, sizeof(A));
+    A.n = C->n; A.m = C->m; A.dv_max = C->dv_max; A.dc_max = C->dc_max;
+    A.chk_cols = C->d_chk_cols; A.sym_chks = C->d_sym_chks; A.sym_deg = C->d_sym_deg;
+    A.y = y; A.n_frames = n_frames; A.frame_offset = frame_offset;
+    A.bits = bits; A.iters = iters; A.pass = pass; A.nb = (C->n + 7) / 8;
+    A.w = P->w; A.theta = P->theta;
+    A.scale = (float)((double)P->eta * (double)sigma);
+    A.clamp = (P->y_max > 0.0f && std::isfinite(P->y_max)) ? 1 : 0;
+    A.y_max = A.clamp ? P->y_max : 0.0f;
+    A.t_max = P->t_max;
+    A.t_smooth = std::max(0, P->t_max - P->smooth_window);
+    A.queue = reinterpret_cast<unsigned long long*>(base);
+    A.yslots = reinterpret_cast<float*>(base + 256);
+    A.st_global = per_cta_st ? reinterpret_cast<uint16_t*>(base + 256 + bytes_y) : nullptr;
+    host_gen_consts(seed, A.G);
+    double p = 1.0;
+    for (int u = 0; u <= P->t_max; ++u) {
+        A.thr[u] = (float)((double)P->theta * p);
+        p = p * (double)P->lambda;
+    }
+    // The work counter must start at zero; the kernel initializes everything else it reads.
+    e = cudaMemsetAsync(A.queue, 0, sizeof(unsigned long long), stream);
+    if (e != cudaSuccess) return cuda_fail(e, "clearing the static work counter");
+    fn<<<grid, plan.block, plan.smem, stream>>>(A);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "decode launch");
+    g_last_launch.grid = grid;
+    g_last_launch.block = plan.block;
+    g_last_launch.smem_bytes = plan.smem;
+    g_last_launch.state_in_smem = plan.st_smem ? 1 : 0;
+    g_last_launch.kernels = 1;
+    g_last_launch.sm_count = sm_count;
+    return NGDBF_OK;
+}

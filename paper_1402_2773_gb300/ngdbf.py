@@ -25,6 +25,7 @@ NGDBF_SMOOTH = 2
 NGDBF_FP32 = 0
 NGDBF_MAX_T = 511
 NGDBF_MAX_WINDOW = 126
+NGDBF_NOALLOC_SCRATCH_BYTES = 40 << 20
 
 HEADER = os.path.join(ROOT, "include", "ngdbf.h")
 
@@ -77,11 +78,12 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.ngdbf_decode_host.argtypes = [vp, vp, ctypes.c_int64, ctypes.c_float,
                                       ctypes.POINTER(ngdbf_params), ctypes.c_uint64, ctypes.c_uint64,
                                       vp, vp, vp, ctypes.c_int64]
+    lib.ngdbf_decode_noalloc.argtypes = lib.ngdbf_decode.argtypes
     lib.ngdbf_last_launch.argtypes = [ctypes.POINTER(ngdbf_launch_info)]
     lib.ngdbf_last_error.argtypes = []
     lib.ngdbf_last_error.restype = ctypes.c_char_p
     for fn in ("ngdbf_code_create", "ngdbf_code_destroy", "ngdbf_code_info", "ngdbf_decode",
-               "ngdbf_decode_host", "ngdbf_last_launch"):
+               "ngdbf_decode_host", "ngdbf_decode_noalloc", "ngdbf_last_launch"):
         getattr(lib, fn).restype = ctypes.c_int
     if path is None:
         _lib = lib
@@ -133,6 +135,16 @@ def ngdbf_decode(code: int, y_ptr: int, n_frames: int, sigma: float, params: ngd
     lib = load()
     _check(lib, lib.ngdbf_decode(code, y_ptr, n_frames, sigma, ctypes.byref(params), seed, frame_offset,
                                  bits_ptr, iters_ptr, pass_ptr, stream))
+
+
+def ngdbf_decode_noalloc(code: int, y_ptr: int, n_frames: int, sigma: float, params: ngdbf_params,
+                         seed: int, frame_offset: int, bits_ptr: int, iters_ptr: int, pass_ptr: int,
+                         stream: int = 0) -> None:
+    """ngdbf_decode without device allocation: scratch is the library's static device array
+    (calls must not overlap on the GPU; the first call on a device should precede any capture)."""
+    lib = load()
+    _check(lib, lib.ngdbf_decode_noalloc(code, y_ptr, n_frames, sigma, ctypes.byref(params), seed,
+                                         frame_offset, bits_ptr, iters_ptr, pass_ptr, stream))
 
 
 def ngdbf_decode_host(code: int, y_ptr: int, n_frames: int, sigma: float, params: ngdbf_params, seed: int,
