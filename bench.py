@@ -45,6 +45,10 @@ DECODER_SEED = 1          # Philox key of the perturbation
 # function 5 + decision bit 1 + penalty sum (2 d_v + 2) + threshold, adaptation, window and
 # ballot 4 = 63 + 2 d_v, i.e. 75 for d_v = 6 (breakdown in the design doc).
 OPS_PER_SYMBOL_ITER = 75
+# DRAM bytes (read + write) per decoded frame of the decode kernel, from the ncu capture in
+# profiles/ngdbf_persistent_kernel_peg6x32_n2048_smngdbf.md (2*10^4 frames per Eb/N0 point,
+# samples 164 MB per launch; traffic scales with frames).  Set to None when the kernel changes.
+DRAM_BYTES_PER_FRAME = 10_460
 
 
 def env_rank():
@@ -247,11 +251,14 @@ def run_ours(args):
     sm_count = launch.get("sm_count") or 152
     peak_ops = sm_count * 128 * peak_mhz * 1e6      # 4 schedulers x 32 lanes issue per SM-clock
     achieved = ops_per_launch / mean_launch_s
-    traffic = None
+    traffic = DRAM_BYTES_PER_FRAME * F if DRAM_BYTES_PER_FRAME else None
     rl = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12, "unit": "Tlane-op/s",
           "frac": achieved / peak_ops, "traffic": traffic,
           "kernel": "ngdbf_persistent_kernel<ADAPT,SMOOTH,state in smem>",
           "ops_per_symbol_iter": OPS_PER_SYMBOL_ITER,
+          "algorithmic_bytes_per_launch": F * (4 * code.n + nb + 5),
+          "traffic_basis": "ncu dram__bytes_read.sum + dram__bytes_write.sum per frame on a 2*10^4-frame "
+                           "capture, scaled to the launch's frames",
           "symbol_iters_per_launch": float(np.mean(sym_iters)), "mean_launch_ms": mean_launch_s * 1e3,
           "peak_basis": f"{sm_count} SMs x 128 lanes x {peak_mhz:.0f} MHz (max SM clock)"}
 

@@ -51,6 +51,7 @@ struct DecodeArgs {
     const uint16_t* chk_cols;   // [dc_max][m]   N(i) column-major, padded with n
     const uint16_t* sym_chks;   // [n][dv_max]   M(k) row-major, padded with m
     const uint8_t* sym_deg;     // [n]           d_v(k)
+    int32_t tables_smem;        // copy the tables into shared memory
     // batch
     const float* y;             // [n_frames][n]
     int64_t n_frames;
@@ -71,11 +72,14 @@ struct DecodeArgs {
 };
 
 struct SmemLayout {
-    int32_t off_frame, off_start, off_ctl, off_xw, off_sw, off_thr, off_st, off_chk, off_sym, total;
+    int32_t off_frame, off_start, off_ctl, off_xw, off_sw, off_cnt, off_thr, off_st, off_chk, off_sym, total;
 };
 
 // Offsets in bytes of the shared-memory arrays.  ctl holds: [0..1] unsatisfied
 // masks (double-buffered by pass parity), [2] live mask, [3] new-slot mask.
+// cnt holds per symbol the bit-sliced count of unsatisfied checks (one word per
+// count bit, bit f for slot f) and d_v(k): 3 slices + degree in 16 bytes when
+// d_v <= 7 (narrow), 7 slices + degree in 32 bytes otherwise (wide).
 __host__ __device__ inline SmemLayout smem_layout(int n, int m, int t_max, int dv_max, int dc_max,
                                                   bool need_thr, bool st_smem, bool tables_smem) {
     SmemLayout L;
@@ -86,9 +90,11 @@ __host__ __device__ inline SmemLayout smem_layout(int n, int m, int t_max, int d
         o += bytes;
         return r;
     };
+    const int cnt_bytes = dv_max <= 7 ? 16 : 32;
     L.off_frame = take(kSlots * 8, 16);
     L.off_start = take(kSlots * 4, 16);
     L.off_ctl = take(8 * 4, 16);
+    L.off_cnt = take(n * cnt_bytes, 16);
     L.off_xw = take((n + 1) * 4, 16);
     L.off_sw = take((m + 1) * 4, 16);
     L.off_thr = need_thr ? take((t_max + 1) * 4, 16) : -1;
@@ -105,15 +111,16 @@ __device__ __forceinline__ int nth_set_bit(uint32_t mask, int j) {
     return __ffs(mask) - 1;
 }
 
-template <bool ADAPT, bool SMOOTH, bool ST_SMEM, bool TABLES_SMEM>
+template <bool ADAPT, bool SMOOTH, bool ST_SMEM, bool WIDE>
 __global__ void __launch_bounds__(1024) ngdbf_persistent_kernel(const __grid_constant__ DecodeArgs A) {
     constexpr bool kState = ADAPT || SMOOTH;
     extern __shared__ __align__(16) unsigned char smem[];
-    const int n = A.n, m = A.m, T = A.t_max;
-    const SmemLayout L = smem_layout(n, m, T, A.dv_max, A.dc_max, ADAPT, ST_SMEM && kState, TABLES_SMEM);
+    const int n = A.n, m = A.m, T = A.t_max, dv_max = A.dv_max, dc_max = A.dc_max;
+    const SmemLayout L = smem_layout(n, m, T, dv_max, dc_max, ADAPT, ST_SMEM && kState, A.tables_smem != 0);
     long long* lane_frame = reinterpret_cast<long long*>(smem + L.off_frame);
     int32_t* lane_start = reinterpret_cast<int32_t*>(smem + L.off_start);
     uint32_t* ctl = reinterpret_cast<uint32_t*>(smem + L.off_ctl);
+    uint4* cnt = reinterpret_cast<uint4*>(smem + L.off_cnt);
     uint32_t* xw = reinterpret_cast<uint32_t*>(smem + L.off_xw);
     uint32_t* sw = reinterpret_cast<uint32_t*>(smem + L.off_sw);
     float* thr = ADAPT ? reinterpret_cast<float*>(smem + L.off_thr) : nullptr;
@@ -122,22 +129,24 @@ __global__ void __launch_bounds__(1024) ngdbf_persistent_kernel(const __grid_con
         st = ST_SMEM ? reinterpret_cast<uint16_t*>(smem + L.off_st)
                      : A.st_global + (size_t)blockIdx.x * n * kSlots;
     }
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+    // adjacency tables: only phases A and A' read them, so a generic pointer to
+    // shared or global memory serves both placements
     const uint16_t* chk_cols = A.chk_cols;
     const uint16_t* sym_chks = A.sym_chks;
     const uint8_t* sym_deg = A.sym_deg;
-    if constexpr (TABLES_SMEM) {
+    if (A.tables_smem) {
         uint16_t* c = reinterpret_cast<uint16_t*>(smem + L.off_chk);
         uint16_t* s = reinterpret_cast<uint16_t*>(smem + L.off_sym);
-        uint8_t* d = reinterpret_cast<uint8_t*>(s + n * A.dv_max);
-        for (int i = threadIdx.x; i < A.dc_max * m; i += blockDim.x) c[i] = A.chk_cols[i];
-        for (int i = threadIdx.x; i < n * A.dv_max; i += blockDim.x) s[i] = A.sym_chks[i];
-        for (int i = threadIdx.x; i < n; i += blockDim.x) d[i] = A.sym_deg[i];
+        uint8_t* d = reinterpret_cast<uint8_t*>(s + n * dv_max);
+        for (int i = tid; i < dc_max * m; i += blockDim.x) c[i] = A.chk_cols[i];
+        for (int i = tid; i < n * dv_max; i += blockDim.x) s[i] = A.sym_chks[i];
+        for (int i = tid; i < n; i += blockDim.x) d[i] = A.sym_deg[i];
         chk_cols = c;
         sym_chks = s;
         sym_deg = d;
     }
     float* ys = A.yslots + (size_t)blockIdx.x * n * kSlots;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
 
     // ---- set-up: zero the state, sentinels, thresholds, first 32 frames ----
     for (int k = tid; k <= n; k += blockDim.x) xw[k] = 0u;
@@ -183,9 +192,9 @@ __global__ void __launch_bounds__(1024) ngdbf_persistent_kernel(const __grid_con
                         if (v > A.y_max) v = A.y_max;
                         if (v < -A.y_max) v = -A.y_max;
                     }
-                    ys[(size_t)k * kSlots + f] = v;
+                    ys[k * kSlots + f] = v;
                     if (!(v >= 0.0f)) word |= 1u << f;
-                    if constexpr (kState) st[(size_t)k * kSlots + f] = 0;
+                    if constexpr (kState) st[k * kSlots + f] = 0;
                 }
                 xw[k] = word;
             }
@@ -193,18 +202,20 @@ __global__ void __launch_bounds__(1024) ngdbf_persistent_kernel(const __grid_con
             refill = false;
         }
 
-        // ---- A. syndromes and the all-satisfied vote ----
+        // ---- A. syndromes (four threads XOR a quarter of a check each) and the vote ----
         {
             uint32_t* unsat = ctl + (pass_id & 1);
             if (tid == 0) ctl[(pass_id + 1) & 1] = 0u;
             uint32_t acc = 0;
-            for (int base = 0; base < m; base += blockDim.x) {
-                const int i = base + tid;
+            const int per_pass = blockDim.x >> 2, sub = tid & 3;
+            for (int base = 0; base < m; base += per_pass) {
+                const int i = base + (tid >> 2);
                 uint32_t s = 0;
-                if (i < m) {
-                    for (int j = 0; j < A.dc_max; ++j) s ^= xw[chk_cols[(size_t)j * m + i]];
-                    sw[i] = s;
-                }
+                if (i < m)
+                    for (int j = sub; j < dc_max; j += 4) s ^= xw[chk_cols[j * m + i]];
+                s ^= __shfl_xor_sync(0xFFFFFFFFu, s, 1);
+                s ^= __shfl_xor_sync(0xFFFFFFFFu, s, 2);
+                if (i < m && sub == 0) sw[i] = s;
                 acc |= s;
             }
             acc = __reduce_or_sync(0xFFFFFFFFu, acc);
@@ -238,7 +249,7 @@ __global__ void __launch_bounds__(1024) ngdbf_persistent_kernel(const __grid_con
                             if (!ok) {
                                 // X_k = terms - 2 * (#-1 decisions), x(T) included here
                                 const int terms = tf - A.t_smooth + 1;
-                                const int neg = (int)(st[(size_t)k * kSlots + f] >> kCShift) + (int)bit;
+                                const int neg = (int)(st[k * kSlots + f] >> kCShift) + (int)bit;
                                 const int X = terms - 2 * neg;
                                 bit = X < 0 ? 1u : (X > 0 ? 0u : bit);
                             }
@@ -283,6 +294,37 @@ __global__ void __launch_bounds__(1024) ngdbf_persistent_kernel(const __grid_con
         }
         if (live == 0) break;
 
+        // ---- A'. per symbol, the bit-sliced count of unsatisfied checks in M(k) ----
+        for (int k = tid; k < n; k += blockDim.x) {
+            const uint16_t* row = sym_chks + k * dv_max;
+            if constexpr (!WIDE) {
+                uint32_t b0 = 0, b1 = 0, b2 = 0;           // count <= 7: three slices
+                for (int e = 0; e < dv_max; ++e) {
+                    const uint32_t s = sw[row[e]];
+                    const uint32_t c0 = b0 & s;
+                    b0 ^= s;
+                    const uint32_t c1 = b1 & c0;
+                    b1 ^= c0;
+                    b2 ^= c1;
+                }
+                cnt[k] = make_uint4(b0, b1, b2, (uint32_t)sym_deg[k]);
+            } else {
+                uint32_t b[7] = {0, 0, 0, 0, 0, 0, 0};     // count <= 127: seven slices
+                for (int e = 0; e < dv_max; ++e) {
+                    uint32_t carry = sw[row[e]];
+#pragma unroll
+                    for (int q = 0; q < 7; ++q) {
+                        const uint32_t c = b[q] & carry;
+                        b[q] ^= carry;
+                        carry = c;
+                    }
+                }
+                cnt[2 * k] = make_uint4(b[0], b[1], b[2], b[3]);
+                cnt[2 * k + 1] = make_uint4(b[4], b[5], b[6], (uint32_t)sym_deg[k]);
+            }
+        }
+        __syncthreads();
+
         // ---- C. Step 2 and Step 3b for every symbol of every live slot ----
         {
             const bool act = (live >> lane) & 1u;
@@ -293,31 +335,50 @@ __global__ void __launch_bounds__(1024) ngdbf_persistent_kernel(const __grid_con
             const bool window = SMOOTH && act && t >= A.t_smooth;
             const int groups = (n + 3) >> 2;
             for (int g = warp; g < groups; g += nwarps) {
+                const int k0 = 4 * g;
+                // issue the sample and state loads before the generator's arithmetic
+                float yv[4];
+                uint32_t sv[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const bool in = k0 + j < n;
+                    yv[j] = in ? ys[(k0 + j) * kSlots + lane] : 0.0f;
+                    if constexpr (kState) sv[j] = in ? (uint32_t)st[(k0 + j) * kSlots + lane] : 0u;
+                }
                 float z[4];
                 gauss4((uint32_t)g, (uint32_t)t, flo, fhi, A.G, z);
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
-                    const int k = 4 * g + j;
+                    const int k = k0 + j;
                     if (k >= n) break;
+                    int unsat_cnt, deg;
+                    if constexpr (!WIDE) {
+                        const uint4 c = cnt[k];
+                        unsat_cnt = (int)(((c.x >> lane) & 1u) | (((c.y >> lane) & 1u) << 1) |
+                                          (((c.z >> lane) & 1u) << 2));
+                        deg = (int)c.w;
+                    } else {
+                        const uint4 c = cnt[2 * k], d = cnt[2 * k + 1];
+                        unsat_cnt = (int)(((c.x >> lane) & 1u) | (((c.y >> lane) & 1u) << 1) |
+                                          (((c.z >> lane) & 1u) << 2) | (((c.w >> lane) & 1u) << 3) |
+                                          (((d.x >> lane) & 1u) << 4) | (((d.y >> lane) & 1u) << 5) |
+                                          (((d.z >> lane) & 1u) << 6));
+                        deg = (int)d.w;
+                    }
+                    const int S = deg - 2 * unsat_cnt;
                     const uint32_t xword = xw[k];
                     const bool xneg = (xword >> lane) & 1u;
-                    int unsat_cnt = 0;
-                    for (int e = 0; e < A.dv_max; ++e)
-                        unsat_cnt += (sw[sym_chks[(size_t)k * A.dv_max + e]] >> lane) & 1u;
-                    const int S = (int)sym_deg[k] - 2 * unsat_cnt;
-                    const float yv = ys[(size_t)k * kSlots + lane];
                     const float q = __fmul_rn(A.scale, z[j]);
-                    const float E = inversion_metric(xneg, yv, S, A.w, q);
+                    const float E = inversion_metric(xneg, yv[j], S, A.w, q);
                     bool flip;
                     if constexpr (kState) {
-                        uint32_t sv = st[(size_t)k * kSlots + lane];
-                        const uint32_t u = min(sv & kUMask, (uint32_t)T);
-                        const float th = ADAPT ? thr[u] : A.theta;
+                        const uint32_t s0 = sv[j];
+                        // u_k <= t - 1 < T for a live slot (cleared on every refill)
+                        const float th = ADAPT ? thr[s0 & kUMask] : A.theta;
                         flip = act && (E < th);
-                        uint32_t nv = sv;
-                        if (ADAPT && act && !flip) nv += 1u;
-                        if (window && xneg) nv += 1u << kCShift;
-                        if (nv != sv) st[(size_t)k * kSlots + lane] = (uint16_t)nv;
+                        const uint32_t nv = s0 + ((ADAPT && act && !flip) ? 1u : 0u) +
+                                            ((window && xneg) ? (1u << kCShift) : 0u);
+                        if (nv != s0) st[k * kSlots + lane] = (uint16_t)nv;
                     } else {
                         flip = act && (E < A.theta);
                     }
@@ -418,17 +479,17 @@ struct LaunchPlan {
 using KernelFn = void (*)(DecodeArgs);
 
 template <bool AD, bool SM>
-KernelFn pick4(bool st_smem, bool tables_smem) {
-    if (st_smem) return tables_smem ? ngdbf_persistent_kernel<AD, SM, true, true> : ngdbf_persistent_kernel<AD, SM, true, false>;
-    return tables_smem ? ngdbf_persistent_kernel<AD, SM, false, true> : ngdbf_persistent_kernel<AD, SM, false, false>;
+KernelFn pick_width(bool st_smem, bool wide) {
+    if (st_smem) return wide ? ngdbf_persistent_kernel<AD, SM, true, true> : ngdbf_persistent_kernel<AD, SM, true, false>;
+    return wide ? ngdbf_persistent_kernel<AD, SM, false, true> : ngdbf_persistent_kernel<AD, SM, false, false>;
 }
 
-KernelFn pick_kernel(int variant, bool st_smem, bool tables_smem) {
+KernelFn pick_kernel(int variant, bool st_smem, bool wide) {
     switch (variant & 3) {
-        case 0: return pick4<false, false>(st_smem, tables_smem);
-        case 1: return pick4<true, false>(st_smem, tables_smem);
-        case 2: return pick4<false, true>(st_smem, tables_smem);
-        default: return pick4<true, true>(st_smem, tables_smem);
+        case 0: return pick_width<false, false>(st_smem, wide);
+        case 1: return pick_width<true, false>(st_smem, wide);
+        case 2: return pick_width<false, true>(st_smem, wide);
+        default: return pick_width<true, true>(st_smem, wide);
     }
 }
 
@@ -460,7 +521,7 @@ ngdbf_status plan_launch(const ngdbf_code* C, const ngdbf_params* P, int64_t n_f
     }
     if (L.total > smem_optin)
         return fail(NGDBF_ERR_UNSUPPORTED, "code too large for the shared-memory decision words");
-    KernelFn fn = pick_kernel(P->variant, st_smem, tables_smem);
+    KernelFn fn = pick_kernel(P->variant, st_smem, C->dv_max > 7);
     e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, L.total);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
     // Most resident warps per SM; ties go to more CTAs (more slots in flight).
@@ -488,6 +549,36 @@ ngdbf_status plan_launch(const ngdbf_code* C, const ngdbf_params* P, int64_t n_f
     *sm_count_out = sm_count;
     (void)smem_per_sm;
     return NGDBF_OK;
+}
+
+// Kernel arguments of one decode: scratch at `base` (work counter, then the
+// per-slot samples), per-slot state at `st_base` when it lives in global memory.
+void fill_args(const ngdbf_code* C, const ngdbf_params* P, const LaunchPlan& plan, const float* y,
+               int64_t n_frames, float sigma, uint64_t seed, uint64_t frame_offset, uint8_t* bits,
+               int32_t* iters, uint8_t* pass, unsigned char* base, unsigned char* st_base,
+               bool st_global, DecodeArgs* out) {
+    DecodeArgs& A = *out;
+    std::memset(&A, 0, sizeof(A));
+    A.n = C->n; A.m = C->m; A.dv_max = C->dv_max; A.dc_max = C->dc_max;
+    A.chk_cols = C->d_chk_cols; A.sym_chks = C->d_sym_chks; A.sym_deg = C->d_sym_deg;
+    A.tables_smem = plan.tables_smem ? 1 : 0;
+    A.y = y; A.n_frames = n_frames; A.frame_offset = frame_offset;
+    A.bits = bits; A.iters = iters; A.pass = pass; A.nb = (C->n + 7) / 8;
+    A.w = P->w; A.theta = P->theta;
+    A.scale = (float)((double)P->eta * (double)sigma);
+    A.clamp = (P->y_max > 0.0f && std::isfinite(P->y_max)) ? 1 : 0;
+    A.y_max = A.clamp ? P->y_max : 0.0f;
+    A.t_max = P->t_max;
+    A.t_smooth = std::max(0, P->t_max - P->smooth_window);
+    A.queue = reinterpret_cast<unsigned long long*>(base);
+    A.yslots = reinterpret_cast<float*>(base + 256);
+    A.st_global = st_global ? reinterpret_cast<uint16_t*>(st_base) : nullptr;
+    host_gen_consts(seed, A.G);
+    double p = 1.0;
+    for (int u = 0; u <= P->t_max; ++u) {
+        A.thr[u] = (float)((double)P->theta * p);
+        p = p * (double)P->lambda;
+    }
 }
 
 ngdbf_status check_params(const ngdbf_params* P, float sigma) {
@@ -554,26 +645,8 @@ ngdbf_status decode_impl(const ngdbf_code* C, const float* y, int64_t n_frames, 
     unsigned char* base = static_cast<unsigned char*>(ws);
 
     DecodeArgs A;
-    std::memset(&A, 0, sizeof(A));
-    A.n = C->n; A.m = C->m; A.dv_max = C->dv_max; A.dc_max = C->dc_max;
-    A.chk_cols = C->d_chk_cols; A.sym_chks = C->d_sym_chks; A.sym_deg = C->d_sym_deg;
-    A.y = y; A.n_frames = n_frames; A.frame_offset = frame_offset;
-    A.bits = bits; A.iters = iters; A.pass = pass; A.nb = (C->n + 7) / 8;
-    A.w = P->w; A.theta = P->theta;
-    A.scale = (float)((double)P->eta * (double)sigma);
-    A.clamp = (P->y_max > 0.0f && std::isfinite(P->y_max)) ? 1 : 0;
-    A.y_max = A.clamp ? P->y_max : 0.0f;
-    A.t_max = P->t_max;
-    A.t_smooth = std::max(0, P->t_max - P->smooth_window);
-    A.queue = reinterpret_cast<unsigned long long*>(base);
-    A.yslots = reinterpret_cast<float*>(base + 256);
-    A.st_global = bytes_st ? reinterpret_cast<uint16_t*>(base + 256 + bytes_y) : nullptr;
-    host_gen_consts(seed, A.G);
-    double p = 1.0;
-    for (int u = 0; u <= P->t_max; ++u) {
-        A.thr[u] = (float)((double)P->theta * p);
-        p = p * (double)P->lambda;
-    }
+    fill_args(C, P, plan, y, n_frames, sigma, seed, frame_offset, bits, iters, pass, base,
+              base + 256 + bytes_y, bytes_st != 0, &A);
 
     e = cudaMemsetAsync(A.queue, 0, sizeof(unsigned long long), stream);
     if (e == cudaSuccess) {
@@ -840,26 +913,8 @@ extern "C" ngdbf_status ngdbf_decode_noalloc(const ngdbf_code_t* C, const float*
     const size_t bytes_y = ((size_t)grid * per_cta_y + 255) / 256 * 256;
 
     DecodeArgs A;
-    std::memset(&A, 0, sizeof(A));
-    A.n = C->n; A.m = C->m; A.dv_max = C->dv_max; A.dc_max = C->dc_max;
-    A.chk_cols = C->d_chk_cols; A.sym_chks = C->d_sym_chks; A.sym_deg = C->d_sym_deg;
-    A.y = y; A.n_frames = n_frames; A.frame_offset = frame_offset;
-    A.bits = bits; A.iters = iters; A.pass = pass; A.nb = (C->n + 7) / 8;
-    A.w = P->w; A.theta = P->theta;
-    A.scale = (float)((double)P->eta * (double)sigma);
-    A.clamp = (P->y_max > 0.0f && std::isfinite(P->y_max)) ? 1 : 0;
-    A.y_max = A.clamp ? P->y_max : 0.0f;
-    A.t_max = P->t_max;
-    A.t_smooth = std::max(0, P->t_max - P->smooth_window);
-    A.queue = reinterpret_cast<unsigned long long*>(base);
-    A.yslots = reinterpret_cast<float*>(base + 256);
-    A.st_global = per_cta_st ? reinterpret_cast<uint16_t*>(base + 256 + bytes_y) : nullptr;
-    host_gen_consts(seed, A.G);
-    double p = 1.0;
-    for (int u = 0; u <= P->t_max; ++u) {
-        A.thr[u] = (float)((double)P->theta * p);
-        p = p * (double)P->lambda;
-    }
+    fill_args(C, P, plan, y, n_frames, sigma, seed, frame_offset, bits, iters, pass, base,
+              base + 256 + bytes_y, per_cta_st != 0, &A);
     // The work counter must start at zero; the kernel initializes everything else it reads.
     e = cudaMemsetAsync(A.queue, 0, sizeof(unsigned long long), stream);
     if (e != cudaSuccess) return cuda_fail(e, "clearing the static work counter");

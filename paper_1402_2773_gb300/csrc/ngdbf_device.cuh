@@ -64,16 +64,25 @@ __device__ __forceinline__ float ln_series(float u, const GenConsts& G) {
     return __fmaf_rn(__int2float_rn(e), 0x1.62e430p-1f /* fl32(ln 2) */, __fmul_rn(2.0f, r));
 }
 
+// (b + 1/2) 2^-(bits) for an integer b < 2^bits <= 2^23, exactly: the float
+// with exponent 0 and mantissa b is 1 + b 2^-23, and subtracting 1 - 2^-24
+// leaves (2b + 1) 2^-24 without rounding; scaling by 2^(23 - bits) is exact.
+__device__ __forceinline__ float half_offset_fraction(uint32_t b) {
+    return __fadd_rn(__uint_as_float(0x3F800000u | b), -0x1.fffffep-1f);
+}
+
 // sin and cos of 2 pi u, u = (a + 1/2) 2^-23 with a a 23-bit integer.
 // 4u = quadrant + xi exactly, xi in [-1/2, 1/2]; the series are in xi^2.
 __device__ __forceinline__ void sincos_2pi(uint32_t a, const GenConsts& G, float& sn, float& cs) {
     uint32_t quad = (a >> 21) & 3u;
-    int32_t rem = (int32_t)(a & 0x1FFFFFu);
-    if (rem >= (1 << 20)) {
-        rem -= (1 << 21);
+    const uint32_t rem = a & 0x1FFFFFu;
+    // v = (rem + 1/2) 2^-21 in (0, 1); above 1/2 it moves to the next quadrant as v - 1
+    const float v = __fmul_rn(half_offset_fraction(rem), 4.0f);
+    float xi = v;
+    if (rem >= (1u << 20)) {
+        xi = __fadd_rn(v, -1.0f);
         quad = (quad + 1u) & 3u;
     }
-    const float xi = __fmul_rn(__fadd_rn(__int2float_rn(rem), 0.5f), 0x1p-21f);
     const float xx = __fmul_rn(xi, xi);
     float ps = G.sin_c[5];
     ps = __fmaf_rn(ps, xx, G.sin_c[4]);
@@ -103,7 +112,7 @@ __device__ __forceinline__ void gauss4(uint32_t g, uint32_t t, uint32_t flo, uin
     philox4x32_10(g, t, flo, fhi, G, r);
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-        const float u0 = __fmul_rn(__fadd_rn(__uint2float_rn(r[2 * h] >> 9), 0.5f), 0x1p-23f);
+        const float u0 = half_offset_fraction(r[2 * h] >> 9);      // ((r >> 9) + 1/2) 2^-23
         const float rho = __fsqrt_rn(__fmul_rn(-2.0f, ln_series(u0, G)));
         float sn, cs;
         sincos_2pi(r[2 * h + 1] >> 9, G, sn, cs);

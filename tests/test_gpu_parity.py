@@ -129,7 +129,7 @@ def test_global_state_path(O):
 
 def test_tables_in_global_memory(O):
     """State fits shared memory only once the adjacency tables are moved out."""
-    code = wl.peg_code(3200, 1600, 3, seed=2)
+    code = wl.peg_code(2600, 1300, 3, seed=2)
     y, _, sig = wl.frames(code, 40, 2.5, seed=1)
     assert_parity(O, code, y, sig, seed=4, lam=0.98, t_max=60, variant=1)
     assert ngdbf.ngdbf_last_launch()["state_in_smem"] == 1
