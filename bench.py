@@ -61,6 +61,17 @@ def shard(rank: int, world: int, frames_per_gpu: int):
     return rank * frames_per_gpu, frames_per_gpu
 
 
+def max_over_ranks(value: float, device) -> float:
+    """Largest value over all ranks (timing only; frames never cross ranks)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return value
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def make_inputs(code, frames, rank, world, pinned=False):
     import torch
     off, F = shard(rank, world, frames)
@@ -233,10 +244,7 @@ def run_ours(args):
         dist.barrier()
     elapsed = t_start.elapsed_time(t_end) / 1e3
     kernel_ms = [evs[s][j][0].elapsed_time(evs[s][j][1]) for s in range(args.steps) for j in range(len(EBN0_DB))]
-    if world > 1:
-        t = torch.tensor([elapsed], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed = float(t.item())
+    elapsed = max_over_ranks(elapsed, "cuda")
     frames_total = F * len(EBN0_DB) * args.steps * world
     fps = frames_total / elapsed
 
@@ -282,10 +290,7 @@ def run_ours(args):
             dc.decode_host(ys_host[j], sigmas[j], gp, seed=DECODER_SEED + j, frame_offset=off,
                            out=(bits_p[j], it_p[j], ps_p[j]))
     e2e_s = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(e2e_s, "cuda")
     e2e_ok = all(np.array_equal(bits_p[j].numpy(), host_outs[j][0]) for j in range(len(EBN0_DB)))
     e2e = {"value": F * len(EBN0_DB) * e2e_steps * world / e2e_s, "unit": "frames/s",
            "h2d_bytes_per_step": F * code.n * 4 * len(EBN0_DB),
