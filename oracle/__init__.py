@@ -26,6 +26,9 @@ CFLAGS = ["-O2", "-fPIC", "-shared", "-std=c11", "-ffp-contract=off", "-fno-fast
 
 ADAPT = 1
 SMOOTH = 2
+FP32 = 0
+FP16 = 1
+FIX = 2
 
 
 class Params(ctypes.Structure):
@@ -43,7 +46,7 @@ def make_params(w=0.75, theta=-0.9, eta=0.96, lam=1.0, y_max=2.5, t_max=100, smo
 
 def compile_lib(src: str = SRC, out: str = LIB_PATH, extra: list[str] | None = None) -> str:
     """Compiles an oracle source file into a shared library (gcc)."""
-    tmp = out + ".tmp"
+    tmp = f"{out}.{os.getpid()}.tmp"
     subprocess.check_call(["gcc", *CFLAGS, *(extra or []), "-o", tmp, src, "-lm", "-lpthread"])
     os.replace(tmp, out)
     return out
@@ -83,11 +86,20 @@ class Oracle:
         lib.oracle_metric_f32.argtypes = [ctypes.c_int, ctypes.c_float, ctypes.c_int, ctypes.c_float,
                                           ctypes.c_float]
         lib.oracle_metric_f32.restype = ctypes.c_float
+        lib.oracle_metric_f16.argtypes = [ctypes.c_int, ctypes.c_float, ctypes.c_int, ctypes.c_float,
+                                          ctypes.c_float]
+        lib.oracle_metric_f16.restype = ctypes.c_float
         lib.oracle_metric_f64.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_double,
                                           ctypes.c_double]
         lib.oracle_metric_f64.restype = ctypes.c_double
         lib.oracle_quantize.argtypes = [ctypes.c_double, ctypes.c_int32, ctypes.c_double]
         lib.oracle_quantize.restype = ctypes.c_double
+        lib.oracle_round_half.argtypes = [ctypes.c_float]
+        lib.oracle_round_half.restype = ctypes.c_float
+        lib.oracle_fix_scale.argtypes = [ctypes.c_int32, ctypes.c_float]
+        lib.oracle_fix_scale.restype = ctypes.c_float
+        lib.oracle_fix_code.argtypes = [ctypes.c_float, ctypes.c_float, ctypes.c_int32]
+        lib.oracle_fix_code.restype = ctypes.c_int32
         lib.oracle_threshold_events.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_int32,
                                                 ctypes.c_int32, ctypes.c_double, f64p, i32p,
                                                 ctypes.c_int32]
@@ -141,11 +153,23 @@ class Oracle:
     def metric_f32(self, x: int, ys: float, S: int, w: float, q: float) -> np.float32:
         return np.float32(self.lib.oracle_metric_f32(x, ys, S, w, q))
 
+    def metric_f16(self, x: int, ys16: float, S: int, w16: float, q: float) -> float:
+        return float(np.float32(self.lib.oracle_metric_f16(x, ys16, S, w16, q)))
+
     def metric_f64(self, x: int, ys: float, S: int, w: float, q: float) -> float:
         return float(self.lib.oracle_metric_f64(x, ys, S, w, q))
 
     def quantize(self, v: float, q_bits: int, y_max: float) -> float:
         return float(self.lib.oracle_quantize(v, q_bits, y_max))
+
+    def round_half(self, x: float) -> float:
+        return float(np.float32(self.lib.oracle_round_half(ctypes.c_float(x))))
+
+    def fix_scale(self, q_bits: int, y_max: float) -> float:
+        return float(np.float32(self.lib.oracle_fix_scale(q_bits, y_max)))
+
+    def fix_code(self, v: float, R: float, kmax: int) -> int:
+        return int(self.lib.oracle_fix_code(v, R, kmax))
 
     def threshold_events(self, theta, lam, t_max, q_bits, y_max, cap=64):
         thr = np.zeros(cap, dtype=np.float64)

@@ -42,6 +42,19 @@
  * The FP32 form evaluates ln and sin/cos with its own series (below) so that
  * the same definition can be evaluated bit-identically elsewhere; the FP64
  * form uses the C library's log/sin/cos on the same uniforms.
+ *
+ * Reduced-precision forms of the inversion function (Sec. IV-E), on the same
+ * FP32 perturbation q_k:
+ *   FP16:  y, w, q and theta lambda^u rounded to binary16 (nearest-even);
+ *          E = h(h(x y + h(w S)) + q) with h() rounding each FP32 result to
+ *          binary16 (one FP32 operation on binary16 operands, then one
+ *          rounding, is the correctly rounded binary16 operation); S is an
+ *          exact integer.
+ *   FIX:   Eq. 8 with Q bits: level k = min(floor(|v| R), 2^(Q-1) - 1) with
+ *          R = fl32(2^Q / (2 Y_max)) and the product |v| R in FP32; held as the
+ *          signed code b = k (v >= 0) or -k-1 (v < 0), value 2b + 1 in units of
+ *          Delta/2 = Y_max / 2^Q.  E~ = x Y~ + W~ S + Q~ in exact integers,
+ *          compared with Theta~(u) = value of fl32(theta lambda^u).
  */
 #include <math.h>
 #include <pthread.h>
@@ -51,6 +64,9 @@
 
 #define ORC_ADAPT 1
 #define ORC_SMOOTH 2
+#define ORC_FP32 0
+#define ORC_FP16 1
+#define ORC_FIX 2
 
 typedef struct {
     float w, theta, eta, lambda, y_max;
@@ -219,6 +235,17 @@ float oracle_metric_f32(int x, float ys, int S, float w, float q) {
     return e + q;
 }
 
+float oracle_round_half(float x);
+
+/* Step 2 in binary16: E = h(h(x y16 + h(w16 S)) + h(q)), each result rounded to binary16. */
+float oracle_metric_f16(int x, float ys16, int S, float w16, float q) {
+    const float q16 = oracle_round_half(q);
+    const float xy = x > 0 ? ys16 : -ys16;
+    const float ws = oracle_round_half(w16 * (float)S);
+    const float e1 = oracle_round_half(xy + ws);
+    return oracle_round_half(e1 + q16);
+}
+
 double oracle_metric_f64(int x, double ys, int S, double w, double q) {
     return (x > 0 ? ys : -ys) + w * (double)S + q;
 }
@@ -232,6 +259,36 @@ double oracle_quantize(double v, int32_t q_bits, double y_max) {
     const double s = v >= 0.0 ? 1.0 : -1.0;
     return s * (k + 0.5) * (2.0 * y_max / nq);
 }
+
+/* Round a float to the nearest binary16 value (ties to even), returned as a
+ * float: quantum 2^(e-10) for normal binary16 (e >= -14), 2^-24 below;
+ * magnitudes >= 65520 overflow to infinity. */
+float oracle_round_half(float x) {
+    uint32_t b;
+    memcpy(&b, &x, 4);
+    const uint32_t a = b & 0x7FFFFFFFu;
+    if (a >= 0x7F800000u) return x;
+    if (a >= 0x477FF000u) return (b >> 31) ? -INFINITY : INFINITY;
+    const int e = (int)(a >> 23) - 127;
+    const double q = ldexp(1.0, e >= -14 ? e - 10 : -24);
+    const double r = rint(fabs((double)x) / q) * q;     /* exact quotient, ties to even */
+    return (float)((b >> 31) ? -r : r);
+}
+
+/* R = fl32(2^Q / (2 Y_max)) of the fixed-point quantizer. */
+float oracle_fix_scale(int32_t q_bits, float y_max) {
+    return (float)(ldexp(1.0, q_bits) / (2.0 * (double)y_max));
+}
+
+/* Signed level code b of v (value 2b + 1 in units of Delta/2); the level is
+ * decided in FP32 and saturates at kmax = 2^(Q-1) - 1. */
+int32_t oracle_fix_code(float v, float R, int32_t kmax) {
+    const float a = fabsf(v) * R;
+    const int32_t k = (a < (float)kmax) ? (int32_t)floorf(a) : kmax;
+    return v >= 0.0f ? k : -k - 1;
+}
+
+static inline int32_t fix_value(float v, float R, int32_t kmax) { return 2 * oracle_fix_code(v, R, kmax) + 1; }
 
 /* Adaptation events (theta~, tau~) of Sec. V-A: tau where g(theta lambda^u)
  * changes, for u = 0..t_max (Table II).  Returns the event count. */
@@ -298,6 +355,12 @@ typedef struct {
     const double* thr64;
     uint64_t seed;
     const float* q_in;        /* optional [t_max][n] perturbations for one frame */
+    int precision;            /* ORC_FP32, ORC_FP16 or ORC_FIX */
+    float w16;                /* binary16 syndrome weight */
+    const float* thr16;       /* [t_max + 1] binary16 thresholds */
+    float fix_R;              /* fixed-point scale and limits */
+    int32_t fix_kmax, fix_W;
+    const int32_t* thr_fix;   /* [t_max + 1] Theta~(u) */
 } orc_ctx;
 
 /* Decodes one frame.  ws must hold 4n + m + 16 int32 words. */
@@ -314,15 +377,21 @@ static void decode_frame(const orc_ctx* X, const float* y, uint64_t frame_id,
     int32_t* Xs = u + n;                           /* n */
     float* ys32 = (float*)(Xs + n);                /* n */
     double* ys64 = (double*)malloc(sizeof(double) * (size_t)n);
+    int32_t* yfix = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
     const int clamp = P->y_max > 0.0f && isfinite(P->y_max);
 
     /* Step 0 and x(0) = sign(y) on saturated samples (Sec. III-A, IV-A). */
     for (int32_t k = 0; k < n; ++k) {
         float v = y[k];
         if (clamp) { if (v > P->y_max) v = P->y_max; if (v < -P->y_max) v = -P->y_max; }
+        if (X->precision == ORC_FP16) v = oracle_round_half(v);
         ys32[k] = v;
         ys64[k] = (double)v;
         x[k] = v >= 0.0f ? 1 : -1;
+        if (X->precision == ORC_FIX) {
+            yfix[k] = fix_value(v, X->fix_R, X->fix_kmax);
+            x[k] = yfix[k] > 0 ? 1 : -1;
+        }
         u[k] = 0;
         Xs[k] = 0;
     }
@@ -344,6 +413,7 @@ static void decode_frame(const orc_ctx* X, const float* y, uint64_t frame_id,
             *iters = t;
             *pass = 1;
             free(ys64);
+            free(yfix);
             return;
         }
         /* Eq. 7: the up/down counter sums x(t) over the smoothing window. */
@@ -368,8 +438,17 @@ static void decode_frame(const orc_ctx* X, const float* y, uint64_t frame_id,
                     if ((k & 3) == 0) oracle_gauss4_f32(X->seed, frame_id, (uint32_t)t, (uint32_t)(k >> 2), z32);
                     q = X->scale32 * z32[k & 3];
                 }
-                float E = oracle_metric_f32(x[k], ys32[k], S, P->w, q);
-                flip = E < X->thr32[u[k]];
+                if (X->precision == ORC_FP16) {
+                    const float E = oracle_metric_f16(x[k], ys32[k], S, X->w16, q);
+                    flip = E < X->thr16[u[k]];
+                } else if (X->precision == ORC_FIX) {
+                    /* Eq. 9 in units of Delta/2: exact integers */
+                    const int32_t Eq = x[k] * yfix[k] + X->fix_W * S + fix_value(q, X->fix_R, X->fix_kmax);
+                    flip = Eq < X->thr_fix[u[k]];
+                } else {
+                    float E = oracle_metric_f32(x[k], ys32[k], S, P->w, q);
+                    flip = E < X->thr32[u[k]];
+                }
             }
             if (flip) x[k] = (int8_t)-x[k];
             else if (adapt) u[k] += 1;
@@ -382,6 +461,7 @@ static void decode_frame(const orc_ctx* X, const float* y, uint64_t frame_id,
     *iters = T;
     *pass = 0;
     free(ys64);
+    free(yfix);
 }
 
 typedef struct {
@@ -416,6 +496,9 @@ static int check_args(int32_t n, int32_t m, const int32_t* row_ptr, const int32_
     for (int32_t i = 0; i < m; ++i) if (row_ptr[i + 1] < row_ptr[i]) return -1;
     for (int32_t e = 0; e < row_ptr[m]; ++e) if (col_idx[e] < 0 || col_idx[e] >= n) return -1;
     if (P->t_max < 0 || P->smooth_window < 0) return -1;
+    if (P->precision < ORC_FP32 || P->precision > ORC_FIX) return -1;
+    if (P->precision == ORC_FIX && (P->q_bits < 2 || P->q_bits > 8 || !(P->y_max > 0.0f) || !isfinite(P->y_max)))
+        return -1;
     return 0;
 }
 
@@ -431,7 +514,23 @@ static int run(int use_f64, int32_t n, int32_t m, const int32_t* row_ptr, const 
     double* thr64 = (double*)malloc(sizeof(double) * (size_t)(P->t_max + 1));
     oracle_threshold_table_f32(P->theta, P->lambda, P->t_max, thr32);
     for (int32_t u = 0; u <= P->t_max; ++u) thr64[u] = (double)P->theta * pow((double)P->lambda, (double)u);
+    float* thr16 = (float*)malloc(sizeof(float) * (size_t)(P->t_max + 1));
+    int32_t* thr_fix = (int32_t*)malloc(sizeof(int32_t) * (size_t)(P->t_max + 1));
     orc_ctx X;
+    X.precision = use_f64 ? ORC_FP32 : P->precision;
+    X.w16 = oracle_round_half(P->w);
+    X.fix_R = 0.0f; X.fix_kmax = 0; X.fix_W = 0;
+    if (X.precision == ORC_FIX) {
+        X.fix_R = oracle_fix_scale(P->q_bits, P->y_max);
+        X.fix_kmax = (1 << (P->q_bits - 1)) - 1;
+        X.fix_W = fix_value(P->w, X.fix_R, X.fix_kmax);
+    }
+    for (int32_t u = 0; u <= P->t_max; ++u) {
+        thr16[u] = oracle_round_half(thr32[u]);
+        thr_fix[u] = X.precision == ORC_FIX ? fix_value(thr32[u], X.fix_R, X.fix_kmax) : 0;
+    }
+    X.thr16 = thr16;
+    X.thr_fix = thr_fix;
     X.C = &C; X.P = P; X.use_f64 = use_f64;
     X.scale32 = noise_scale_f32(P->eta, sigma);
     X.scale64 = (double)P->eta * (double)sigma;
@@ -451,7 +550,7 @@ static int run(int use_f64, int32_t n, int32_t m, const int32_t* row_ptr, const 
     decode_worker(&jobs[0]);
     int status = jobs[0].status;
     for (int32_t i = 1; i < n_threads; ++i) { pthread_join(th[i], NULL); status |= jobs[i].status; }
-    free(thr32); free(thr64);
+    free(thr32); free(thr64); free(thr16); free(thr_fix);
     code_free(&C);
     return status;
 }

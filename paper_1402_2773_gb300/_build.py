@@ -39,7 +39,7 @@ def stale(target: str, deps: list[str]) -> bool:
 def build_cuda(force: bool = False, verbose: bool = False) -> str:
     """Compiles libngdbf.so next to this file; returns its path."""
     if force or stale(LIB_PATH, DEPS):
-        tmp = LIB_PATH + ".tmp"
+        tmp = f"{LIB_PATH}.{os.getpid()}.tmp"
         cmd = [nvcc(), *NVCC_FLAGS, *(["-Xptxas", "-v"] if verbose else []), "-o", tmp, *SOURCES]
         subprocess.check_call(cmd)
         os.replace(tmp, LIB_PATH)

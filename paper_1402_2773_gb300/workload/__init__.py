@@ -34,7 +34,7 @@ _lib = None
 def build(force: bool = False) -> str:
     """Compiles the workload helper library with gcc (host code only)."""
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
-        tmp = _LIB_PATH + ".tmp"
+        tmp = f"{_LIB_PATH}.{os.getpid()}.tmp"
         subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-std=c11", "-D_GNU_SOURCE",
                                "-o", tmp, _SRC, "-lm", "-lpthread"])
         os.replace(tmp, _LIB_PATH)

@@ -424,10 +424,167 @@ def pin_f32_f64_statistics(O):
     assert abs(ps32.mean() - ps64.mean()) < 0.05
 
 
+# ---------------------------------------------------------------------------
+# reduced-precision forms (Sec. IV-E)
+# ---------------------------------------------------------------------------
+
+def pin_round_half(O):
+    """binary16 rounding (ties to even) equals numpy's float16 conversion, subnormals and overflow included."""
+    rng = np.random.default_rng(3)
+    vals = np.concatenate([
+        rng.standard_normal(3000).astype(np.float32) * np.float32(3.0),
+        (rng.standard_normal(1000) * 1e-5).astype(np.float32),           # binary16 subnormals
+        (rng.standard_normal(500) * 3e4).astype(np.float32),              # near overflow
+        np.array([65504.0, 65519.99, 65520.0, -65520.0, 2.0 ** -24, 2.0 ** -25, 3 * 2.0 ** -26,
+                  1.0 + 2.0 ** -11, 1.0 + 3 * 2.0 ** -11, -0.0, 0.0], dtype=np.float32)])
+    # exact ties between neighbouring binary16 values
+    h = rng.standard_normal(500).astype(np.float16)
+    nxt = np.nextafter(h, np.float16(np.inf))
+    ties = ((h.astype(np.float64) + nxt.astype(np.float64)) / 2).astype(np.float32)
+    vals = np.concatenate([vals, ties])
+    for v in vals:
+        got = O.round_half(float(v))
+        with np.errstate(over="ignore"):
+            want = float(np.float32(v).astype(np.float16))
+        assert (got == want) or (np.isnan(got) and np.isnan(want)), f"round_half({v!r}) = {got}, numpy {want}"
+        assert np.signbit(got) == np.signbit(want)
+
+
+def pin_metric_f16(O):
+    """The binary16 inversion function equals numpy's float16 arithmetic on the same operands."""
+    rng = np.random.default_rng(6)
+    for _ in range(3000):
+        y16 = np.float16(rng.normal() * 1.5)
+        w16 = np.float16(rng.uniform(0.05, 1.5))
+        S = int(rng.integers(-7, 8))
+        x = int(rng.choice([-1, 1]))
+        q = np.float32(rng.normal() * 0.7)
+        xy = y16 if x > 0 else -y16
+        want = np.float16(np.float16(xy + np.float16(w16 * np.float16(S))) + np.float16(q))
+        got = O.metric_f16(x, float(y16), S, float(w16), float(q))
+        assert got == float(want), (x, y16, S, w16, q, got, want)
+
+
+def pin_fix_quantizer(O):
+    """The FP32-decided level code agrees with Eq. 8 (g in double) away from level boundaries;
+    saturation, the missing zero level and the sign convention hold."""
+    rng = np.random.default_rng(4)
+    for q_bits, y_max in ((3, 2.5), (4, 1.5), (5, 1.75), (8, 2.5), (8, 2.0)):
+        R = O.fix_scale(q_bits, y_max)
+        assert R == float(np.float32(2.0 ** q_bits / (2.0 * np.float32(y_max))))
+        kmax = 2 ** (q_bits - 1) - 1
+        d = 2.0 * y_max / 2 ** q_bits
+        for v in rng.uniform(-1.3 * y_max, 1.3 * y_max, 2000).astype(np.float32):
+            frac = abs(float(v)) / d
+            if abs(frac - round(frac)) < 1e-4:
+                continue                       # FP32 and FP64 may decide a boundary differently
+            b = O.fix_code(float(v), R, kmax)
+            assert -kmax - 1 <= b <= kmax
+            assert (2 * b + 1) * d / 2 == O.quantize(float(v), q_bits, y_max)
+        assert O.fix_code(0.0, R, kmax) == 0 and O.fix_code(-0.0, R, kmax) == 0
+        assert O.fix_code(1e30, R, kmax) == kmax and O.fix_code(-1e30, R, kmax) == -kmax - 1
+
+
+def pin_table2_fixed_point(O):
+    """Table II again, through the decoder's fixed-point thresholds Theta~(u) = V(fl32(theta lambda^u))."""
+    want = {}
+    for q, i, th, tau in _golden_lines("table2_threshold_events.txt"):
+        want.setdefault(int(q), []).append((float(th), int(tau)))
+    thr = O.threshold_table_f32(-0.9, 0.99, 300)
+    for q, events in want.items():
+        R = O.fix_scale(q, 2.5)
+        kmax = 2 ** (q - 1) - 1
+        d = 5.0 / 2 ** q
+        vals = [(2 * O.fix_code(float(t), R, kmax) + 1) * d / 2 for t in thr]
+        got = [(vals[0], 0)] + [(vals[u], u) for u in range(1, len(vals)) if vals[u] != vals[u - 1]]
+        assert [(round(a, 4), b) for a, b in got] == events, (q, got)
+
+
+def pin_trace_fixed_point(O):
+    """Case I (Q = 4, Y_max = 2, Delta = 1/4, levels in units of Delta/2): y = (3,3,3,-3,3,3,3)
+    saturates to Y~ = (15,15,15,-15,15,15,15); w = 0.875 -> W~ = 7; theta = -0.375 -> Theta~ = -3;
+    eta = 0 -> q~ = V(0) = +1.  At t = 0 all three checks fail: E~_3 = 15 + 7(-3) + 1 = -5 < -3
+    flips x_3; E~_0,1,2 = 15 - 14 + 1 = 2 and E~_4,5,6 = 15 - 7 + 1 = 9 do not.  t = 1 is valid."""
+    C = hamming_code()
+    y = np.array([3, 3, 3, -3, 3, 3, 3], np.float32)
+    p = oracle_pkg.make_params(w=0.875, theta=-0.375, eta=0.0, lam=1.0, y_max=2.0, t_max=6,
+                               precision=oracle_pkg.FIX, q_bits=4)
+    bits, it, ps = O.decode_f32(C, y[None, :], 0.5, p, seed=1)
+    assert (int(bits[0, 0]), int(it[0]), int(ps[0])) == (0, 1, 1)
+    # theta = -0.625 -> Theta~ = -5: E~_3 = -5 is a tie, nothing flips, T is reached
+    p = oracle_pkg.make_params(w=0.875, theta=-0.625, eta=0.0, lam=1.0, y_max=2.0, t_max=6,
+                               precision=oracle_pkg.FIX, q_bits=4)
+    bits, it, ps = O.decode_f32(C, y[None, :], 0.5, p, seed=1)
+    assert (int(bits[0, 0]), int(it[0]), int(ps[0])) == (0x08, 6, 0)
+
+
+def _dyadic_frames(C, F, step, seed):
+    rng = np.random.default_rng(seed)
+    y, cw, _ = wl.frames(C, F, None, seed=seed)
+    noise = rng.integers(-16, 17, size=y.shape) * step
+    return (y + noise).astype(np.float32)
+
+
+def pin_fp16_reduces_to_fp32(O):
+    """With eta = 0 and inputs on a coarse dyadic grid every FP32 intermediate is a binary16
+    value, so the FP16 decoder must equal the FP32 decoder exactly."""
+    C = _pin_code()
+    y = _dyadic_frames(C, 40, 1.0 / 16, seed=21)
+    for variant in (0, 2):
+        p32 = oracle_pkg.make_params(w=0.5, theta=-0.75, eta=0.0, lam=1.0, t_max=30, smooth_window=8,
+                                     variant=variant, precision=oracle_pkg.FP32)
+        p16 = oracle_pkg.make_params(w=0.5, theta=-0.75, eta=0.0, lam=1.0, t_max=30, smooth_window=8,
+                                     variant=variant, precision=oracle_pkg.FP16)
+        a = O.decode_f32(C, y, 0.5, p32, seed=1)
+        b = O.decode_f32(C, y, 0.5, p16, seed=1)
+        assert all((u == v).all() for u, v in zip(a, b))
+        assert (a[2] == 0).any() and (a[2] == 1).any()
+
+
+def pin_fix_reduces_to_fp32(O):
+    """With Q = 4, Y_max = 2 (Delta = 1/4) and y, w, theta at level centres, eta = 0 gives
+    q~ = V(0) = +1, i.e. E~ (Delta/2) = E + Delta/2: the fixed-point decoder must equal the FP32
+    decoder run with theta - Delta/2."""
+    C = _pin_code()
+    rng = np.random.default_rng(22)
+    y, _, _ = wl.frames(C, 40, None, seed=22)
+    centres = (2 * rng.integers(-8, 8, size=y.shape) + 1) * 0.125   # +-0.125 .. +-1.875
+    y = np.where(y > 0, np.abs(centres), -np.abs(centres)).astype(np.float32)
+    # saturated samples: the fixed-point level tops out at 15 * Delta/2 = 1.875, which the FP32
+    # run reproduces by clamping at 1.875
+    y = np.where(rng.random(y.shape) < 0.25, np.sign(y) * 3.0, y).astype(np.float32)
+    y = np.where(rng.random(y.shape) < 0.02, -y, y).astype(np.float32)    # errors to correct
+    for variant in (0, 2):
+        pfix = oracle_pkg.make_params(w=0.375, theta=-0.625, eta=0.0, lam=1.0, y_max=2.0, t_max=30,
+                                      smooth_window=8, variant=variant, precision=oracle_pkg.FIX, q_bits=4)
+        p32 = oracle_pkg.make_params(w=0.375, theta=-0.75, eta=0.0, lam=1.0, y_max=1.875, t_max=30,
+                                     smooth_window=8, variant=variant, precision=oracle_pkg.FP32)
+        a = O.decode_f32(C, y, 0.5, pfix, seed=1)
+        b = O.decode_f32(C, y, 0.5, p32, seed=1)
+        assert all((u == v).all() for u, v in zip(a, b))
+        assert (a[2] == 0).any() and (a[2] == 1).any()
+
+
+def pin_precision_statistics(O):
+    """FP16 and 8-bit fixed point decode the same frames to nearly the FP32 results."""
+    C = _pin_code()
+    y, _, sig = wl.frames(C, 300, 3.0, seed=23)
+    res = {}
+    for prec, qb in ((oracle_pkg.FP32, 0), (oracle_pkg.FP16, 0), (oracle_pkg.FIX, 8)):
+        p = oracle_pkg.make_params(w=0.75, theta=-0.9, eta=0.9, lam=0.95, t_max=50, variant=3,
+                                   precision=prec, q_bits=qb)
+        res[prec] = O.decode_f32(C, y, sig, p, seed=2)
+    for prec in (oracle_pkg.FP16, oracle_pkg.FIX):
+        assert abs(res[prec][2].mean() - res[oracle_pkg.FP32][2].mean()) < 0.06
+        assert (res[prec][1] == res[oracle_pkg.FP32][1]).mean() > 0.3
+
+
 ALL_PINS = [
     pin_philox_kat, pin_ln_f32, pin_sincos_f32, pin_gauss_f32_vs_library, pin_gauss_statistics,
     pin_noise_variance, pin_threshold_table, pin_table2, pin_fig20, pin_quantizer,
     pin_trace_gdbf, pin_trace_injected_noise, pin_trace_adaptation, pin_trace_smoothing,
     pin_trace_clamp_sign_tie, pin_noiseless, pin_eta0_is_gdbf, pin_codeword_and_ml,
     pin_f32_matches_injected_noise, pin_frame_independence, pin_f32_f64_statistics,
+    pin_round_half, pin_metric_f16, pin_fix_quantizer, pin_trace_fixed_point, pin_table2_fixed_point, pin_fp16_reduces_to_fp32,
+    pin_fix_reduces_to_fp32, pin_precision_statistics,
 ]

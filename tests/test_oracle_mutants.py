@@ -55,6 +55,18 @@ MUTANTS = [
     ("sequential update", "if (flip) x[k] = (int8_t)-x[k];",
      "if (flip) { x[k] = (int8_t)-x[k]; for (int32_t e = C->sym_ptr[k]; e < C->sym_ptr[k + 1]; ++e) s[C->chk_idx[e]] = (int8_t)-s[C->chk_idx[e]]; }"),
     ("frame id offset", "J->frame_offset + (uint64_t)f,", "J->frame_offset + (uint64_t)f + 1,"),
+    ("half rounding mode", "rint(fabs((double)x) / q) * q", "floor(fabs((double)x) / q) * q"),
+    ("half quantum", "e >= -14 ? e - 10 : -24", "e >= -14 ? e - 11 : -24"),
+    ("half overflow", "if (a >= 0x477FF000u)", "if (a >= 0x477FE000u)"),
+    ("f16 metric drops a rounding", "const float e1 = oracle_round_half(xy + ws);", "const float e1 = xy + ws;"),
+    ("f16 metric drops q rounding", "const float q16 = oracle_round_half(q);", "const float q16 = q;"),
+    ("fix scale", "return (float)(ldexp(1.0, q_bits) / (2.0 * (double)y_max));",
+     "return (float)(ldexp(1.0, q_bits) / (double)y_max);"),
+    ("fix saturation", "X.fix_kmax = (1 << (P->q_bits - 1)) - 1;", "X.fix_kmax = (1 << (P->q_bits - 1));"),
+    ("fix negative code", "return v >= 0.0f ? k : -k - 1;", "return v >= 0.0f ? k : -k;"),
+    ("fix value", "return 2 * oracle_fix_code(v, R, kmax) + 1;", "return 2 * oracle_fix_code(v, R, kmax);"),
+    ("fix weight", "X.fix_W = fix_value(P->w, X.fix_R, X.fix_kmax);", "X.fix_W = fix_value(P->w, X.fix_R, X.fix_kmax) + 2;"),
+    ("fix metric sign", "const int32_t Eq = x[k] * yfix[k] + X->fix_W * S", "const int32_t Eq = x[k] * yfix[k] - X->fix_W * S"),
 ]
 
 RUNNER = r"""
