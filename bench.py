@@ -38,6 +38,8 @@ FRAMES_PER_POINT = 1_000_000
 EBN0_DB = (3.5, 4.0, 4.5)
 PARAMS = dict(w=0.1875, theta=-0.7, eta=0.65, lam=0.993, y_max=2.0, t_max=300, smooth_window=64,
               variant=3)
+# precision name -> (NGDBF precision, q_bits, dtype label)
+PRECISIONS = {"fp32": (0, 0, "f32"), "fp16": (1, 0, "f16"), "fix8": (2, 8, "i8")}
 DATA_SEED = 2014          # information bits and channel noise
 DECODER_SEED = 1          # Philox key of the perturbation
 # Algorithmic lane operations per (symbol, iteration) of the FP32 path: Philox 20 + uniforms 4
@@ -145,12 +147,13 @@ def measured_peaks():
         return {}
 
 
-def cpu_baseline(code, ys, cws, sigmas, gpu_outs, target_s=15.0):
-    """FP32 reference decoder on all host cores, on a bounded sample of the same frames;
-    also checks that the GPU decoded those frames identically."""
+def cpu_baseline(code, ys, cws, sigmas, gpu_outs, precision="fp32", target_s=15.0):
+    """Reference decoder (same arithmetic) on all host cores, on a bounded sample of the same
+    frames; also checks that the GPU decoded those frames identically."""
     import oracle
     O = oracle.load()
-    op = oracle.make_params(**PARAMS)
+    prec, q_bits, _ = PRECISIONS[precision]
+    op = oracle.make_params(**PARAMS, precision=prec, q_bits=q_bits)
     cores = os.cpu_count() or 1
     # calibrate on a small slice, then size the sample for about target_s seconds
     probe = max(cores, 64)
@@ -171,7 +174,7 @@ def cpu_baseline(code, ys, cws, sigmas, gpu_outs, target_s=15.0):
     fps = total / secs
     return {"value": fps, "unit": "frames/s", "cores": cores, "kind": "oracle",
             "sample": f"first {per_point} frames of each of the {len(EBN0_DB)} Eb/N0 batches "
-                      f"({total} frames, FP32 reference decoder, {cores} threads)",
+                      f"({total} frames, {precision} reference decoder, {cores} threads)",
             "info_gbit_s": fps * code.k / 1e9, "seconds": secs,
             "parity": {"frames": total, "mismatches": mism}}
 
@@ -207,7 +210,8 @@ def run_ours(args):
     code = wl.code_c2()
     off, ys_host, cws, sigmas = make_inputs(code, args.frames_per_point, rank, world, pinned=True)
     dc = ngdbf.DeviceCode.from_code(code)
-    gp = ngdbf.make_params(**PARAMS)
+    prec, q_bits, dtype = PRECISIONS[args.precision]
+    gp = ngdbf.make_params(**PARAMS, precision=prec, q_bits=q_bits)
     ys = [y.cuda(non_blocking=False) for y in ys_host]
     F = args.frames_per_point
     nb = (code.n + 7) // 8
@@ -299,16 +303,17 @@ def run_ours(args):
 
     base = None
     if rank == 0 and not args.no_cpu_baseline:
-        base = cpu_baseline(code, [y.numpy() for y in ys_host], cws, sigmas, host_outs)
+        base = cpu_baseline(code, [y.numpy() for y in ys_host], cws, sigmas, host_outs, args.precision)
 
     if rank == 0:
         line = {
             "metric": "decoded frames/s", "value": fps, "unit": "frames/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dtype,
             "data": "synthetic (seeded PEG code, random information words, AWGN)",
             "config": {"workload": "SM-NGDBF (adaptive, smoothed), PEG (6,32) N=2048 M=384 rate 1665/2048, "
                                    "10^6 frames at each of Eb/N0 3.5/4.0/4.5 dB per step",
+                       "precision": args.precision,
                        "code": "peg(6,32) N=2048 M=384 seed 1", "frames_per_point": F,
                        "ebn0_db": list(EBN0_DB), "params": PARAMS, "decoder_seed": DECODER_SEED,
                        "l2": "inputs larger than L2 (8.2 GB of samples per batch)",
@@ -326,6 +331,113 @@ def run_ours(args):
     dc.close()
     if world > 1:
         dist.destroy_process_group()
+
+
+# Uneven multi-code workload: five seeded PEG codes, frame counts from a seeded geometric
+# distribution (mean 4096), per-code Eb/N0 in [3.5, 4.5] dB and T in 100..300, SM-NGDBF with
+# the paper's parameter sets (rate 1/2: Figs. 2-4; high rate: Fig. 5).
+MULTI_CODES = [((3, 504, 252), "peg(3,6) N=504"), ((3, 1008, 504), "peg(3,6) N=1008"),
+               ((4, 4096, 2048), "peg(4,8) N=4096"), ((6, 2048, 384), "peg(6,32) N=2048"),
+               ((3, 8192, 1639), "peg(3,15) N=8192")]
+MULTI_SEED = 404
+
+
+def multicode_jobs(rank=0):
+    rng = np.random.default_rng(MULTI_SEED)
+    jobs = []
+    for (dv, n, m), name in MULTI_CODES:
+        F = int(rng.geometric(1.0 / 4096))
+        eb = float(rng.uniform(3.5, 4.5))
+        T = int(rng.integers(100, 301))
+        code = wl.peg_code(n, m, dv, seed=1, name=name)
+        if code.rate > 0.7:
+            prm = dict(w=0.1875, theta=-0.7, eta=0.65, lam=0.993, y_max=2.0)
+        else:
+            prm = dict(w=0.75, theta=-0.9, eta=0.95 if dv == 3 else 0.7, lam=0.99, y_max=2.5)
+        prm.update(t_max=T, smooth_window=64, variant=3)
+        jobs.append(dict(code=code, frames=F, ebn0=eb, params=prm, offset=rank * 10 ** 7))
+    return jobs
+
+
+def run_multicode(args):
+    """One persistent launch over the job table against one launch per code."""
+    import torch
+    from paper_1402_2773_gb300 import ngdbf
+
+    rank, world, local = env_rank()
+    torch.cuda.set_device(local)
+    ngdbf.load()
+    jobs = multicode_jobs(rank)
+    dcs, ys, sig, gps = [], [], [], []
+    for j, jb in enumerate(jobs):
+        y, _, s_ = wl.frames(jb["code"], jb["frames"], jb["ebn0"], seed=DATA_SEED + 10 + j, frame_offset=jb["offset"])
+        dcs.append(ngdbf.DeviceCode.from_code(jb["code"]))
+        ys.append(torch.from_numpy(y).cuda())
+        sig.append(s_)
+        gps.append(ngdbf.make_params(**jb["params"]))
+    stream = torch.cuda.current_stream()
+    batch = ngdbf.Batch([(dc, y, s_, gp, jb["offset"]) for dc, y, s_, gp, jb in zip(dcs, ys, sig, gps, jobs)],
+                        seed=DECODER_SEED, flags=ngdbf.NGDBF_BATCH_GRAPH | ngdbf.NGDBF_BATCH_TUNE)
+    launch = ngdbf.ngdbf_last_launch()
+    outs = [(torch.empty_like(o[0]), torch.empty_like(o[1]), torch.empty_like(o[2])) for o in batch.outputs]
+
+    def plain():
+        for dc, y, s_, gp, jb, o in zip(dcs, ys, sig, gps, jobs, outs):
+            dc.decode(y, s_, gp, seed=DECODER_SEED, frame_offset=jb["offset"], out=o, stream=stream)
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for _ in range(args.steps):
+            fn()
+        t1.record(stream)
+        torch.cuda.synchronize()
+        return t0.elapsed_time(t1) / 1e3
+
+    with ClockSampler(local) as clk:
+        t_plain = max_over_ranks(timed(plain), "cuda")
+        t_batch = max_over_ranks(timed(lambda: batch.launch(stream)), "cuda")
+    same = all(all(torch.equal(a, b) for a, b in zip(o1, o2)) for o1, o2 in zip(batch.outputs, outs))
+    frames = sum(jb["frames"] for jb in jobs)
+    fps = frames * args.steps * world / t_batch
+    fps_plain = frames * args.steps * world / t_plain
+    host = [tuple(t.cpu().numpy() for t in o) for o in batch.outputs]
+    per_code = []
+    ops = 0.0
+    for jb, o in zip(jobs, host):
+        it = o[1].astype(np.int64)
+        dv = jb["code"].dense().sum(axis=0).max()
+        ops += float(it.sum()) * jb["code"].n * (63 + 2 * int(dv))
+        per_code.append({"code": jb["code"].name, "frames": jb["frames"], "ebn0_db": round(jb["ebn0"], 3),
+                         "t_max": jb["params"]["t_max"], "avg_iters": float(it.mean()),
+                         "pass_rate": float(o[2].mean())})
+    clocks = clk.summary()
+    peak = (launch.get("sm_count") or 152) * 128 * (clocks.get("sm_max_mhz") or 2070.0) * 1e6
+    achieved = ops / (t_batch / args.steps)
+    if rank == 0:
+        print(json.dumps({
+            "metric": "decoded frames/s", "value": fps, "unit": "frames/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_batch / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded PEG codes, random information words, AWGN)",
+            "config": {"workload": "uneven multi-code batch: five PEG codes, geometric frame counts "
+                                   "(mean 4096), per-code Eb/N0 and T, SM-NGDBF, one persistent launch "
+                                   "(CUDA graph, tuned block size)", "codes": per_code,
+                       "l2": "inputs and slot state smaller than L2 between launches (both arms alike)"},
+            "plain_per_code": {"value": fps_plain, "unit": "frames/s", "ms_per_step": t_plain / args.steps * 1e3,
+                               "launches_per_step": len(jobs)},
+            "speedup_vs_plain": fps / fps_plain, "results_identical": bool(same),
+            "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "Tlane-op/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "kernel": "ngdbf_multi_kernel<ADAPT,SMOOTH,...>"},
+            "launch": launch, "gpu_launches": args.steps, "clocks": clocks,
+        }))
+    batch.close()
+    for dc in dcs:
+        dc.close()
 
 
 def run_reference(args):
@@ -388,6 +500,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", choices=["sm-ngdbf-6x32", "multicode"], default="sm-ngdbf-6x32",
+                    help="the benchmark workload (default) or the uneven multi-code batch")
+    ap.add_argument("--precision", choices=sorted(PRECISIONS), default="fp32",
+                    help="arithmetic of the held samples and E_k (the perturbation stays FP32)")
     ap.add_argument("--frames-per-point", type=int, default=FRAMES_PER_POINT,
                     help="frames per Eb/N0 batch (the benchmark workload is 10^6; smaller only for profiling)")
     args = ap.parse_args()
@@ -395,6 +511,8 @@ def main():
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "multicode":
+        run_multicode(args)
     else:
         run_ours(args)
 

@@ -61,8 +61,17 @@ typedef enum {
 /* Variant bits (Sec. III-C/D/E).  0 = plain M-NGDBF with one threshold. */
 enum { NGDBF_ADAPT = 1, NGDBF_SMOOTH = 2 };
 
-/* Arithmetic of the inversion function.  Only FP32 is implemented here. */
-enum { NGDBF_FP32 = 0 };
+/* Arithmetic of the held samples and the inversion function (Sec. IV-E); the
+ * perturbation is always the FP32 generator output.
+ *   NGDBF_FP32  E = ((x y + w S) + q), every step rounded to FP32.
+ *   NGDBF_FP16  y, w, q and theta lambda^u rounded to binary16 (nearest even);
+ *               E = h(h(x y + h(w S)) + q) with every result rounded to binary16.
+ *   NGDBF_FIX   Eq. 8 with q_bits = Q (2..8): level k = min(floor(|v| R),
+ *               2^(Q-1) - 1), R = fl32(2^Q / (2 y_max)), the product in FP32;
+ *               value 2b + 1 (b = k, or -k-1 for v < 0) in units of y_max / 2^Q;
+ *               E~ = x Y~ + W~ S + Q~ in exact integers against the level of
+ *               fl32(theta lambda^u).  Samples are held in 8 bits. */
+enum { NGDBF_FP32 = 0, NGDBF_FP16 = 1, NGDBF_FIX = 2 };
 
 /* Limits of this build. */
 enum {
@@ -82,8 +91,8 @@ typedef struct ngdbf_params {
     int32_t t_max;        /* T: at most T flip phases, 0 <= T <= NGDBF_MAX_T */
     int32_t smooth_window;/* W: X_k sums x(t) for t = max(0, T-W) .. T, 0 <= W <= 126 */
     int32_t variant;      /* OR of NGDBF_ADAPT, NGDBF_SMOOTH */
-    int32_t precision;    /* NGDBF_FP32 */
-    int32_t q_bits;       /* reserved, must be 0 */
+    int32_t precision;    /* NGDBF_FP32, NGDBF_FP16 or NGDBF_FIX */
+    int32_t q_bits;       /* NGDBF_FIX: Q in 2..8 (needs a finite y_max > 0); otherwise 0 */
 } ngdbf_params;
 
 typedef struct ngdbf_code ngdbf_code_t;   /* opaque; owned by the library */
@@ -178,7 +187,55 @@ ngdbf_status ngdbf_decode_noalloc(const ngdbf_code_t* code, const float* y, int6
                                   uint64_t frame_offset, uint8_t* bits, int32_t* iters,
                                   uint8_t* pass, void* stream);
 
-/* Launch shape of the most recent ngdbf_decode on the calling thread. */
+/*
+ * Job tables: several decode jobs -- codes of different length, rate, degree
+ * and iteration limit, each with its own frames, sigma and parameters -- in
+ * ONE persistent launch.  CTAs start on jobs in proportion to their estimated
+ * work (frames x n x (T + 1)); a CTA whose job has no unclaimed frame left and
+ * whose slots are idle moves to the job with the most unclaimed frames.  Each
+ * frame's result is the one ngdbf_decode gives for the same job (same seed,
+ * frame id = frame_offset + index): bit for bit, alone or in any mix.
+ * Restrictions within one table: every job has the same params.variant and
+ * params.precision; the perturbation seed is shared.
+ */
+typedef struct ngdbf_job {
+    const ngdbf_code_t* code;
+    const float* y;              /* DEVICE float[n_frames][n] */
+    int64_t n_frames;
+    float sigma;
+    ngdbf_params params;
+    uint64_t frame_offset;
+    uint8_t* bits;               /* DEVICE uint8[n_frames][ceil(n/8)] */
+    int32_t* iters;              /* DEVICE int32[n_frames] */
+    uint8_t* pass;               /* DEVICE uint8[n_frames] */
+} ngdbf_job;
+
+typedef struct ngdbf_batch ngdbf_batch_t;   /* opaque; owns device scratch and the job table */
+
+enum {
+    NGDBF_BATCH_TUNE = 1,   /* time the candidate block sizes on this table, keep the fastest */
+    NGDBF_BATCH_GRAPH = 2   /* capture the launch (queue reset + kernel) in a CUDA graph */
+};
+
+/*
+ * Builds a launch plan for n_jobs jobs (HOST array, copied): validates every
+ * job as ngdbf_decode would, uploads the job table and thresholds, allocates
+ * scratch, chooses the launch shape (timed on `stream` with NGDBF_BATCH_TUNE,
+ * which runs the table several times and so writes the outputs), and, with
+ * NGDBF_BATCH_GRAPH, captures the launch in a CUDA graph.  The buffers named
+ * by the jobs must stay valid while the batch exists.
+ * Errors: INVALID_ARG, UNSUPPORTED (mixed variant or precision, limits), OOM, CUDA.
+ */
+ngdbf_status ngdbf_batch_create(const ngdbf_job* jobs, int32_t n_jobs, uint64_t seed, int32_t flags,
+                                void* stream, ngdbf_batch_t** out);
+
+/* Decodes every job of the table once on `stream` (asynchronous). */
+ngdbf_status ngdbf_batch_launch(ngdbf_batch_t* batch, void* stream);
+
+/* Releases the plan; no launch of it may still be running. */
+ngdbf_status ngdbf_batch_destroy(ngdbf_batch_t* batch);
+
+/* Launch shape of the most recent ngdbf_decode* or ngdbf_batch_* call on the calling thread. */
 typedef struct ngdbf_launch_info {
     int32_t grid;            /* CTAs (each owns 32 frame slots) */
     int32_t block;           /* threads per CTA */

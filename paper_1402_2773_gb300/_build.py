@@ -8,8 +8,9 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 LIB_PATH = os.path.join(PKG, "libngdbf.so")
-SOURCES = [os.path.join(CSRC, "ngdbf_decode.cu")]
-DEPS = SOURCES + [os.path.join(CSRC, "ngdbf_device.cuh"), os.path.join(ROOT, "include", "ngdbf.h")]
+SOURCES = [os.path.join(CSRC, "ngdbf_decode.cu"), os.path.join(CSRC, "ngdbf_multi.cu")]
+HEADERS = [os.path.join(CSRC, h) for h in ("ngdbf_device.cuh", "ngdbf_kernels.cuh", "ngdbf_multi.h")]
+DEPS = SOURCES + HEADERS + [os.path.join(ROOT, "include", "ngdbf.h")]
 
 NVCC_FLAGS = [
     "-std=c++17", "-O3", "-lineinfo",
@@ -18,9 +19,7 @@ NVCC_FLAGS = [
     # no contraction elsewhere either
     "--fmad=false",
     "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
-    "-shared",
 ]
-
 
 def nvcc() -> str:
     for cand in (os.environ.get("NVCC"), "/usr/local/cuda/bin/nvcc", "nvcc"):
@@ -37,12 +36,24 @@ def stale(target: str, deps: list[str]) -> bool:
 
 
 def build_cuda(force: bool = False, verbose: bool = False) -> str:
-    """Compiles libngdbf.so next to this file; returns its path."""
+    """Compiles libngdbf.so next to this file (translation units in parallel); returns its path."""
     if force or stale(LIB_PATH, DEPS):
-        tmp = f"{LIB_PATH}.{os.getpid()}.tmp"
-        cmd = [nvcc(), *NVCC_FLAGS, *(["-Xptxas", "-v"] if verbose else []), "-o", tmp, *SOURCES]
-        subprocess.check_call(cmd)
-        os.replace(tmp, LIB_PATH)
+        tag = f"{os.getpid()}"
+        objs = [f"{src}.{tag}.o" for src in SOURCES]
+        procs = [subprocess.Popen([nvcc(), *NVCC_FLAGS, *(["-Xptxas", "-v"] if verbose else []),
+                                   "-c", "-o", obj, src]) for src, obj in zip(SOURCES, objs)]
+        codes = [p.wait() for p in procs]
+        try:
+            if any(codes):
+                raise subprocess.CalledProcessError(max(codes), "nvcc -c")
+            tmp = f"{LIB_PATH}.{tag}.tmp"
+            subprocess.check_call([nvcc(), "-shared", "-gencode", "arch=compute_103a,code=sm_103a",
+                                   "-o", tmp, *objs])
+            os.replace(tmp, LIB_PATH)
+        finally:
+            for o in objs:
+                if os.path.exists(o):
+                    os.remove(o)
     return LIB_PATH
 
 

@@ -1,30 +1,7 @@
-// ngdbf_decode.cu -- persistent slot-refill NGDBF decoder for sm_103a and its C ABI.
-//
-// Work decomposition.  A CTA owns 32 frame slots, one per bit of a 32-bit
-// word: the decisions x_k of its 32 frames are one word per symbol k and the
-// syndromes s_i one word per check i (bit f set <=> x_k = -1 / check i
-// unsatisfied for slot f).  Each round the CTA
-//   A. forms every syndrome word as the XOR of the d_c decision words of a
-//      check (Sec. III-A, Step 1 of Sec. III-B), OR-reduces them to the
-//      "some check unsatisfied" mask with warp reductions,
-//   B. retires slots whose frame satisfied every check (pass) or reached T
-//      (smoothed output, Sec. III-E), writes their outputs, takes new frames
-//      from a global atomic queue for them and loads those frames, then
-//   C. runs Step 2 / Step 3b for every symbol of every live slot: a warp
-//      processes four symbols (one Philox call) at a time with lane = slot,
-//      counts the lane's unsatisfied checks among M(k), forms
-//      E_k = x_k y_k + w S_k + q_k, compares it with theta lambda^{u_k},
-//      adapts u_k, accumulates the smoothing counter, and rebuilds the
-//      decision word with a warp ballot.
-// Slots therefore iterate independently (each frame has its own t), a
-// converged frame frees its slot at once, and the CTA only stops when the
-// queue is empty and its last slot finished.
-//
-// Per-(symbol, slot) state: the saturated sample (FP32, global scratch laid
-// out [k][slot], L2-resident), and a 16-bit word holding u_k (bits 0-8) and
-// the number of -1 decisions inside the smoothing window (bits 9-15), in
-// shared memory when it fits, else in global scratch.  Decision and syndrome
-// words, the code adjacency, and the threshold table live in shared memory.
+// ngdbf_decode.cu -- the single-job NGDBF kernel and the C ABI (validation, code tables,
+// launch planning, host pipeline, job tables).  Device code shared with the job-table
+// kernel lives in ngdbf_kernels.cuh.
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -36,363 +13,23 @@
 #include <vector>
 
 #include "../../include/ngdbf.h"
-#include "ngdbf_device.cuh"
+#include "ngdbf_kernels.cuh"
 
 namespace ngdbf {
 
-constexpr int kSlots = 32;
-constexpr int kMaxT = NGDBF_MAX_T;
-constexpr uint32_t kUMask = 0x1FFu;   // u_k: bits 0-8
-constexpr int kCShift = 9;            // smoothing count: bits 9-15
-
-struct DecodeArgs {
-    // code tables (device)
-    int32_t n, m, dv_max, dc_max;
-    const uint16_t* chk_cols;   // [dc_max][m]   N(i) column-major, padded with n
-    const uint16_t* sym_chks;   // [n][dv_max]   M(k) row-major, padded with m
-    const uint8_t* sym_deg;     // [n]           d_v(k)
-    int32_t tables_smem;        // copy the tables into shared memory
-    // batch
-    const float* y;             // [n_frames][n]
-    int64_t n_frames;
-    uint64_t frame_offset;
-    uint8_t* bits;              // [n_frames][nb]
-    int32_t* iters;
-    uint8_t* pass;
-    int32_t nb;
-    // parameters
-    float w, theta, scale, y_max;
-    int32_t clamp, t_max, t_smooth;   // t_smooth = max(0, T - W)
-    // scratch
-    float* yslots;              // [grid][n][32]
-    uint16_t* st_global;        // [grid][n][32] when the state is not in shared memory
-    unsigned long long* queue;  // next unclaimed frame index
-    GenConsts G;
-    float thr[kMaxT + 1];       // fl32(theta lambda^u), u = 0..T
-};
-
-struct SmemLayout {
-    int32_t off_frame, off_start, off_ctl, off_xw, off_sw, off_cnt, off_thr, off_st, off_chk, off_sym, total;
-};
-
-// Offsets in bytes of the shared-memory arrays.  ctl holds: [0..1] unsatisfied
-// masks (double-buffered by pass parity), [2] live mask, [3] new-slot mask.
-// cnt holds per symbol the bit-sliced count of unsatisfied checks (one word per
-// count bit, bit f for slot f) and d_v(k): 3 slices + degree in 16 bytes when
-// d_v <= 7 (narrow), 7 slices + degree in 32 bytes otherwise (wide).
-__host__ __device__ inline SmemLayout smem_layout(int n, int m, int t_max, int dv_max, int dc_max,
-                                                  bool need_thr, bool st_smem, bool tables_smem) {
-    SmemLayout L;
-    int o = 0;
-    auto take = [&](int bytes, int align) {
-        o = (o + align - 1) / align * align;
-        int r = o;
-        o += bytes;
-        return r;
-    };
-    const int cnt_bytes = dv_max <= 7 ? 16 : 32;
-    L.off_frame = take(kSlots * 8, 16);
-    L.off_start = take(kSlots * 4, 16);
-    L.off_ctl = take(8 * 4, 16);
-    L.off_cnt = take(n * cnt_bytes, 16);
-    L.off_xw = take((n + 1) * 4, 16);
-    L.off_sw = take((m + 1) * 4, 16);
-    L.off_thr = need_thr ? take((t_max + 1) * 4, 16) : -1;
-    L.off_st = st_smem ? take(n * kSlots * 2, 16) : -1;
-    L.off_chk = tables_smem ? take(dc_max * m * 2, 16) : -1;
-    L.off_sym = tables_smem ? take(n * dv_max * 2 + n, 16) : -1;
-    L.total = (o + 15) / 16 * 16;
-    return L;
-}
-
-// Position of the (j+1)-th set bit of mask (j < popc(mask)).
-__device__ __forceinline__ int nth_set_bit(uint32_t mask, int j) {
-    for (int i = 0; i < j; ++i) mask &= mask - 1u;
-    return __ffs(mask) - 1;
-}
-
-template <bool ADAPT, bool SMOOTH, bool ST_SMEM, bool WIDE>
+template <bool ADAPT, bool SMOOTH, bool ST_SMEM, bool WIDE, int PREC>
 __global__ void __launch_bounds__(1024) ngdbf_persistent_kernel(const __grid_constant__ DecodeArgs A) {
-    constexpr bool kState = ADAPT || SMOOTH;
-    extern __shared__ __align__(16) unsigned char smem[];
-    const int n = A.n, m = A.m, T = A.t_max, dv_max = A.dv_max, dc_max = A.dc_max;
-    const SmemLayout L = smem_layout(n, m, T, dv_max, dc_max, ADAPT, ST_SMEM && kState, A.tables_smem != 0);
-    long long* lane_frame = reinterpret_cast<long long*>(smem + L.off_frame);
-    int32_t* lane_start = reinterpret_cast<int32_t*>(smem + L.off_start);
-    uint32_t* ctl = reinterpret_cast<uint32_t*>(smem + L.off_ctl);
-    uint4* cnt = reinterpret_cast<uint4*>(smem + L.off_cnt);
-    uint32_t* xw = reinterpret_cast<uint32_t*>(smem + L.off_xw);
-    uint32_t* sw = reinterpret_cast<uint32_t*>(smem + L.off_sw);
-    float* thr = ADAPT ? reinterpret_cast<float*>(smem + L.off_thr) : nullptr;
-    uint16_t* st = nullptr;
-    if constexpr (kState) {
-        st = ST_SMEM ? reinterpret_cast<uint16_t*>(smem + L.off_st)
-                     : A.st_global + (size_t)blockIdx.x * n * kSlots;
-    }
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
-    // adjacency tables: only phases A and A' read them, so a generic pointer to
-    // shared or global memory serves both placements
-    const uint16_t* chk_cols = A.chk_cols;
-    const uint16_t* sym_chks = A.sym_chks;
-    const uint8_t* sym_deg = A.sym_deg;
-    if (A.tables_smem) {
-        uint16_t* c = reinterpret_cast<uint16_t*>(smem + L.off_chk);
-        uint16_t* s = reinterpret_cast<uint16_t*>(smem + L.off_sym);
-        uint8_t* d = reinterpret_cast<uint8_t*>(s + n * dv_max);
-        for (int i = tid; i < dc_max * m; i += blockDim.x) c[i] = A.chk_cols[i];
-        for (int i = tid; i < n * dv_max; i += blockDim.x) s[i] = A.sym_chks[i];
-        for (int i = tid; i < n; i += blockDim.x) d[i] = A.sym_deg[i];
-        chk_cols = c;
-        sym_chks = s;
-        sym_deg = d;
-    }
-    float* ys = A.yslots + (size_t)blockIdx.x * n * kSlots;
-
-    // ---- set-up: zero the state, sentinels, thresholds, first 32 frames ----
-    for (int k = tid; k <= n; k += blockDim.x) xw[k] = 0u;
-    for (int i = tid; i <= m; i += blockDim.x) sw[i] = 0u;
-    if constexpr (ADAPT)
-        for (int u = tid; u <= T; u += blockDim.x) thr[u] = A.thr[u];
-    if constexpr (kState)
-        for (int e = tid; e < n * kSlots; e += blockDim.x) st[e] = 0;
-    if (tid == 0) {
-        for (int c = 0; c < 8; ++c) ctl[c] = 0u;
-        const unsigned long long base = atomicAdd(A.queue, (unsigned long long)kSlots);
-        uint32_t live = 0;
-        for (int f = 0; f < kSlots; ++f) {
-            const unsigned long long fid = base + f;
-            lane_start[f] = 0;
-            if (fid < (unsigned long long)A.n_frames) {
-                lane_frame[f] = (long long)fid;
-                live |= 1u << f;
-            } else {
-                lane_frame[f] = -1;
-            }
-        }
-        ctl[2] = live;
-        ctl[3] = live;
-    }
-    __syncthreads();
-
-    int round = 0;   // flip phases executed by this CTA; slot f is at t = round - lane_start[f]
-    int pass_id = 0;
-    bool refill = true;
-    for (;;) {
-        if (refill) {
-            // ---- load new frames: saturated samples into the slot columns, x(0) = sign(y) ----
-            const uint32_t fresh = ctl[3];
-            for (int k = tid; k < n; k += blockDim.x) {
-                uint32_t word = xw[k] & ~fresh;
-                uint32_t rest = fresh;
-                while (rest) {
-                    const int f = __ffs(rest) - 1;
-                    rest &= rest - 1;
-                    float v = __ldg(A.y + (size_t)lane_frame[f] * n + k);
-                    if (A.clamp) {
-                        if (v > A.y_max) v = A.y_max;
-                        if (v < -A.y_max) v = -A.y_max;
-                    }
-                    ys[k * kSlots + f] = v;
-                    if (!(v >= 0.0f)) word |= 1u << f;
-                    if constexpr (kState) st[k * kSlots + f] = 0;
-                }
-                xw[k] = word;
-            }
-            __syncthreads();
-            refill = false;
-        }
-
-        // ---- A. syndromes (four threads XOR a quarter of a check each) and the vote ----
-        {
-            uint32_t* unsat = ctl + (pass_id & 1);
-            if (tid == 0) ctl[(pass_id + 1) & 1] = 0u;
-            uint32_t acc = 0;
-            const int per_pass = blockDim.x >> 2, sub = tid & 3;
-            for (int base = 0; base < m; base += per_pass) {
-                const int i = base + (tid >> 2);
-                uint32_t s = 0;
-                if (i < m)
-                    for (int j = sub; j < dc_max; j += 4) s ^= xw[chk_cols[j * m + i]];
-                s ^= __shfl_xor_sync(0xFFFFFFFFu, s, 1);
-                s ^= __shfl_xor_sync(0xFFFFFFFFu, s, 2);
-                if (i < m && sub == 0) sw[i] = s;
-                acc |= s;
-            }
-            acc = __reduce_or_sync(0xFFFFFFFFu, acc);
-            if (lane == 0 && acc) atomicOr(unsat, acc);
-            __syncthreads();
-        }
-        const uint32_t unsat = ctl[pass_id & 1];
-        ++pass_id;
-        uint32_t live = ctl[2];
-        const uint32_t conv = live & ~unsat;
-        const int my_t = round - lane_start[lane];
-        const uint32_t at_T = __ballot_sync(0xFFFFFFFFu, ((live >> lane) & 1u) && my_t >= T);
-        const uint32_t fin = conv | (live & at_T);
-
-        if (fin) {
-            // ---- B. outputs of finished slots ----
-            const int nfin = __popc(fin);
-            const int work = nfin * A.nb;
-            for (int idx = tid; idx < work; idx += blockDim.x) {
-                const int j = idx / A.nb, b = idx - j * A.nb;
-                const int f = nth_set_bit(fin, j);
-                const bool ok = (conv >> f) & 1u;
-                const int tf = round - lane_start[f];
-                uint32_t byte = 0;
-#pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    const int k = 8 * b + q;
-                    if (k < n) {
-                        uint32_t bit = (xw[k] >> f) & 1u;
-                        if constexpr (SMOOTH) {
-                            if (!ok) {
-                                // X_k = terms - 2 * (#-1 decisions), x(T) included here
-                                const int terms = tf - A.t_smooth + 1;
-                                const int neg = (int)(st[k * kSlots + f] >> kCShift) + (int)bit;
-                                const int X = terms - 2 * neg;
-                                bit = X < 0 ? 1u : (X > 0 ? 0u : bit);
-                            }
-                        }
-                        byte |= bit << q;
-                    }
-                }
-                A.bits[(size_t)lane_frame[f] * A.nb + b] = (uint8_t)byte;
-            }
-            if (tid < nfin) {
-                const int f = nth_set_bit(fin, tid);
-                const bool ok = (conv >> f) & 1u;
-                const long long fr = lane_frame[f];
-                A.iters[fr] = ok ? round - lane_start[f] : T;
-                A.pass[fr] = ok ? 1 : 0;
-            }
-            __syncthreads();
-            // ---- claim new frames for the finished slots ----
-            if (tid == 0) {
-                uint32_t fresh = 0;
-                const unsigned long long base = atomicAdd(A.queue, (unsigned long long)nfin);
-                for (int j = 0; j < nfin; ++j) {
-                    const int f = nth_set_bit(fin, j);
-                    const unsigned long long fid = base + j;
-                    if (fid < (unsigned long long)A.n_frames) {
-                        lane_frame[f] = (long long)fid;
-                        lane_start[f] = round;
-                        fresh |= 1u << f;
-                    } else {
-                        lane_frame[f] = -1;
-                    }
-                }
-                ctl[2] = (live & ~fin) | fresh;
-                ctl[3] = fresh;
-            }
-            __syncthreads();
-            live = ctl[2];
-            if (ctl[3]) {
-                refill = true;      // new frames need their t = 0 syndrome test first
-                continue;
-            }
-        }
-        if (live == 0) break;
-
-        // ---- A'. per symbol, the bit-sliced count of unsatisfied checks in M(k) ----
-        for (int k = tid; k < n; k += blockDim.x) {
-            const uint16_t* row = sym_chks + k * dv_max;
-            if constexpr (!WIDE) {
-                uint32_t b0 = 0, b1 = 0, b2 = 0;           // count <= 7: three slices
-                for (int e = 0; e < dv_max; ++e) {
-                    const uint32_t s = sw[row[e]];
-                    const uint32_t c0 = b0 & s;
-                    b0 ^= s;
-                    const uint32_t c1 = b1 & c0;
-                    b1 ^= c0;
-                    b2 ^= c1;
-                }
-                cnt[k] = make_uint4(b0, b1, b2, (uint32_t)sym_deg[k]);
-            } else {
-                uint32_t b[7] = {0, 0, 0, 0, 0, 0, 0};     // count <= 127: seven slices
-                for (int e = 0; e < dv_max; ++e) {
-                    uint32_t carry = sw[row[e]];
-#pragma unroll
-                    for (int q = 0; q < 7; ++q) {
-                        const uint32_t c = b[q] & carry;
-                        b[q] ^= carry;
-                        carry = c;
-                    }
-                }
-                cnt[2 * k] = make_uint4(b[0], b[1], b[2], b[3]);
-                cnt[2 * k + 1] = make_uint4(b[4], b[5], b[6], (uint32_t)sym_deg[k]);
-            }
-        }
-        __syncthreads();
-
-        // ---- C. Step 2 and Step 3b for every symbol of every live slot ----
-        {
-            const bool act = (live >> lane) & 1u;
-            const long long fr = lane_frame[lane];
-            const uint64_t fid = A.frame_offset + (uint64_t)(act ? fr : 0);
-            const uint32_t flo = (uint32_t)fid, fhi = (uint32_t)(fid >> 32);
-            const int t = act ? round - lane_start[lane] : 0;
-            const bool window = SMOOTH && act && t >= A.t_smooth;
-            const int groups = (n + 3) >> 2;
-            for (int g = warp; g < groups; g += nwarps) {
-                const int k0 = 4 * g;
-                // issue the sample and state loads before the generator's arithmetic
-                float yv[4];
-                uint32_t sv[4];
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const bool in = k0 + j < n;
-                    yv[j] = in ? ys[(k0 + j) * kSlots + lane] : 0.0f;
-                    if constexpr (kState) sv[j] = in ? (uint32_t)st[(k0 + j) * kSlots + lane] : 0u;
-                }
-                float z[4];
-                gauss4((uint32_t)g, (uint32_t)t, flo, fhi, A.G, z);
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const int k = k0 + j;
-                    if (k >= n) break;
-                    int unsat_cnt, deg;
-                    if constexpr (!WIDE) {
-                        const uint4 c = cnt[k];
-                        unsat_cnt = (int)(((c.x >> lane) & 1u) | (((c.y >> lane) & 1u) << 1) |
-                                          (((c.z >> lane) & 1u) << 2));
-                        deg = (int)c.w;
-                    } else {
-                        const uint4 c = cnt[2 * k], d = cnt[2 * k + 1];
-                        unsat_cnt = (int)(((c.x >> lane) & 1u) | (((c.y >> lane) & 1u) << 1) |
-                                          (((c.z >> lane) & 1u) << 2) | (((c.w >> lane) & 1u) << 3) |
-                                          (((d.x >> lane) & 1u) << 4) | (((d.y >> lane) & 1u) << 5) |
-                                          (((d.z >> lane) & 1u) << 6));
-                        deg = (int)d.w;
-                    }
-                    const int S = deg - 2 * unsat_cnt;
-                    const uint32_t xword = xw[k];
-                    const bool xneg = (xword >> lane) & 1u;
-                    const float q = __fmul_rn(A.scale, z[j]);
-                    const float E = inversion_metric(xneg, yv[j], S, A.w, q);
-                    bool flip;
-                    if constexpr (kState) {
-                        const uint32_t s0 = sv[j];
-                        // u_k <= t - 1 < T for a live slot (cleared on every refill)
-                        const float th = ADAPT ? thr[s0 & kUMask] : A.theta;
-                        flip = act && (E < th);
-                        const uint32_t nv = s0 + ((ADAPT && act && !flip) ? 1u : 0u) +
-                                            ((window && xneg) ? (1u << kCShift) : 0u);
-                        if (nv != s0) st[k * kSlots + lane] = (uint16_t)nv;
-                    } else {
-                        flip = act && (E < A.theta);
-                    }
-                    const uint32_t fm = __ballot_sync(0xFFFFFFFFu, flip);
-                    if (lane == 0 && fm) xw[k] = xword ^ fm;
-                }
-            }
-        }
-        __syncthreads();
-        ++round;
-    }
+    using HeldT = typename Held<PREC>::T;
+    const Job& J = A.J;
+    const SmemLayout L = smem_layout(J.n, J.m, J.t_max, J.dv_max, J.dc_max, ADAPT,
+                                     ST_SMEM && (ADAPT || SMOOTH), A.tables_smem != 0);
+    HeldT* ys = static_cast<HeldT*>(A.yslots) + (size_t)blockIdx.x * J.n * kSlots;
+    uint16_t* st = A.st_global ? A.st_global + (size_t)blockIdx.x * J.n * kSlots : nullptr;
+    decode_job<ADAPT, SMOOTH, ST_SMEM, WIDE, PREC>(J, A.thr, A.G, L, A.tables_smem != 0, ys, st);
 }
 
 }  // namespace ngdbf
+
 
 // ===========================================================================
 // Host side: validation, code tables, launch configuration, C ABI
@@ -478,20 +115,32 @@ struct LaunchPlan {
 
 using KernelFn = void (*)(DecodeArgs);
 
-template <bool AD, bool SM>
+template <bool AD, bool SM, int PREC>
 KernelFn pick_width(bool st_smem, bool wide) {
-    if (st_smem) return wide ? ngdbf_persistent_kernel<AD, SM, true, true> : ngdbf_persistent_kernel<AD, SM, true, false>;
-    return wide ? ngdbf_persistent_kernel<AD, SM, false, true> : ngdbf_persistent_kernel<AD, SM, false, false>;
+    if (st_smem) return wide ? ngdbf_persistent_kernel<AD, SM, true, true, PREC> : ngdbf_persistent_kernel<AD, SM, true, false, PREC>;
+    return wide ? ngdbf_persistent_kernel<AD, SM, false, true, PREC> : ngdbf_persistent_kernel<AD, SM, false, false, PREC>;
 }
 
-KernelFn pick_kernel(int variant, bool st_smem, bool wide) {
+template <int PREC>
+KernelFn pick_variant(int variant, bool st_smem, bool wide) {
     switch (variant & 3) {
-        case 0: return pick_width<false, false>(st_smem, wide);
-        case 1: return pick_width<true, false>(st_smem, wide);
-        case 2: return pick_width<false, true>(st_smem, wide);
-        default: return pick_width<true, true>(st_smem, wide);
+        case 0: return pick_width<false, false, PREC>(st_smem, wide);
+        case 1: return pick_width<true, false, PREC>(st_smem, wide);
+        case 2: return pick_width<false, true, PREC>(st_smem, wide);
+        default: return pick_width<true, true, PREC>(st_smem, wide);
     }
 }
+
+KernelFn pick_kernel(int variant, int precision, bool st_smem, bool wide) {
+    switch (precision) {
+        case NGDBF_FP16: return pick_variant<kFP16>(variant, st_smem, wide);
+        case NGDBF_FIX: return pick_variant<kFIX>(variant, st_smem, wide);
+        default: return pick_variant<kFP32>(variant, st_smem, wide);
+    }
+}
+
+// Bytes of one held sample.
+size_t held_bytes(int precision) { return precision == NGDBF_FP16 ? 2 : (precision == NGDBF_FIX ? 1 : 4); }
 
 ngdbf_status plan_launch(const ngdbf_code* C, const ngdbf_params* P, int64_t n_frames, int dev,
                          LaunchPlan* plan, KernelFn* fn_out, int* sm_count_out) {
@@ -521,7 +170,7 @@ ngdbf_status plan_launch(const ngdbf_code* C, const ngdbf_params* P, int64_t n_f
     }
     if (L.total > smem_optin)
         return fail(NGDBF_ERR_UNSUPPORTED, "code too large for the shared-memory decision words");
-    KernelFn fn = pick_kernel(P->variant, st_smem, C->dv_max > 7);
+    KernelFn fn = pick_kernel(P->variant, P->precision, st_smem, C->dv_max > 7);
     e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, L.total);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
     // Most resident warps per SM; ties go to more CTAs (more slots in flight).
@@ -551,6 +200,44 @@ ngdbf_status plan_launch(const ngdbf_code* C, const ngdbf_params* P, int64_t n_f
     return NGDBF_OK;
 }
 
+// Job fields of one decode and its threshold words thr[0..t_max].
+void fill_job(const ngdbf_code* C, const ngdbf_params* P, const float* y, int64_t n_frames, float sigma,
+              uint64_t frame_offset, uint8_t* bits, int32_t* iters, uint8_t* pass,
+              unsigned long long* queue, Job* out, uint32_t* thr) {
+    Job& J = *out;
+    std::memset(&J, 0, sizeof(J));
+    J.n = C->n; J.m = C->m; J.dv_max = C->dv_max; J.dc_max = C->dc_max;
+    J.chk_cols = C->d_chk_cols; J.sym_chks = C->d_sym_chks; J.sym_deg = C->d_sym_deg;
+    J.y = y; J.n_frames = n_frames; J.frame_offset = frame_offset;
+    J.bits = bits; J.iters = iters; J.pass = pass; J.nb = (C->n + 7) / 8;
+    J.w = P->precision == NGDBF_FP16 ? __half2float(__float2half_rn(P->w)) : P->w;
+    J.scale = (float)((double)P->eta * (double)sigma);
+    J.clamp = (P->y_max > 0.0f && std::isfinite(P->y_max)) ? 1 : 0;
+    J.y_max = J.clamp ? P->y_max : 0.0f;
+    J.t_max = P->t_max;
+    J.t_smooth = std::max(0, P->t_max - P->smooth_window);
+    J.queue = queue;
+    if (P->precision == NGDBF_FIX) {
+        J.fix_R = (float)(std::ldexp(1.0, P->q_bits) / (2.0 * (double)P->y_max));
+        J.fix_kmax = (1 << (P->q_bits - 1)) - 1;
+        J.fix_W = 2 * fix_code(P->w, J.fix_R, J.fix_kmax) + 1;
+    }
+    double p = 1.0;
+    for (int u = 0; u <= P->t_max; ++u) {
+        const float th = (float)((double)P->theta * p);      // fl32(theta lambda^u)
+        uint32_t word;
+        if (P->precision == NGDBF_FIX) {
+            const int32_t v = 2 * fix_code(th, J.fix_R, J.fix_kmax) + 1;
+            std::memcpy(&word, &v, 4);
+        } else {
+            const float h = P->precision == NGDBF_FP16 ? __half2float(__float2half_rn(th)) : th;
+            std::memcpy(&word, &h, 4);
+        }
+        thr[u] = word;
+        p = p * (double)P->lambda;
+    }
+}
+
 // Kernel arguments of one decode: scratch at `base` (work counter, then the
 // per-slot samples), per-slot state at `st_base` when it lives in global memory.
 void fill_args(const ngdbf_code* C, const ngdbf_params* P, const LaunchPlan& plan, const float* y,
@@ -559,26 +246,13 @@ void fill_args(const ngdbf_code* C, const ngdbf_params* P, const LaunchPlan& pla
                bool st_global, DecodeArgs* out) {
     DecodeArgs& A = *out;
     std::memset(&A, 0, sizeof(A));
-    A.n = C->n; A.m = C->m; A.dv_max = C->dv_max; A.dc_max = C->dc_max;
-    A.chk_cols = C->d_chk_cols; A.sym_chks = C->d_sym_chks; A.sym_deg = C->d_sym_deg;
+    fill_job(C, P, y, n_frames, sigma, frame_offset, bits, iters, pass,
+             reinterpret_cast<unsigned long long*>(base), &A.J, A.thr);
+    A.J.thr = nullptr;                 // thresholds travel inline in the launch
     A.tables_smem = plan.tables_smem ? 1 : 0;
-    A.y = y; A.n_frames = n_frames; A.frame_offset = frame_offset;
-    A.bits = bits; A.iters = iters; A.pass = pass; A.nb = (C->n + 7) / 8;
-    A.w = P->w; A.theta = P->theta;
-    A.scale = (float)((double)P->eta * (double)sigma);
-    A.clamp = (P->y_max > 0.0f && std::isfinite(P->y_max)) ? 1 : 0;
-    A.y_max = A.clamp ? P->y_max : 0.0f;
-    A.t_max = P->t_max;
-    A.t_smooth = std::max(0, P->t_max - P->smooth_window);
-    A.queue = reinterpret_cast<unsigned long long*>(base);
-    A.yslots = reinterpret_cast<float*>(base + 256);
+    A.yslots = base + 256;
     A.st_global = st_global ? reinterpret_cast<uint16_t*>(st_base) : nullptr;
     host_gen_consts(seed, A.G);
-    double p = 1.0;
-    for (int u = 0; u <= P->t_max; ++u) {
-        A.thr[u] = (float)((double)P->theta * p);
-        p = p * (double)P->lambda;
-    }
 }
 
 ngdbf_status check_params(const ngdbf_params* P, float sigma) {
@@ -594,8 +268,14 @@ ngdbf_status check_params(const ngdbf_params* P, float sigma) {
     if (P->smooth_window < 0) return fail(NGDBF_ERR_INVALID_ARG, "smooth_window must be >= 0");
     if (P->smooth_window > NGDBF_MAX_WINDOW) return fail(NGDBF_ERR_UNSUPPORTED, "smooth_window above NGDBF_MAX_WINDOW");
     if (P->variant & ~3) return fail(NGDBF_ERR_INVALID_ARG, "unknown variant bits");
-    if (P->precision != NGDBF_FP32) return fail(NGDBF_ERR_UNSUPPORTED, "only NGDBF_FP32 is implemented");
-    if (P->q_bits != 0) return fail(NGDBF_ERR_INVALID_ARG, "q_bits is reserved and must be 0");
+    if (P->precision < NGDBF_FP32 || P->precision > NGDBF_FIX) return fail(NGDBF_ERR_INVALID_ARG, "unknown precision");
+    if (P->precision == NGDBF_FIX) {
+        if (P->q_bits < 2 || P->q_bits > 8) return fail(NGDBF_ERR_INVALID_ARG, "fixed point needs 2 <= q_bits <= 8");
+        if (!(P->y_max > 0.0f) || !std::isfinite(P->y_max))
+            return fail(NGDBF_ERR_INVALID_ARG, "fixed point needs a finite y_max > 0 (it sets the step)");
+    } else if (P->q_bits != 0) {
+        return fail(NGDBF_ERR_INVALID_ARG, "q_bits must be 0 unless precision is NGDBF_FIX");
+    }
     return NGDBF_OK;
 }
 
@@ -632,7 +312,7 @@ ngdbf_status decode_impl(const ngdbf_code* C, const float* y, int64_t n_frames, 
     if (s != NGDBF_OK) return s;
     const bool state = (P->variant & 3) != 0;
     const size_t slot_elems = (size_t)plan.grid * C->n * kSlots;
-    const size_t bytes_y = (slot_elems * 4 + 255) / 256 * 256;
+    const size_t bytes_y = (slot_elems * held_bytes(P->precision) + 255) / 256 * 256;
     const size_t bytes_st = (state && !plan.st_smem) ? (slot_elems * 2 + 255) / 256 * 256 : 0;
     const size_t total = 256 + bytes_y + bytes_st;
     void* ws = nullptr;
@@ -648,7 +328,7 @@ ngdbf_status decode_impl(const ngdbf_code* C, const float* y, int64_t n_frames, 
     fill_args(C, P, plan, y, n_frames, sigma, seed, frame_offset, bits, iters, pass, base,
               base + 256 + bytes_y, bytes_st != 0, &A);
 
-    e = cudaMemsetAsync(A.queue, 0, sizeof(unsigned long long), stream);
+    e = cudaMemsetAsync(A.J.queue, 0, sizeof(unsigned long long), stream);
     if (e == cudaSuccess) {
         fn<<<plan.grid, plan.block, plan.smem, stream>>>(A);
         e = cudaGetLastError();
@@ -901,7 +581,7 @@ extern "C" ngdbf_status ngdbf_decode_noalloc(const ngdbf_code_t* C, const float*
 
     // Fit the launch into the static array: fewer CTAs when a full grid does not fit.
     const bool state = (P->variant & 3) != 0;
-    const size_t per_cta_y = (size_t)C->n * kSlots * 4;
+    const size_t per_cta_y = (size_t)C->n * kSlots * held_bytes(P->precision);
     const size_t per_cta_st = (state && !plan.st_smem) ? (size_t)C->n * kSlots * 2 : 0;
     const size_t avail = (size_t)NGDBF_NOALLOC_SCRATCH_BYTES - 256 - 256;   // counter + alignment
     const size_t max_grid = avail / (per_cta_y + per_cta_st);
@@ -916,7 +596,7 @@ extern "C" ngdbf_status ngdbf_decode_noalloc(const ngdbf_code_t* C, const float*
     fill_args(C, P, plan, y, n_frames, sigma, seed, frame_offset, bits, iters, pass, base,
               base + 256 + bytes_y, per_cta_st != 0, &A);
     // The work counter must start at zero; the kernel initializes everything else it reads.
-    e = cudaMemsetAsync(A.queue, 0, sizeof(unsigned long long), stream);
+    e = cudaMemsetAsync(A.J.queue, 0, sizeof(unsigned long long), stream);
     if (e != cudaSuccess) return cuda_fail(e, "clearing the static work counter");
     fn<<<grid, plan.block, plan.smem, stream>>>(A);
     e = cudaGetLastError();
@@ -927,5 +607,294 @@ extern "C" ngdbf_status ngdbf_decode_noalloc(const ngdbf_code_t* C, const float*
     g_last_launch.state_in_smem = plan.st_smem ? 1 : 0;
     g_last_launch.kernels = 1;
     g_last_launch.sm_count = sm_count;
+    return NGDBF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Job tables: several decode jobs in one persistent launch (ngdbf_multi.cu).
+// ---------------------------------------------------------------------------
+
+#include "ngdbf_multi.h"
+
+struct ngdbf_batch {
+    int device = 0, n_jobs = 0, sm_count = 0;
+    void* fn = nullptr;                 // job-table kernel
+    int grid = 0, block = 0, smem = 0, state_in_smem = 0;
+    MultiArgs args;
+    unsigned char* d_mem = nullptr;     // jobs | thresholds | queues | first_job | samples | state
+    unsigned long long* d_queues = nullptr;
+    int32_t* d_first = nullptr;
+    std::vector<int64_t> frames, weight;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+namespace {
+
+size_t align256(size_t v) { return (v + 255) / 256 * 256; }
+
+// First job of every CTA: CTAs in proportion to the estimated work of each job
+// (frames x n x (T + 1)), at least one CTA per job with frames, at most one CTA
+// per 32 of its frames; CTAs left over go to the jobs with the most work per CTA.
+std::vector<int32_t> assign_ctas(const ngdbf_batch& B, int grid) {
+    const int J = B.n_jobs;
+    std::vector<int64_t> cap(J), cnt(J, 0);
+    double total = 0;
+    for (int j = 0; j < J; ++j) {
+        cap[j] = (B.frames[j] + kSlots - 1) / kSlots;
+        total += (double)B.weight[j];
+    }
+    int used = 0;
+    for (int j = 0; j < J; ++j) {
+        if (B.frames[j] == 0) continue;
+        int64_t c = (int64_t)std::floor((double)grid * (double)B.weight[j] / std::max(total, 1.0));
+        cnt[j] = std::min(std::max<int64_t>(c, 1), cap[j]);
+        used += (int)cnt[j];
+    }
+    while (used > grid) {                       // more jobs than CTAs: trim the lightest loads
+        int pick = -1;
+        double best = 1e300;
+        for (int j = 0; j < J; ++j)
+            if (cnt[j] > 1 || (cnt[j] == 1 && used > grid)) {
+                const double per = (double)B.weight[j] / (double)cnt[j];
+                if (cnt[j] > 0 && per < best) { best = per; pick = j; }
+            }
+        if (pick < 0) break;
+        cnt[pick] -= 1;
+        used -= 1;
+    }
+    while (used < grid) {
+        int pick = -1;
+        double best = -1;
+        for (int j = 0; j < J; ++j)
+            if (cnt[j] < cap[j]) {
+                const double per = (double)B.weight[j] / (double)(cnt[j] + 1);
+                if (per > best) { best = per; pick = j; }
+            }
+        if (pick < 0) break;
+        cnt[pick] += 1;
+        used += 1;
+    }
+    std::vector<int32_t> first;
+    first.reserve(grid);
+    for (int j = 0; j < J; ++j)
+        for (int64_t c = 0; c < cnt[j]; ++c) first.push_back(j);
+    while ((int)first.size() < grid) first.push_back(-1);   // no frames left to start on
+    return first;
+}
+
+cudaError_t batch_enqueue(ngdbf_batch* B, cudaStream_t stream) {
+    cudaError_t e = cudaMemsetAsync(B->d_queues, 0, sizeof(unsigned long long) * B->n_jobs, stream);
+    if (e != cudaSuccess) return e;
+    return launch_multi(B->fn, B->args, B->grid, B->block, B->smem, stream);
+}
+
+ngdbf_status batch_set_shape(ngdbf_batch* B, int block, int bps) {
+    B->block = block;
+    int64_t groups = 0;
+    for (int j = 0; j < B->n_jobs; ++j) groups += (B->frames[j] + kSlots - 1) / kSlots;
+    B->grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)B->sm_count * bps, groups));
+    std::vector<int32_t> first = assign_ctas(*B, B->grid);
+    cudaError_t e = cudaMemcpy(B->d_first, first.data(), first.size() * 4, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "job table: first jobs");
+    return NGDBF_OK;
+}
+
+void batch_free(ngdbf_batch* B) {
+    if (!B) return;
+    if (B->exec) cudaGraphExecDestroy(B->exec);
+    if (B->graph) cudaGraphDestroy(B->graph);
+    if (B->d_mem) cudaFree(B->d_mem);
+    delete B;
+}
+
+}  // namespace
+
+extern "C" ngdbf_status ngdbf_batch_create(const ngdbf_job* jobs, int32_t n_jobs, uint64_t seed, int32_t flags,
+                                           void* stream_ptr, ngdbf_batch_t** out) {
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_ptr);
+    if (!out) return fail(NGDBF_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!jobs || n_jobs < 1) return fail(NGDBF_ERR_INVALID_ARG, "need at least one job");
+    if (flags & ~(NGDBF_BATCH_TUNE | NGDBF_BATCH_GRAPH)) return fail(NGDBF_ERR_INVALID_ARG, "unknown flags");
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    const int variant = jobs[0].params.variant, precision = jobs[0].params.precision;
+    int n_max = 0, m_max = 0, t_max = 0, dv_max = 0, dc_max = 0;
+    size_t thr_words = 0;
+    for (int j = 0; j < n_jobs; ++j) {
+        const ngdbf_job& q = jobs[j];
+        if (!q.code) return fail(NGDBF_ERR_INVALID_ARG, "job without a code");
+        ngdbf_status s = check_params(&q.params, q.sigma);
+        if (s != NGDBF_OK) return s;
+        if (q.params.variant != variant || q.params.precision != precision)
+            return fail(NGDBF_ERR_UNSUPPORTED, "jobs of one table must share variant and precision");
+        if (q.code->device != dev) return fail(NGDBF_ERR_INVALID_ARG, "code tables belong to another device");
+        if (q.n_frames < 0) return fail(NGDBF_ERR_INVALID_ARG, "n_frames < 0");
+        if (q.n_frames > 0) {
+            if (!q.y || !q.bits || !q.iters || !q.pass) return fail(NGDBF_ERR_INVALID_ARG, "NULL buffer");
+            for (const void* p : {(const void*)q.y, (const void*)q.bits, (const void*)q.iters, (const void*)q.pass}) {
+                cudaPointerAttributes a;
+                e = cudaPointerGetAttributes(&a, p);
+                if (e != cudaSuccess || !(a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged)) {
+                    cudaGetLastError();
+                    return fail(NGDBF_ERR_INVALID_ARG, "job buffers must be device memory");
+                }
+            }
+        }
+        n_max = std::max(n_max, q.code->n);
+        m_max = std::max(m_max, q.code->m);
+        t_max = std::max(t_max, q.params.t_max);
+        dv_max = std::max(dv_max, q.code->dv_max);
+        dc_max = std::max(dc_max, q.code->dc_max);
+        thr_words += (size_t)q.params.t_max + 1;
+    }
+    ngdbf_batch* B = new (std::nothrow) ngdbf_batch;
+    if (!B) return fail(NGDBF_ERR_OOM, "host allocation");
+    B->device = dev;
+    B->n_jobs = n_jobs;
+    int smem_optin = 0;
+    e = cudaDeviceGetAttribute(&B->sm_count, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) { batch_free(B); return cuda_fail(e, "cudaDeviceGetAttribute"); }
+    // shared memory for the largest code and T; state, then tables, move out when needed
+    const bool state = (variant & 3) != 0, adapt = (variant & NGDBF_ADAPT) != 0, wide = dv_max > 7;
+    bool st_smem = state, tables_smem = true;
+    auto layout = [&]() { return smem_layout(n_max, m_max, t_max, dv_max, dc_max, adapt, st_smem, tables_smem); };
+    void* fn = multi_kernel_fn(variant, precision, st_smem, wide);
+    cudaFuncAttributes fa;
+    e = cudaFuncGetAttributes(&fa, fn);
+    if (e != cudaSuccess) { batch_free(B); return cuda_fail(e, "cudaFuncGetAttributes"); }
+    const int limit = smem_optin - (int)fa.sharedSizeBytes;
+    SmemLayout L = layout();
+    if (L.total > limit) { tables_smem = false; L = layout(); }
+    if (L.total > limit && st_smem) {
+        st_smem = false; tables_smem = true; L = layout();
+        if (L.total > limit) { tables_smem = false; L = layout(); }
+    }
+    if (L.total > limit) { batch_free(B); return fail(NGDBF_ERR_UNSUPPORTED, "largest code too large for shared memory"); }
+    fn = multi_kernel_fn(variant, precision, st_smem, wide);
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, L.total);
+    if (e != cudaSuccess) { batch_free(B); return cuda_fail(e, "cudaFuncSetAttribute"); }
+    B->fn = fn;
+    B->smem = L.total;
+    B->state_in_smem = st_smem ? 1 : 0;
+    // candidate block sizes and the largest grid any of them needs
+    std::vector<std::pair<int, int>> shapes;
+    int max_bps = 0;
+    for (int block : {1024, 512, 256}) {
+        int bps = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, (const void*)fn, block, L.total);
+        if (e != cudaSuccess) { batch_free(B); return cuda_fail(e, "occupancy"); }
+        if (bps > 0) { shapes.push_back({block, bps}); max_bps = std::max(max_bps, bps); }
+    }
+    if (shapes.empty()) { batch_free(B); return fail(NGDBF_ERR_UNSUPPORTED, "job-table kernel does not fit on an SM"); }
+    const size_t grid_max = (size_t)B->sm_count * max_bps;
+    const size_t per_slot_y = (size_t)n_max * kSlots * held_bytes(precision);
+    const size_t per_slot_st = (state && !st_smem) ? (size_t)n_max * kSlots * 2 : 0;
+    const size_t off_jobs = 0, off_thr = align256(sizeof(Job) * n_jobs), off_q = off_thr + align256(thr_words * 4);
+    const size_t off_first = off_q + align256(8 * (size_t)n_jobs), off_y = off_first + align256(4 * grid_max);
+    const size_t off_st = off_y + align256(grid_max * per_slot_y);
+    const size_t total = off_st + align256(grid_max * per_slot_st);
+    e = cudaMalloc(&B->d_mem, total);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        batch_free(B);
+        return fail(e == cudaErrorMemoryAllocation ? NGDBF_ERR_OOM : NGDBF_ERR_CUDA, "job table scratch");
+    }
+    B->d_queues = reinterpret_cast<unsigned long long*>(B->d_mem + off_q);
+    B->d_first = reinterpret_cast<int32_t*>(B->d_mem + off_first);
+    // job table and thresholds
+    std::vector<Job> hjobs(n_jobs);
+    std::vector<uint32_t> hthr(thr_words);
+    size_t tpos = 0;
+    B->frames.resize(n_jobs);
+    B->weight.resize(n_jobs);
+    for (int j = 0; j < n_jobs; ++j) {
+        const ngdbf_job& q = jobs[j];
+        fill_job(q.code, &q.params, q.y, q.n_frames, q.sigma, q.frame_offset, q.bits, q.iters, q.pass,
+                 B->d_queues + j, &hjobs[j], hthr.data() + tpos);
+        hjobs[j].thr = reinterpret_cast<const uint32_t*>(B->d_mem + off_thr) + tpos;
+        tpos += (size_t)q.params.t_max + 1;
+        B->frames[j] = q.n_frames;
+        B->weight[j] = q.n_frames * (int64_t)q.code->n * (q.params.t_max + 1);
+    }
+    e = cudaMemcpy(B->d_mem + off_jobs, hjobs.data(), sizeof(Job) * n_jobs, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(B->d_mem + off_thr, hthr.data(), hthr.size() * 4, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) { batch_free(B); return cuda_fail(e, "job table upload"); }
+    MultiArgs& A = B->args;
+    std::memset(&A, 0, sizeof(A));
+    A.jobs = reinterpret_cast<const Job*>(B->d_mem + off_jobs);
+    A.n_jobs = n_jobs;
+    A.first_job = B->d_first;
+    A.n_max = n_max; A.m_max = m_max; A.t_max = t_max; A.dv_max = dv_max; A.dc_max = dc_max;
+    A.tables_smem = tables_smem ? 1 : 0;
+    A.yslots = B->d_mem + off_y;
+    A.st_global = per_slot_st ? reinterpret_cast<uint16_t*>(B->d_mem + off_st) : nullptr;
+    host_gen_consts(seed, A.G);
+    // launch shape: the largest block by default, or the fastest candidate on this table
+    ngdbf_status s = batch_set_shape(B, shapes[0].first, shapes[0].second);
+    if (s == NGDBF_OK && (flags & NGDBF_BATCH_TUNE) && shapes.size() > 1) {
+        cudaEvent_t t0, t1;
+        cudaEventCreate(&t0);
+        cudaEventCreate(&t1);
+        float best = 1e30f;
+        std::pair<int, int> best_shape = shapes[0];
+        for (const auto& sh : shapes) {
+            s = batch_set_shape(B, sh.first, sh.second);
+            if (s != NGDBF_OK) break;
+            e = batch_enqueue(B, stream);                    // warm-up
+            if (e == cudaSuccess) e = cudaEventRecord(t0, stream);
+            if (e == cudaSuccess) e = batch_enqueue(B, stream);
+            if (e == cudaSuccess) e = cudaEventRecord(t1, stream);
+            if (e == cudaSuccess) e = cudaEventSynchronize(t1);
+            if (e != cudaSuccess) { s = cuda_fail(e, "tuning launch"); break; }
+            float ms = 0;
+            cudaEventElapsedTime(&ms, t0, t1);
+            if (ms < best) { best = ms; best_shape = sh; }
+        }
+        cudaEventDestroy(t0);
+        cudaEventDestroy(t1);
+        if (s == NGDBF_OK) s = batch_set_shape(B, best_shape.first, best_shape.second);
+    }
+    if (s != NGDBF_OK) { batch_free(B); return s; }
+    if (flags & NGDBF_BATCH_GRAPH) {
+        cudaStream_t cs;
+        e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            cudaError_t le = batch_enqueue(B, cs);
+            e = cudaStreamEndCapture(cs, &B->graph);
+            if (le != cudaSuccess) e = le;
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&B->exec, B->graph, 0);
+        cudaStreamDestroy(cs);
+        if (e != cudaSuccess) { batch_free(B); return cuda_fail(e, "graph capture of the job table"); }
+    }
+    *out = B;
+    return NGDBF_OK;
+}
+
+extern "C" ngdbf_status ngdbf_batch_launch(ngdbf_batch_t* B, void* stream_ptr) {
+    if (!B) return fail(NGDBF_ERR_INVALID_ARG, "batch is NULL");
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_ptr);
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev != B->device) return fail(NGDBF_ERR_INVALID_ARG, "batch belongs to another device");
+    e = B->exec ? cudaGraphLaunch(B->exec, stream) : batch_enqueue(B, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "job table launch");
+    g_last_launch.grid = B->grid;
+    g_last_launch.block = B->block;
+    g_last_launch.smem_bytes = B->smem;
+    g_last_launch.state_in_smem = B->state_in_smem;
+    g_last_launch.kernels = 1;
+    g_last_launch.sm_count = B->sm_count;
+    return NGDBF_OK;
+}
+
+extern "C" ngdbf_status ngdbf_batch_destroy(ngdbf_batch_t* B) {
+    batch_free(B);
     return NGDBF_OK;
 }

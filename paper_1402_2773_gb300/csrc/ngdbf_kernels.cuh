@@ -1,0 +1,485 @@
+// ngdbf_kernels.cuh -- shared device code of the NGDBF decoder (sm_103a): job and launch
+// descriptors, the shared-memory layout and the persistent slot loop for one job.
+//
+// Work decomposition.  A CTA owns 32 frame slots, one per bit of a 32-bit
+// word: the decisions x_k of its 32 frames are one word per symbol k and the
+// syndromes s_i one word per check i (bit f set <=> x_k = -1 / check i
+// unsatisfied for slot f).  Each round the CTA
+//   A. forms every syndrome word as the XOR of the d_c decision words of a
+//      check (Sec. III-A, Step 1 of Sec. III-B), OR-reduces them to the
+//      "some check unsatisfied" mask with warp reductions,
+//   B. retires slots whose frame satisfied every check (pass) or reached T
+//      (smoothed output, Sec. III-E), writes their outputs, takes new frames
+//      from a global atomic queue for them and loads those frames,
+//   A'. adds, per symbol, the syndrome words of M(k) into a bit-sliced counter
+//      of unsatisfied checks (shared by the 32 slots), then
+//   C. runs Step 2 / Step 3b for every symbol of every live slot: a warp
+//      processes four symbols (one Philox call) at a time with lane = slot,
+//      reads the lane's count, forms E_k = x_k y_k + w S_k + q_k, compares it
+//      with theta lambda^{u_k}, adapts u_k, accumulates the smoothing counter,
+//      and rebuilds the decision word with a warp ballot.
+// Slots therefore iterate independently (each frame has its own t), a
+// converged frame frees its slot at once, and the CTA only stops when the
+// queue is empty and its last slot finished.
+//
+// Per-(symbol, slot) state: the held sample (global scratch laid out
+// [k][slot], L2-resident), and a 16-bit word holding u_k (bits 0-8) and
+// the number of -1 decisions inside the smoothing window (bits 9-15), in
+// shared memory when it fits, else in global scratch.  Decision and syndrome
+// words, the code adjacency, and the threshold table live in shared memory.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+
+#include "../../include/ngdbf.h"
+#include "ngdbf_device.cuh"
+
+namespace ngdbf {
+
+constexpr int kSlots = 32;
+constexpr int kMaxT = NGDBF_MAX_T;
+constexpr uint32_t kUMask = 0x1FFu;   // u_k: bits 0-8
+constexpr int kCShift = 9;            // smoothing count: bits 9-15
+
+// Arithmetic of the held samples and of E_k (Sec. IV-E): the perturbation is
+// always the FP32 generator output.
+enum Precision { kFP32 = 0, kFP16 = 1, kFIX = 2 };
+
+template <int PREC> struct Held;
+template <> struct Held<kFP32> { using T = float; };
+template <> struct Held<kFP16> { using T = __half; };
+template <> struct Held<kFIX> { using T = int8_t; };   // signed level code b, value 2b + 1
+
+// One decode job: a code, a batch of frames and the parameters of the method.
+struct Job {
+    // code tables (device)
+    int32_t n, m, dv_max, dc_max;
+    const uint16_t* chk_cols;   // [dc_max][m]   N(i) column-major, padded with n
+    const uint16_t* sym_chks;   // [n][dv_max]   M(k) row-major, padded with m
+    const uint8_t* sym_deg;     // [n]           d_v(k)
+    // batch
+    const float* y;             // [n_frames][n]
+    int64_t n_frames;
+    uint64_t frame_offset;
+    uint8_t* bits;              // [n_frames][nb]
+    int32_t* iters;
+    uint8_t* pass;
+    int32_t nb;
+    // parameters
+    float w, scale, y_max;      // w: FP32 value, or its binary16 value for FP16
+    int32_t clamp, t_max, t_smooth;   // t_smooth = max(0, T - W)
+    float fix_R;                // fixed point: fl32(2^Q / (2 Y_max)), kmax = 2^(Q-1) - 1, W~
+    int32_t fix_kmax, fix_W;
+    // thresholds theta lambda^u, u = 0..T: FP32 bits, binary16 values as FP32 bits, or
+    // fixed-point levels Theta~(u) as int32 (device memory; the single-job launch passes
+    // them inline instead)
+    const uint32_t* thr;
+    unsigned long long* queue;  // next unclaimed frame of this job
+};
+
+// Launch of one job: the job and its thresholds travel as kernel parameters.
+struct DecodeArgs {
+    Job J;
+    int32_t tables_smem;        // copy the adjacency tables into shared memory
+    void* yslots;               // [grid][n][32] held samples (4, 2 or 1 bytes each)
+    uint16_t* st_global;        // [grid][n][32] when the state is not in shared memory
+    GenConsts G;
+    uint32_t thr[kMaxT + 1];
+};
+
+// Launch of a job table: CTA c starts with job first_job[c] and, once that job has
+// no unclaimed frame left and its slots are idle, moves to the job with the most
+// unclaimed frames.  Shared memory is laid out for the largest code and T.
+struct MultiArgs {
+    const Job* jobs;
+    int32_t n_jobs;
+    const int32_t* first_job;   // [grid]
+    int32_t n_max, m_max, t_max, dv_max, dc_max;   // layout maxima over the jobs
+    int32_t tables_smem;
+    void* yslots;               // [grid][n_max][32]
+    uint16_t* st_global;        // [grid][n_max][32] when the state is not in shared memory
+    GenConsts G;
+};
+
+struct SmemLayout {
+    int32_t off_frame, off_start, off_ctl, off_xw, off_sw, off_cnt, off_thr, off_st, off_chk, off_sym, total;
+};
+
+// Offsets in bytes of the shared-memory arrays.  ctl holds: [0..1] unsatisfied
+// masks (double-buffered by pass parity), [2] live mask, [3] new-slot mask.
+// cnt holds per symbol the bit-sliced count of unsatisfied checks (one word per
+// count bit, bit f for slot f) and d_v(k): 3 slices + degree in 16 bytes when
+// d_v <= 7 (narrow), 7 slices + degree in 32 bytes otherwise (wide).
+__host__ __device__ inline SmemLayout smem_layout(int n, int m, int t_max, int dv_max, int dc_max,
+                                                  bool need_thr, bool st_smem, bool tables_smem) {
+    SmemLayout L;
+    int o = 0;
+    auto take = [&](int bytes, int align) {
+        o = (o + align - 1) / align * align;
+        int r = o;
+        o += bytes;
+        return r;
+    };
+    const int cnt_bytes = dv_max <= 7 ? 16 : 32;
+    L.off_frame = take(kSlots * 8, 16);
+    L.off_start = take(kSlots * 4, 16);
+    L.off_ctl = take(8 * 4, 16);
+    L.off_cnt = take(n * cnt_bytes, 16);
+    L.off_xw = take((n + 1) * 4, 16);
+    L.off_sw = take((m + 1) * 4, 16);
+    L.off_thr = need_thr ? take((t_max + 1) * 4, 16) : -1;
+    L.off_st = st_smem ? take(n * kSlots * 2, 16) : -1;
+    L.off_chk = tables_smem ? take(dc_max * m * 2, 16) : -1;
+    L.off_sym = tables_smem ? take(n * dv_max * 2 + n, 16) : -1;
+    L.total = (o + 15) / 16 * 16;
+    return L;
+}
+
+// Signed fixed-point level code of v (Eq. 8): k = min(floor(|v| R), kmax) decided in FP32,
+// b = k for v >= 0 and -k - 1 otherwise; the level's value is 2b + 1 in units of Delta/2.
+__host__ __device__ inline int32_t fix_code(float v, float R, int32_t kmax) {
+#ifdef __CUDA_ARCH__
+    const float a = __fmul_rn(fabsf(v), R);
+    const int32_t k = (a < (float)kmax) ? __float2int_rd(a) : kmax;
+#else
+    const float a = std::fabs(v) * R;
+    const int32_t k = (a < (float)kmax) ? (int32_t)std::floor(a) : kmax;
+#endif
+    return v >= 0.0f ? k : -k - 1;
+}
+
+// Rounds an FP32 value to binary16 (nearest even) and back.
+__device__ __forceinline__ float to_half(float v) { return __half2float(__float2half_rn(v)); }
+
+// Position of the (j+1)-th set bit of mask (j < popc(mask)).
+__device__ __forceinline__ int nth_set_bit(uint32_t mask, int j) {
+    for (int i = 0; i < j; ++i) mask &= mask - 1u;
+    return __ffs(mask) - 1;
+}
+
+// The slot loop for one job (rows a0-a8 of the method): CTA-wide, returns when the job
+// has no unclaimed frame left and every slot of this CTA is idle.  `A` is the job (kernel
+// parameters or a shared-memory copy), `thr_src` its thresholds, `L` the shared-memory
+// layout of the launch, `ys`/`st_cta` this CTA's slot scratch.
+template <bool ADAPT, bool SMOOTH, bool ST_SMEM, bool WIDE, int PREC>
+__device__ __forceinline__ void decode_job(const Job& A, const uint32_t* thr_src, const GenConsts& G,
+                                           const SmemLayout& L, bool tables_smem,
+                                           typename Held<PREC>::T* ys, uint16_t* st_cta) {
+    constexpr bool kState = ADAPT || SMOOTH;
+    using HeldT = typename Held<PREC>::T;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int n = A.n, m = A.m, T = A.t_max, dv_max = A.dv_max, dc_max = A.dc_max;
+    long long* lane_frame = reinterpret_cast<long long*>(smem + L.off_frame);
+    int32_t* lane_start = reinterpret_cast<int32_t*>(smem + L.off_start);
+    uint32_t* ctl = reinterpret_cast<uint32_t*>(smem + L.off_ctl);
+    uint4* cnt = reinterpret_cast<uint4*>(smem + L.off_cnt);
+    uint32_t* xw = reinterpret_cast<uint32_t*>(smem + L.off_xw);
+    uint32_t* sw = reinterpret_cast<uint32_t*>(smem + L.off_sw);
+    uint32_t* thr = ADAPT ? reinterpret_cast<uint32_t*>(smem + L.off_thr) : nullptr;
+    uint16_t* st = nullptr;
+    if constexpr (kState) {
+        st = ST_SMEM ? reinterpret_cast<uint16_t*>(smem + L.off_st) : st_cta;
+    }
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+    // adjacency tables: only phases A and A' read them, so a generic pointer to
+    // shared or global memory serves both placements
+    const uint16_t* chk_cols = A.chk_cols;
+    const uint16_t* sym_chks = A.sym_chks;
+    const uint8_t* sym_deg = A.sym_deg;
+    if (tables_smem) {
+        uint16_t* c = reinterpret_cast<uint16_t*>(smem + L.off_chk);
+        uint16_t* s = reinterpret_cast<uint16_t*>(smem + L.off_sym);
+        uint8_t* d = reinterpret_cast<uint8_t*>(s + n * dv_max);
+        for (int i = tid; i < dc_max * m; i += blockDim.x) c[i] = A.chk_cols[i];
+        for (int i = tid; i < n * dv_max; i += blockDim.x) s[i] = A.sym_chks[i];
+        for (int i = tid; i < n; i += blockDim.x) d[i] = A.sym_deg[i];
+        chk_cols = c;
+        sym_chks = s;
+        sym_deg = d;
+    }
+
+    // ---- set-up: zero the state, sentinels, thresholds, first 32 frames ----
+    for (int k = tid; k <= n; k += blockDim.x) xw[k] = 0u;
+    for (int i = tid; i <= m; i += blockDim.x) sw[i] = 0u;
+    if constexpr (ADAPT)
+        for (int u = tid; u <= T; u += blockDim.x) thr[u] = thr_src[u];
+    if constexpr (kState)
+        for (int e = tid; e < n * kSlots; e += blockDim.x) st[e] = 0;
+    if (tid == 0) {
+        for (int c = 0; c < 8; ++c) ctl[c] = 0u;
+        const unsigned long long base = atomicAdd(A.queue, (unsigned long long)kSlots);
+        uint32_t live = 0;
+        for (int f = 0; f < kSlots; ++f) {
+            const unsigned long long fid = base + f;
+            lane_start[f] = 0;
+            if (fid < (unsigned long long)A.n_frames) {
+                lane_frame[f] = (long long)fid;
+                live |= 1u << f;
+            } else {
+                lane_frame[f] = -1;
+            }
+        }
+        ctl[2] = live;
+        ctl[3] = live;
+    }
+    __syncthreads();
+
+    int round = 0;   // flip phases executed by this CTA; slot f is at t = round - lane_start[f]
+    int pass_id = 0;
+    bool refill = true;
+    for (;;) {
+        if (refill) {
+            // ---- load new frames: saturated samples into the slot columns, x(0) = sign(y) ----
+            const uint32_t fresh = ctl[3];
+            for (int k = tid; k < n; k += blockDim.x) {
+                uint32_t word = xw[k] & ~fresh;
+                uint32_t rest = fresh;
+                while (rest) {
+                    const int f = __ffs(rest) - 1;
+                    rest &= rest - 1;
+                    float v = __ldg(A.y + (size_t)lane_frame[f] * n + k);
+                    if (A.clamp) {
+                        if (v > A.y_max) v = A.y_max;
+                        if (v < -A.y_max) v = -A.y_max;
+                    }
+                    bool negative;
+                    if constexpr (PREC == kFP32) {
+                        ys[k * kSlots + f] = v;
+                        negative = !(v >= 0.0f);
+                    } else if constexpr (PREC == kFP16) {
+                        const __half h = __float2half_rn(v);
+                        ys[k * kSlots + f] = h;
+                        negative = !(__half2float(h) >= 0.0f);        // sign(-0) = +1
+                    } else {
+                        const int32_t b = fix_code(v, A.fix_R, A.fix_kmax);
+                        ys[k * kSlots + f] = (int8_t)b;
+                        negative = b < 0;
+                    }
+                    if (negative) word |= 1u << f;
+                    if constexpr (kState) st[k * kSlots + f] = 0;
+                }
+                xw[k] = word;
+            }
+            __syncthreads();
+            refill = false;
+        }
+
+        // ---- A. syndromes (four threads XOR a quarter of a check each) and the vote ----
+        {
+            uint32_t* unsat = ctl + (pass_id & 1);
+            if (tid == 0) ctl[(pass_id + 1) & 1] = 0u;
+            uint32_t acc = 0;
+            const int per_pass = blockDim.x >> 2, sub = tid & 3;
+            for (int base = 0; base < m; base += per_pass) {
+                const int i = base + (tid >> 2);
+                uint32_t s = 0;
+                if (i < m)
+                    for (int j = sub; j < dc_max; j += 4) s ^= xw[chk_cols[j * m + i]];
+                s ^= __shfl_xor_sync(0xFFFFFFFFu, s, 1);
+                s ^= __shfl_xor_sync(0xFFFFFFFFu, s, 2);
+                if (i < m && sub == 0) sw[i] = s;
+                acc |= s;
+            }
+            acc = __reduce_or_sync(0xFFFFFFFFu, acc);
+            if (lane == 0 && acc) atomicOr(unsat, acc);
+            __syncthreads();
+        }
+        const uint32_t unsat = ctl[pass_id & 1];
+        ++pass_id;
+        uint32_t live = ctl[2];
+        const uint32_t conv = live & ~unsat;
+        const int my_t = round - lane_start[lane];
+        const uint32_t at_T = __ballot_sync(0xFFFFFFFFu, ((live >> lane) & 1u) && my_t >= T);
+        const uint32_t fin = conv | (live & at_T);
+
+        if (fin) {
+            // ---- B. outputs of finished slots ----
+            const int nfin = __popc(fin);
+            const int work = nfin * A.nb;
+            for (int idx = tid; idx < work; idx += blockDim.x) {
+                const int j = idx / A.nb, b = idx - j * A.nb;
+                const int f = nth_set_bit(fin, j);
+                const bool ok = (conv >> f) & 1u;
+                const int tf = round - lane_start[f];
+                uint32_t byte = 0;
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const int k = 8 * b + q;
+                    if (k < n) {
+                        uint32_t bit = (xw[k] >> f) & 1u;
+                        if constexpr (SMOOTH) {
+                            if (!ok) {
+                                // X_k = terms - 2 * (#-1 decisions), x(T) included here
+                                const int terms = tf - A.t_smooth + 1;
+                                const int neg = (int)(st[k * kSlots + f] >> kCShift) + (int)bit;
+                                const int X = terms - 2 * neg;
+                                bit = X < 0 ? 1u : (X > 0 ? 0u : bit);
+                            }
+                        }
+                        byte |= bit << q;
+                    }
+                }
+                A.bits[(size_t)lane_frame[f] * A.nb + b] = (uint8_t)byte;
+            }
+            if (tid < nfin) {
+                const int f = nth_set_bit(fin, tid);
+                const bool ok = (conv >> f) & 1u;
+                const long long fr = lane_frame[f];
+                A.iters[fr] = ok ? round - lane_start[f] : T;
+                A.pass[fr] = ok ? 1 : 0;
+            }
+            __syncthreads();
+            // ---- claim new frames for the finished slots ----
+            if (tid == 0) {
+                uint32_t fresh = 0;
+                const unsigned long long base = atomicAdd(A.queue, (unsigned long long)nfin);
+                for (int j = 0; j < nfin; ++j) {
+                    const int f = nth_set_bit(fin, j);
+                    const unsigned long long fid = base + j;
+                    if (fid < (unsigned long long)A.n_frames) {
+                        lane_frame[f] = (long long)fid;
+                        lane_start[f] = round;
+                        fresh |= 1u << f;
+                    } else {
+                        lane_frame[f] = -1;
+                    }
+                }
+                ctl[2] = (live & ~fin) | fresh;
+                ctl[3] = fresh;
+            }
+            __syncthreads();
+            live = ctl[2];
+            if (ctl[3]) {
+                refill = true;      // new frames need their t = 0 syndrome test first
+                continue;
+            }
+        }
+        if (live == 0) break;
+
+        // ---- A'. per symbol, the bit-sliced count of unsatisfied checks in M(k) ----
+        for (int k = tid; k < n; k += blockDim.x) {
+            const uint16_t* row = sym_chks + k * dv_max;
+            if constexpr (!WIDE) {
+                uint32_t b0 = 0, b1 = 0, b2 = 0;           // count <= 7: three slices
+                for (int e = 0; e < dv_max; ++e) {
+                    const uint32_t s = sw[row[e]];
+                    const uint32_t c0 = b0 & s;
+                    b0 ^= s;
+                    const uint32_t c1 = b1 & c0;
+                    b1 ^= c0;
+                    b2 ^= c1;
+                }
+                cnt[k] = make_uint4(b0, b1, b2, (uint32_t)sym_deg[k]);
+            } else {
+                uint32_t b[7] = {0, 0, 0, 0, 0, 0, 0};     // count <= 127: seven slices
+                for (int e = 0; e < dv_max; ++e) {
+                    uint32_t carry = sw[row[e]];
+#pragma unroll
+                    for (int q = 0; q < 7; ++q) {
+                        const uint32_t c = b[q] & carry;
+                        b[q] ^= carry;
+                        carry = c;
+                    }
+                }
+                cnt[2 * k] = make_uint4(b[0], b[1], b[2], b[3]);
+                cnt[2 * k + 1] = make_uint4(b[4], b[5], b[6], (uint32_t)sym_deg[k]);
+            }
+        }
+        __syncthreads();
+
+        // ---- C. Step 2 and Step 3b for every symbol of every live slot ----
+        {
+            const bool act = (live >> lane) & 1u;
+            const long long fr = lane_frame[lane];
+            const uint64_t fid = A.frame_offset + (uint64_t)(act ? fr : 0);
+            const uint32_t flo = (uint32_t)fid, fhi = (uint32_t)(fid >> 32);
+            const int t = act ? round - lane_start[lane] : 0;
+            const bool window = SMOOTH && act && t >= A.t_smooth;
+            const int groups = (n + 3) >> 2;
+            const uint32_t th0 = thr_src[0];    // threshold of the non-adaptive variants
+            const float scale = A.scale, wgt = A.w, fix_R = A.fix_R;
+            const int32_t fix_kmax = A.fix_kmax, fix_W = A.fix_W;
+            for (int g = warp; g < groups; g += nwarps) {
+                const int k0 = 4 * g;
+                // issue the sample and state loads before the generator's arithmetic
+                HeldT yv[4];
+                uint32_t sv[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const bool in = k0 + j < n;
+                    yv[j] = in ? ys[(k0 + j) * kSlots + lane] : HeldT(0);
+                    if constexpr (kState) sv[j] = in ? (uint32_t)st[(k0 + j) * kSlots + lane] : 0u;
+                }
+                float z[4];
+                gauss4((uint32_t)g, (uint32_t)t, flo, fhi, G, z);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int k = k0 + j;
+                    if (k >= n) break;
+                    int unsat_cnt, deg;
+                    if constexpr (!WIDE) {
+                        const uint4 c = cnt[k];
+                        unsat_cnt = (int)(((c.x >> lane) & 1u) | (((c.y >> lane) & 1u) << 1) |
+                                          (((c.z >> lane) & 1u) << 2));
+                        deg = (int)c.w;
+                    } else {
+                        const uint4 c = cnt[2 * k], d = cnt[2 * k + 1];
+                        unsat_cnt = (int)(((c.x >> lane) & 1u) | (((c.y >> lane) & 1u) << 1) |
+                                          (((c.z >> lane) & 1u) << 2) | (((c.w >> lane) & 1u) << 3) |
+                                          (((d.x >> lane) & 1u) << 4) | (((d.y >> lane) & 1u) << 5) |
+                                          (((d.z >> lane) & 1u) << 6));
+                        deg = (int)d.w;
+                    }
+                    const int S = deg - 2 * unsat_cnt;
+                    const uint32_t xword = xw[k];
+                    const bool xneg = (xword >> lane) & 1u;
+                    const float q = __fmul_rn(scale, z[j]);
+                    // below_threshold(u): E_k < theta_k in the held arithmetic
+                    auto below = [&](uint32_t th_bits) -> bool {
+                        if constexpr (PREC == kFP32) {
+                            return inversion_metric(xneg, yv[j], S, wgt, q) < __uint_as_float(th_bits);
+                        } else if constexpr (PREC == kFP16) {
+                            // each result rounded to binary16 (one FP32 operation on binary16
+                            // operands, then one rounding, is the binary16 operation)
+                            const float y16 = __half2float(yv[j]);
+                            const float xy = xneg ? -y16 : y16;
+                            const float ws = to_half(__fmul_rn(wgt, __int2float_rn(S)));
+                            const float e1 = to_half(__fadd_rn(xy, ws));
+                            const float E = to_half(__fadd_rn(e1, to_half(q)));
+                            return E < __uint_as_float(th_bits);
+                        } else {
+                            // Eq. 9 in units of Delta/2, exact integers
+                            const int32_t Y = 2 * (int32_t)yv[j] + 1;
+                            const int32_t Qv = 2 * fix_code(q, fix_R, fix_kmax) + 1;
+                            return (xneg ? -Y : Y) + fix_W * S + Qv < (int32_t)th_bits;
+                        }
+                    };
+                    bool flip;
+                    if constexpr (kState) {
+                        const uint32_t s0 = sv[j];
+                        // u_k <= t - 1 < T for a live slot (cleared on every refill)
+                        const uint32_t th = ADAPT ? thr[s0 & kUMask] : th0;
+                        const bool lower = below(th);       // evaluated for every lane, no branch
+                        flip = act && lower;
+                        const uint32_t nv = s0 + ((ADAPT && act && !flip) ? 1u : 0u) +
+                                            ((window && xneg) ? (1u << kCShift) : 0u);
+                        if (nv != s0) st[k * kSlots + lane] = (uint16_t)nv;
+                    } else {
+                        const bool lower = below(th0);
+                        flip = act && lower;
+                    }
+                    const uint32_t fm = __ballot_sync(0xFFFFFFFFu, flip);
+                    if (lane == 0 && fm) xw[k] = xword ^ fm;
+                }
+            }
+        }
+        __syncthreads();
+        ++round;
+    }
+}
+
+}  // namespace ngdbf

@@ -1,0 +1,18 @@
+// ngdbf_multi.h -- host-side entry to the job-table kernel (defined in ngdbf_multi.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "ngdbf_kernels.cuh"
+
+namespace ngdbf {
+
+// The job-table kernel for a variant (NGDBF_ADAPT | NGDBF_SMOOTH), a precision and the
+// placements of the per-slot state and the count slices; usable with cudaFuncSetAttribute
+// and the occupancy calculator.
+void* multi_kernel_fn(int variant, int precision, bool st_smem, bool wide);
+
+// Launches the job-table kernel `fn` on `stream`.
+cudaError_t launch_multi(void* fn, const MultiArgs& args, int grid, int block, int smem, cudaStream_t stream);
+
+}  // namespace ngdbf

@@ -23,6 +23,8 @@ NGDBF_ERR_UNSUPPORTED = 4
 NGDBF_ADAPT = 1
 NGDBF_SMOOTH = 2
 NGDBF_FP32 = 0
+NGDBF_FP16 = 1
+NGDBF_FIX = 2
 NGDBF_MAX_T = 511
 NGDBF_MAX_WINDOW = 126
 NGDBF_NOALLOC_SCRATCH_BYTES = 40 << 20
@@ -44,6 +46,16 @@ class ngdbf_params(ctypes.Structure):
                 ("q_bits", ctypes.c_int32)]
 
 
+class ngdbf_job(ctypes.Structure):
+    _fields_ = [("code", ctypes.c_void_p), ("y", ctypes.c_void_p), ("n_frames", ctypes.c_int64),
+                ("sigma", ctypes.c_float), ("params", ngdbf_params), ("frame_offset", ctypes.c_uint64),
+                ("bits", ctypes.c_void_p), ("iters", ctypes.c_void_p), ("pass_", ctypes.c_void_p)]
+
+
+NGDBF_BATCH_TUNE = 1
+NGDBF_BATCH_GRAPH = 2
+
+
 class ngdbf_launch_info(ctypes.Structure):
     _fields_ = [("grid", ctypes.c_int32), ("block", ctypes.c_int32), ("smem_bytes", ctypes.c_int32),
                 ("state_in_smem", ctypes.c_int32), ("kernels", ctypes.c_int32),
@@ -51,8 +63,8 @@ class ngdbf_launch_info(ctypes.Structure):
 
 
 def make_params(w=0.75, theta=-0.9, eta=0.96, lam=1.0, y_max=2.5, t_max=100, smooth_window=64,
-                variant=0) -> ngdbf_params:
-    return ngdbf_params(w, theta, eta, lam, y_max, t_max, smooth_window, variant, NGDBF_FP32, 0)
+                variant=0, precision=NGDBF_FP32, q_bits=0) -> ngdbf_params:
+    return ngdbf_params(w, theta, eta, lam, y_max, t_max, smooth_window, variant, precision, q_bits)
 
 
 _lib = None
@@ -79,11 +91,16 @@ def load(path: str | None = None) -> ctypes.CDLL:
                                       ctypes.POINTER(ngdbf_params), ctypes.c_uint64, ctypes.c_uint64,
                                       vp, vp, vp, ctypes.c_int64]
     lib.ngdbf_decode_noalloc.argtypes = lib.ngdbf_decode.argtypes
+    lib.ngdbf_batch_create.argtypes = [ctypes.POINTER(ngdbf_job), ctypes.c_int32, ctypes.c_uint64,
+                                       ctypes.c_int32, vp, ctypes.POINTER(vp)]
+    lib.ngdbf_batch_launch.argtypes = [vp, vp]
+    lib.ngdbf_batch_destroy.argtypes = [vp]
     lib.ngdbf_last_launch.argtypes = [ctypes.POINTER(ngdbf_launch_info)]
     lib.ngdbf_last_error.argtypes = []
     lib.ngdbf_last_error.restype = ctypes.c_char_p
     for fn in ("ngdbf_code_create", "ngdbf_code_destroy", "ngdbf_code_info", "ngdbf_decode",
-               "ngdbf_decode_host", "ngdbf_decode_noalloc", "ngdbf_last_launch"):
+               "ngdbf_decode_host", "ngdbf_decode_noalloc", "ngdbf_last_launch", "ngdbf_batch_create",
+               "ngdbf_batch_launch", "ngdbf_batch_destroy"):
         getattr(lib, fn).restype = ctypes.c_int
     if path is None:
         _lib = lib
@@ -155,6 +172,25 @@ def ngdbf_decode_host(code: int, y_ptr: int, n_frames: int, sigma: float, params
                                       frame_offset, bits_ptr, iters_ptr, pass_ptr, chunk_frames))
 
 
+def ngdbf_batch_create(jobs, seed: int, flags: int = 0, stream: int = 0) -> int:
+    """jobs: a sequence of ngdbf_job; returns the batch handle."""
+    lib = load()
+    arr = (ngdbf_job * len(jobs))(*jobs)
+    h = ctypes.c_void_p()
+    _check(lib, lib.ngdbf_batch_create(arr, len(jobs), seed, flags, stream, ctypes.byref(h)))
+    return h.value
+
+
+def ngdbf_batch_launch(batch: int, stream: int = 0) -> None:
+    lib = load()
+    _check(lib, lib.ngdbf_batch_launch(batch, stream))
+
+
+def ngdbf_batch_destroy(batch: int) -> None:
+    lib = load()
+    _check(lib, lib.ngdbf_batch_destroy(batch))
+
+
 def ngdbf_last_launch() -> dict:
     lib = load()
     info = ngdbf_launch_info()
@@ -220,3 +256,40 @@ class DeviceCode:
         ngdbf_decode_host(self.handle, ptr(y), F, float(sigma), params, int(seed), int(frame_offset),
                           ptr(bits), ptr(iters), ptr(pas), chunk_frames)
         return bits, iters, pas
+
+
+class Batch:
+    """Several decode jobs (DeviceCode, CUDA samples, sigma, params, frame offset) in one launch;
+    outputs are allocated here as CUDA tensors (bits, iters, pass per job)."""
+
+    def __init__(self, jobs, seed: int = 1, flags: int = NGDBF_BATCH_GRAPH, stream=None):
+        import torch
+        self.outputs, cj = [], []
+        for code, y, sigma, params, frame_offset in jobs:
+            F = y.shape[0]
+            bits = torch.empty((F, (code.n + 7) // 8), dtype=torch.uint8, device=y.device)
+            iters = torch.empty(F, dtype=torch.int32, device=y.device)
+            pas = torch.empty(F, dtype=torch.uint8, device=y.device)
+            self.outputs.append((bits, iters, pas))
+            cj.append(ngdbf_job(code.handle, y.data_ptr(), F, float(sigma), params, int(frame_offset),
+                                bits.data_ptr(), iters.data_ptr(), pas.data_ptr()))
+        self._keep = [j for j in jobs]
+        s = stream if stream is not None else torch.cuda.current_stream()
+        self.handle = ngdbf_batch_create(cj, seed, flags, s.cuda_stream)
+
+    def launch(self, stream=None):
+        import torch
+        s = stream if stream is not None else torch.cuda.current_stream()
+        ngdbf_batch_launch(self.handle, s.cuda_stream)
+        return self.outputs
+
+    def close(self):
+        if self.handle:
+            ngdbf_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -62,3 +62,33 @@ def test_host_validation_without_a_device(lib):
 def test_missing_library_fails_loudly(tmp_path):
     with pytest.raises(RuntimeError, match="not built"):
         ngdbf.load(str(tmp_path / "absent.so"))
+
+
+def test_struct_layouts_match_the_c_compiler(tmp_path):
+    """sizeof/offsetof of every public struct, from gcc on include/ngdbf.h, equal the binding's."""
+    import subprocess
+    src = tmp_path / "layout.c"
+    src.write_text('''#include <stddef.h>
+#include <stdio.h>
+#include "ngdbf.h"
+#define F(T, f) printf("%s.%s %zu\\n", #T, #f, offsetof(T, f));
+int main(void) {
+    printf("ngdbf_params %zu\\nngdbf_job %zu\\nngdbf_launch_info %zu\\n", sizeof(ngdbf_params),
+           sizeof(ngdbf_job), sizeof(ngdbf_launch_info));
+    F(ngdbf_job, code) F(ngdbf_job, y) F(ngdbf_job, n_frames) F(ngdbf_job, sigma) F(ngdbf_job, params)
+    F(ngdbf_job, frame_offset) F(ngdbf_job, bits) F(ngdbf_job, iters) F(ngdbf_job, pass)
+    F(ngdbf_params, q_bits) F(ngdbf_launch_info, sm_count)
+    return 0;
+}
+''')
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-std=c11", "-I", str(ngdbf.os.path.dirname(ngdbf.HEADER)), "-o", str(exe), str(src)])
+    got = dict(ln.split() for ln in subprocess.check_output([str(exe)], text=True).splitlines())
+    assert int(got["ngdbf_params"]) == ctypes.sizeof(ngdbf.ngdbf_params)
+    assert int(got["ngdbf_job"]) == ctypes.sizeof(ngdbf.ngdbf_job)
+    assert int(got["ngdbf_launch_info"]) == ctypes.sizeof(ngdbf.ngdbf_launch_info)
+    for f in ("code", "y", "n_frames", "sigma", "params", "frame_offset", "bits", "iters"):
+        assert int(got[f"ngdbf_job.{f}"]) == getattr(ngdbf.ngdbf_job, f).offset, f
+    assert int(got["ngdbf_job.pass"]) == ngdbf.ngdbf_job.pass_.offset
+    assert int(got["ngdbf_params.q_bits"]) == ngdbf.ngdbf_params.q_bits.offset
+    assert int(got["ngdbf_launch_info.sm_count"]) == ngdbf.ngdbf_launch_info.sm_count.offset

@@ -1,0 +1,138 @@
+"""Job tables: several codes in one persistent launch, bit-exact against the reference decoder
+and against one ngdbf_decode per job."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1402_2773_gb300 import ngdbf, workload as wl
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+THREADS = os.cpu_count() or 1
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1402_2773_gb300 import _build
+    _build.build_cuda()
+    ngdbf.load()
+    torch.cuda.set_device(0)
+
+
+@pytest.fixture(scope="module")
+def O():
+    return oracle.load()
+
+
+def wide_code():
+    rng = np.random.default_rng(5)
+    n, m = 203, 101
+    H = np.zeros((m, n), np.uint8)
+    for k in range(n):
+        H[rng.choice(m, size=int(rng.integers(2, 6)), replace=False), k] = 1
+    H[:9, 0] = 1
+    for i in np.nonzero(H.sum(1) == 0)[0]:
+        H[i, rng.integers(n)] = 1
+    return wl.code_from_dense(H)
+
+
+def make_jobs(specs, variant, precision=ngdbf.NGDBF_FP32, q_bits=0):
+    """specs: (code, frames, ebn0, t_max, theta, lam, w, eta, data seed, frame offset)."""
+    jobs = []
+    for code, F, eb, T, theta, lam, w, eta, dseed, off in specs:
+        y, _, sig = wl.frames(code, F, eb, seed=dseed)
+        kw = dict(w=w, theta=theta, eta=eta, lam=lam, y_max=2.5, t_max=T, smooth_window=min(64, T),
+                  variant=variant, precision=precision, q_bits=q_bits)
+        jobs.append(dict(code=code, y=y, sigma=sig, gp=ngdbf.make_params(**kw), op=oracle.make_params(**kw),
+                         off=off))
+    return jobs
+
+
+def run_batch(jobs, seed, flags):
+    dcs = [ngdbf.DeviceCode.from_code(j["code"]) for j in jobs]
+    ys = [torch.from_numpy(j["y"]).cuda() for j in jobs]
+    b = ngdbf.Batch([(dc, y, j["sigma"], j["gp"], j["off"]) for dc, y, j in zip(dcs, ys, jobs)],
+                    seed=seed, flags=flags)
+    outs = b.launch()
+    torch.cuda.synchronize()
+    res = [tuple(t.cpu().numpy() for t in o) for o in outs]
+    info = ngdbf.ngdbf_last_launch()
+    outs2 = b.launch()                      # a second launch gives the same results
+    torch.cuda.synchronize()
+    res2 = [tuple(t.cpu().numpy() for t in o) for o in outs2]
+    for r, r2 in zip(res, res2):
+        assert all((a == c).all() for a, c in zip(r, r2))
+    single = []
+    for dc, y, j in zip(dcs, ys, jobs):
+        single.append(tuple(t.cpu().numpy() for t in dc.decode(y, j["sigma"], j["gp"], seed=seed,
+                                                              frame_offset=j["off"])))
+    torch.cuda.synchronize()
+    b.close()
+    for dc in dcs:
+        dc.close()
+    return res, single, info
+
+
+def check(O, jobs, seed, flags=ngdbf.NGDBF_BATCH_GRAPH):
+    res, single, info = run_batch(jobs, seed, flags)
+    for j, r, s in zip(jobs, res, single):
+        assert all((a == c).all() for a, c in zip(r, s)), "batch result differs from ngdbf_decode"
+        if j["y"].shape[0]:
+            ob, oi, op = O.decode_f32(j["code"], j["y"], j["sigma"], j["op"], seed=seed, frame_offset=j["off"],
+                                      threads=THREADS)
+            assert (r[0] == ob).all() and (r[1] == oi).all() and (r[2] == op).all(), "batch differs from oracle"
+    return info
+
+
+def mix(scale=1):
+    return [
+        (wl.peg_code(504, 252, 3, seed=1), 300 * scale, 3.0, 100, -0.9, 0.99, 0.75, 0.96, 1, 0),
+        (wl.code_c1(), 257 * scale, 3.5, 160, -0.8, 0.98, 0.7, 0.9, 2, 1000),
+        (wl.peg_code(1024, 512, 4, seed=1), 130 * scale, 2.8, 200, -0.9, 0.99, 0.75, 0.8, 3, 5),
+        (wl.code_c2(), 90 * scale, 4.0, 300, -0.7, 0.993, 0.1875, 0.65, 4, 77),
+        (wide_code(), 61 * scale, 3.0, 120, -0.6, 0.97, 0.6, 0.9, 5, 0),
+    ]
+
+
+@pytest.mark.parametrize("variant", [0, 3])
+def test_mixed_codes_one_launch(O, variant):
+    info = check(O, make_jobs(mix(), variant), seed=9)
+    assert info["kernels"] == 1
+
+
+def test_tuned_and_direct_launch(O):
+    check(O, make_jobs(mix(), 1), seed=3, flags=ngdbf.NGDBF_BATCH_TUNE)
+    check(O, make_jobs(mix(), 2), seed=4, flags=0)
+
+
+@pytest.mark.parametrize("prec", [dict(precision=ngdbf.NGDBF_FP16), dict(precision=ngdbf.NGDBF_FIX, q_bits=8)],
+                         ids=["fp16", "fix8"])
+def test_mixed_codes_reduced_precision(O, prec):
+    check(O, make_jobs(mix(), 3, **prec), seed=5)
+
+
+def test_state_in_global_memory_for_the_whole_table(O):
+    specs = mix()[:2] + [(wl.peg_code(8192, 1639, 3, seed=1), 40, 3.0, 80, -0.9, 0.99, 0.75, 0.9, 6, 9)]
+    info = check(O, make_jobs(specs, 3), seed=7)
+    assert info["state_in_smem"] == 0
+
+
+def test_many_small_jobs_and_empty_jobs(O):
+    code = wl.peg_code(504, 252, 3, seed=1)
+    specs = [(code, int(f), 3.2, 60, -0.9, 0.98, 0.75, 0.9, 100 + i, 50 * i)
+             for i, f in enumerate([0, 1, 5, 33, 0, 2] + [3] * 200)]
+    check(O, make_jobs(specs, 3), seed=8)
+
+
+def test_mixed_variants_are_rejected():
+    code = wl.peg_code(504, 252, 3, seed=1)
+    dc = ngdbf.DeviceCode.from_code(code)
+    y = torch.zeros((4, code.n), dtype=torch.float32, device="cuda")
+    with pytest.raises(ngdbf.NgdbfError) as e:
+        ngdbf.Batch([(dc, y, 0.5, ngdbf.make_params(variant=0), 0), (dc, y, 0.5, ngdbf.make_params(variant=1), 0)])
+    assert e.value.status == ngdbf.NGDBF_ERR_UNSUPPORTED
+    dc.close()

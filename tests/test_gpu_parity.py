@@ -36,7 +36,8 @@ def O():
 
 
 def params_pair(**kw):
-    d = dict(w=0.75, theta=-0.9, eta=0.96, lam=1.0, y_max=2.5, t_max=100, smooth_window=64, variant=0)
+    d = dict(w=0.75, theta=-0.9, eta=0.96, lam=1.0, y_max=2.5, t_max=100, smooth_window=64, variant=0,
+             precision=ngdbf.NGDBF_FP32, q_bits=0)
     d.update(kw)
     return ngdbf.make_params(**d), oracle.make_params(**d)
 
@@ -212,6 +213,46 @@ def test_host_entry_point_matches_device(O):
     assert (hb2 == ob).all() and (hi2 == oi).all() and (hp2 == ops).all()
 
 
+PRECISIONS = [dict(precision=ngdbf.NGDBF_FP16), dict(precision=ngdbf.NGDBF_FIX, q_bits=8),
+              dict(precision=ngdbf.NGDBF_FIX, q_bits=4, y_max=1.75), dict(precision=ngdbf.NGDBF_FIX, q_bits=3)]
+PREC_IDS = ["fp16", "fix8", "fix4", "fix3"]
+
+
+@pytest.mark.parametrize("prec", PRECISIONS, ids=PREC_IDS)
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
+def test_precision_variants_small(O, prec, variant):
+    code = wl.peg_code(504, 252, 3, seed=3)
+    y, _, sig = wl.frames(code, 70, 2.8, seed=31)
+    assert_parity(O, code, y, sig, seed=6, variant=variant, lam=0.97, t_max=60, smooth_window=12, **prec)
+
+
+@pytest.mark.parametrize("prec", PRECISIONS[:2], ids=PREC_IDS[:2])
+def test_precision_variants_workloads(O, prec):
+    """(3,6) N=1008 plain at 4 dB and (6,32) N=2048 SM-NGDBF at 4 dB in FP16 and 8-bit fixed point."""
+    code = wl.code_c1()
+    y, _, sig = wl.frames(code, 1500, 4.0, seed=32)
+    assert_parity(O, code, y, sig, seed=1, w=0.75, theta=-0.9, eta=0.96, t_max=100, **prec)
+    code = wl.code_c2()
+    y, _, sig = wl.frames(code, 200, 4.0, seed=33)
+    assert_parity(O, code, y, sig, seed=7, w=0.1875, theta=-0.7, eta=0.65, lam=0.993, y_max=2.0,
+                  t_max=300, smooth_window=64, variant=3, **prec)
+
+
+@pytest.mark.parametrize("prec", PRECISIONS[:2], ids=PREC_IDS[:2])
+def test_precision_variants_global_state_and_wide(O, prec):
+    """State in global memory (N=8192) and symbol degree above 7 (seven count slices)."""
+    code = wl.peg_code(8192, 1639, 3, seed=1)
+    y, _, sig = wl.frames(code, 40, 3.0, seed=34)
+    assert_parity(O, code, y, sig, seed=4, lam=0.99, t_max=80, smooth_window=20, variant=3, **prec)
+    code = irregular_code(203, 101, seed=5)
+    H = code.dense()
+    H[:, 0] = 0
+    H[:9, 0] = 1                                   # one symbol of degree 9
+    code = wl.code_from_dense(H)
+    y, _, sig = wl.frames(code, 70, 3.0, seed=35)
+    assert_parity(O, code, y, sig, seed=3, variant=3, lam=0.97, t_max=40, smooth_window=9, **prec)
+
+
 def test_invalid_arguments_report_status():
     code = wl.peg_code(504, 252, 3, seed=3)
     dc = ngdbf.DeviceCode.from_code(code)
@@ -225,6 +266,11 @@ def test_invalid_arguments_report_status():
     with pytest.raises(ngdbf.NgdbfError) as e:
         dc.decode(y, -1.0, ngdbf.make_params())
     assert e.value.status == ngdbf.NGDBF_ERR_INVALID_ARG
+    for bad in (dict(precision=ngdbf.NGDBF_FIX, q_bits=9), dict(precision=ngdbf.NGDBF_FIX, q_bits=8, y_max=0.0),
+                dict(precision=ngdbf.NGDBF_FP16, q_bits=4), dict(precision=7)):
+        with pytest.raises(ngdbf.NgdbfError) as e:
+            dc.decode(y, 0.5, ngdbf.make_params(**bad))
+        assert e.value.status == ngdbf.NGDBF_ERR_INVALID_ARG
     host = np.zeros((4, code.n), np.float32)
     out = torch.empty((4, 63), dtype=torch.uint8, device="cuda")
     it = torch.empty(4, dtype=torch.int32, device="cuda")
