@@ -55,7 +55,8 @@ typedef enum {
     NGDBF_ERR_INVALID_ARG = 1,   /* bad pointer, size, index or parameter */
     NGDBF_ERR_OOM = 2,           /* device or host allocation failed */
     NGDBF_ERR_CUDA = 3,          /* a CUDA runtime call failed */
-    NGDBF_ERR_UNSUPPORTED = 4    /* valid input outside this build's limits */
+    NGDBF_ERR_UNSUPPORTED = 4,   /* valid input outside this build's limits */
+    NGDBF_ERR_TIMEOUT = 5        /* a wait ran out of time */
 } ngdbf_status;
 
 /* Variant bits (Sec. III-C/D/E).  0 = plain M-NGDBF with one threshold. */
@@ -234,6 +235,62 @@ ngdbf_status ngdbf_batch_launch(ngdbf_batch_t* batch, void* stream);
 
 /* Releases the plan; no launch of it may still be running. */
 ngdbf_status ngdbf_batch_destroy(ngdbf_batch_t* batch);
+
+/*
+ * Serving loop (continuous batching).  A server owns a scheduler thread, a set
+ * of streams and a device-memory budget.  Requests -- a code, HOST samples,
+ * sigma, params, a frame offset and HOST output buffers -- may be submitted at
+ * any time from any thread.  The scheduler admits pending requests in arrival
+ * order while the device memory they need (samples, outputs, and the slot
+ * scratch and job table of their launch) fits the budget beside the launches
+ * already running, packs the admitted requests into one job-table launch
+ * (copy in, decode, copy out) on a free stream, and retires a launch when its
+ * stream passes it, which returns its memory for the next requests.  Launches
+ * on different streams overlap on the device: the CTAs of a persistent launch
+ * exit as its frames finish and the next launch's CTAs take those SMs.  Each
+ * request's result equals ngdbf_decode's for the same job, alone or in any
+ * mix.  Requests packed together share variant and precision; the seed of the
+ * perturbation is the server's.  Page-locked host buffers let the copies run
+ * asynchronously; with pageable ones the scheduler thread blocks on each copy.
+ */
+typedef struct ngdbf_server ngdbf_server_t;
+
+typedef struct ngdbf_server_stats {
+    int64_t submitted, completed, failed;
+    int64_t launches;                 /* job-table launches issued */
+    int64_t frames;                   /* frames of completed requests */
+    int64_t peak_bytes_in_use;        /* largest device memory held by running launches */
+    int32_t peak_concurrent_launches; /* most launches in flight at once */
+    int32_t reserved;
+} ngdbf_server_stats;
+
+/* device_budget_bytes: device memory the running launches may hold together;
+ * max_inflight_launches: 1..16 streams; max_jobs_per_launch: 1..4096 requests
+ * packed into one launch. */
+ngdbf_status ngdbf_server_create(size_t device_budget_bytes, int32_t max_inflight_launches,
+                                 int32_t max_jobs_per_launch, uint64_t seed, ngdbf_server_t** out);
+
+/* Queues one request (validated now; HOST buffers must stay valid until the
+ * request completes).  *request_id receives its id (1, 2, ...). */
+ngdbf_status ngdbf_server_submit(ngdbf_server_t* server, const ngdbf_code_t* code, const float* y_host,
+                                 int64_t n_frames, float sigma, const ngdbf_params* params,
+                                 uint64_t frame_offset, uint8_t* bits_host, int32_t* iters_host,
+                                 uint8_t* pass_host, uint64_t* request_id);
+
+/* Completed requests not reported before, up to `capacity`: ids[i], the time
+ * from submission to outputs written (seconds) and the request's status
+ * (NGDBF_OK, or why it failed, e.g. NGDBF_ERR_OOM when it alone exceeds the
+ * budget).  *n_out receives the count. */
+ngdbf_status ngdbf_server_poll(ngdbf_server_t* server, uint64_t* ids, double* latency_s, int32_t* status,
+                               int32_t capacity, int32_t* n_out);
+
+/* Blocks until every submitted request has completed; NGDBF_ERR_TIMEOUT after timeout_s. */
+ngdbf_status ngdbf_server_wait(ngdbf_server_t* server, double timeout_s);
+
+ngdbf_status ngdbf_server_get_stats(ngdbf_server_t* server, ngdbf_server_stats* out);
+
+/* Finishes the requests already admitted, drops the pending ones, releases everything. */
+ngdbf_status ngdbf_server_destroy(ngdbf_server_t* server);
 
 /* Launch shape of the most recent ngdbf_decode* or ngdbf_batch_* call on the calling thread. */
 typedef struct ngdbf_launch_info {

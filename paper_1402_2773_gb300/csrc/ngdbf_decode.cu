@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "../../include/ngdbf.h"
+#include "ngdbf_host.h"
 #include "ngdbf_kernels.cuh"
 
 namespace ngdbf {
@@ -37,15 +38,9 @@ __global__ void __launch_bounds__(1024) ngdbf_persistent_kernel(const __grid_con
 
 using namespace ngdbf;
 
-struct ngdbf_code {
-    int32_t n, m, dv_max, dc_max;
-    int device;
-    uint16_t* d_chk_cols;
-    uint16_t* d_sym_chks;
-    uint8_t* d_sym_deg;
-};
 
-namespace {
+namespace ngdbf {
+namespace host {
 
 thread_local std::string g_last_error;
 thread_local ngdbf_launch_info g_last_launch = {0, 0, 0, 0, 0, 0};
@@ -54,6 +49,17 @@ ngdbf_status fail(ngdbf_status s, const std::string& msg) {
     g_last_error = msg;
     return s;
 }
+
+void set_last_launch(int grid, int block, int smem, int state_in_smem, int kernels, int sm_count) {
+    g_last_launch.grid = grid;
+    g_last_launch.block = block;
+    g_last_launch.smem_bytes = smem;
+    g_last_launch.state_in_smem = state_in_smem;
+    g_last_launch.kernels = kernels;
+    g_last_launch.sm_count = sm_count;
+}
+
+size_t align256(size_t v) { return (v + 255) / 256 * 256; }
 
 ngdbf_status cuda_fail(cudaError_t e, const char* what) {
     return fail(NGDBF_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
@@ -345,7 +351,10 @@ ngdbf_status decode_impl(const ngdbf_code* C, const float* y, int64_t n_frames, 
     return NGDBF_OK;
 }
 
-}  // namespace
+}  // namespace host
+}  // namespace ngdbf
+
+using namespace ngdbf::host;
 
 extern "C" {
 
@@ -629,25 +638,24 @@ struct ngdbf_batch {
     cudaGraphExec_t exec = nullptr;
 };
 
-namespace {
-
-size_t align256(size_t v) { return (v + 255) / 256 * 256; }
+namespace ngdbf {
+namespace host {
 
 // First job of every CTA: CTAs in proportion to the estimated work of each job
 // (frames x n x (T + 1)), at least one CTA per job with frames, at most one CTA
 // per 32 of its frames; CTAs left over go to the jobs with the most work per CTA.
-std::vector<int32_t> assign_ctas(const ngdbf_batch& B, int grid) {
-    const int J = B.n_jobs;
+std::vector<int32_t> assign_ctas(const std::vector<int64_t>& frames, const std::vector<int64_t>& weight, int grid) {
+    const int J = (int)frames.size();
     std::vector<int64_t> cap(J), cnt(J, 0);
     double total = 0;
     for (int j = 0; j < J; ++j) {
-        cap[j] = (B.frames[j] + kSlots - 1) / kSlots;
-        total += (double)B.weight[j];
+        cap[j] = (frames[j] + kSlots - 1) / kSlots;
+        total += (double)weight[j];
     }
     int used = 0;
     for (int j = 0; j < J; ++j) {
-        if (B.frames[j] == 0) continue;
-        int64_t c = (int64_t)std::floor((double)grid * (double)B.weight[j] / std::max(total, 1.0));
+        if (frames[j] == 0) continue;
+        int64_t c = (int64_t)std::floor((double)grid * (double)weight[j] / std::max(total, 1.0));
         cnt[j] = std::min(std::max<int64_t>(c, 1), cap[j]);
         used += (int)cnt[j];
     }
@@ -656,7 +664,7 @@ std::vector<int32_t> assign_ctas(const ngdbf_batch& B, int grid) {
         double best = 1e300;
         for (int j = 0; j < J; ++j)
             if (cnt[j] > 1 || (cnt[j] == 1 && used > grid)) {
-                const double per = (double)B.weight[j] / (double)cnt[j];
+                const double per = (double)weight[j] / (double)cnt[j];
                 if (cnt[j] > 0 && per < best) { best = per; pick = j; }
             }
         if (pick < 0) break;
@@ -668,7 +676,7 @@ std::vector<int32_t> assign_ctas(const ngdbf_batch& B, int grid) {
         double best = -1;
         for (int j = 0; j < J; ++j)
             if (cnt[j] < cap[j]) {
-                const double per = (double)B.weight[j] / (double)(cnt[j] + 1);
+                const double per = (double)weight[j] / (double)(cnt[j] + 1);
                 if (per > best) { best = per; pick = j; }
             }
         if (pick < 0) break;
@@ -683,6 +691,72 @@ std::vector<int32_t> assign_ctas(const ngdbf_batch& B, int grid) {
     return first;
 }
 
+ngdbf_status plan_table(const ngdbf_job* jobs, int32_t n_jobs, int dev, TablePlan* out) {
+    TablePlan& T = *out;
+    T = TablePlan();
+    const int variant = jobs[0].params.variant, precision = jobs[0].params.precision;
+    for (int j = 0; j < n_jobs; ++j) {
+        const ngdbf_job& q = jobs[j];
+        if (!q.code) return fail(NGDBF_ERR_INVALID_ARG, "job without a code");
+        ngdbf_status s = check_params(&q.params, q.sigma);
+        if (s != NGDBF_OK) return s;
+        if (q.params.variant != variant || q.params.precision != precision)
+            return fail(NGDBF_ERR_UNSUPPORTED, "jobs of one table must share variant and precision");
+        if (q.code->device != dev) return fail(NGDBF_ERR_INVALID_ARG, "code tables belong to another device");
+        if (q.n_frames < 0) return fail(NGDBF_ERR_INVALID_ARG, "n_frames < 0");
+        T.n_max = std::max(T.n_max, q.code->n);
+        T.m_max = std::max(T.m_max, q.code->m);
+        T.t_max = std::max(T.t_max, q.params.t_max);
+        T.dv_max = std::max(T.dv_max, q.code->dv_max);
+        T.dc_max = std::max(T.dc_max, q.code->dc_max);
+        T.thr_words += (size_t)q.params.t_max + 1;
+    }
+    T.variant = variant;
+    T.precision = precision;
+    int smem_optin = 0;
+    cudaError_t e = cudaDeviceGetAttribute(&T.sm_count, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
+    // shared memory for the largest code and T; state, then tables, move out when needed
+    const bool state = (variant & 3) != 0, adapt = (variant & NGDBF_ADAPT) != 0;
+    T.wide = T.dv_max > 7;
+    bool st_smem = state, tables_smem = true;
+    auto layout = [&]() { return smem_layout(T.n_max, T.m_max, T.t_max, T.dv_max, T.dc_max, adapt, st_smem, tables_smem); };
+    void* fn = multi_kernel_fn(variant, precision, st_smem, T.wide);
+    cudaFuncAttributes fa;
+    e = cudaFuncGetAttributes(&fa, fn);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncGetAttributes");
+    const int limit = smem_optin - (int)fa.sharedSizeBytes;
+    SmemLayout L = layout();
+    if (L.total > limit) { tables_smem = false; L = layout(); }
+    if (L.total > limit && st_smem) {
+        st_smem = false; tables_smem = true; L = layout();
+        if (L.total > limit) { tables_smem = false; L = layout(); }
+    }
+    if (L.total > limit) return fail(NGDBF_ERR_UNSUPPORTED, "largest code too large for shared memory");
+    fn = multi_kernel_fn(variant, precision, st_smem, T.wide);
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, L.total);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+    T.fn = fn;
+    T.smem = L.total;
+    T.st_smem = st_smem;
+    T.tables_smem = tables_smem;
+    T.state_global = state && !st_smem;
+    for (int block : {1024, 512, 256}) {
+        int bps = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, (const void*)fn, block, L.total);
+        if (e != cudaSuccess) return cuda_fail(e, "occupancy");
+        if (bps > 0) T.shapes.push_back({block, bps});
+    }
+    if (T.shapes.empty()) return fail(NGDBF_ERR_UNSUPPORTED, "job-table kernel does not fit on an SM");
+    return NGDBF_OK;
+}
+
+}  // namespace host
+}  // namespace ngdbf
+
+namespace {
+
 cudaError_t batch_enqueue(ngdbf_batch* B, cudaStream_t stream) {
     cudaError_t e = cudaMemsetAsync(B->d_queues, 0, sizeof(unsigned long long) * B->n_jobs, stream);
     if (e != cudaSuccess) return e;
@@ -694,7 +768,7 @@ ngdbf_status batch_set_shape(ngdbf_batch* B, int block, int bps) {
     int64_t groups = 0;
     for (int j = 0; j < B->n_jobs; ++j) groups += (B->frames[j] + kSlots - 1) / kSlots;
     B->grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)B->sm_count * bps, groups));
-    std::vector<int32_t> first = assign_ctas(*B, B->grid);
+    std::vector<int32_t> first = assign_ctas(B->frames, B->weight, B->grid);
     cudaError_t e = cudaMemcpy(B->d_first, first.data(), first.size() * 4, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_fail(e, "job table: first jobs");
     return NGDBF_OK;
@@ -720,80 +794,37 @@ extern "C" ngdbf_status ngdbf_batch_create(const ngdbf_job* jobs, int32_t n_jobs
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
-    const int variant = jobs[0].params.variant, precision = jobs[0].params.precision;
-    int n_max = 0, m_max = 0, t_max = 0, dv_max = 0, dc_max = 0;
-    size_t thr_words = 0;
+    TablePlan T;
+    ngdbf_status ps = plan_table(jobs, n_jobs, dev, &T);
+    if (ps != NGDBF_OK) return ps;
     for (int j = 0; j < n_jobs; ++j) {
         const ngdbf_job& q = jobs[j];
-        if (!q.code) return fail(NGDBF_ERR_INVALID_ARG, "job without a code");
-        ngdbf_status s = check_params(&q.params, q.sigma);
-        if (s != NGDBF_OK) return s;
-        if (q.params.variant != variant || q.params.precision != precision)
-            return fail(NGDBF_ERR_UNSUPPORTED, "jobs of one table must share variant and precision");
-        if (q.code->device != dev) return fail(NGDBF_ERR_INVALID_ARG, "code tables belong to another device");
-        if (q.n_frames < 0) return fail(NGDBF_ERR_INVALID_ARG, "n_frames < 0");
-        if (q.n_frames > 0) {
-            if (!q.y || !q.bits || !q.iters || !q.pass) return fail(NGDBF_ERR_INVALID_ARG, "NULL buffer");
-            for (const void* p : {(const void*)q.y, (const void*)q.bits, (const void*)q.iters, (const void*)q.pass}) {
-                cudaPointerAttributes a;
-                e = cudaPointerGetAttributes(&a, p);
-                if (e != cudaSuccess || !(a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged)) {
-                    cudaGetLastError();
-                    return fail(NGDBF_ERR_INVALID_ARG, "job buffers must be device memory");
-                }
+        if (q.n_frames == 0) continue;
+        if (!q.y || !q.bits || !q.iters || !q.pass) return fail(NGDBF_ERR_INVALID_ARG, "NULL buffer");
+        for (const void* p : {(const void*)q.y, (const void*)q.bits, (const void*)q.iters, (const void*)q.pass}) {
+            cudaPointerAttributes a;
+            e = cudaPointerGetAttributes(&a, p);
+            if (e != cudaSuccess || !(a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged)) {
+                cudaGetLastError();
+                return fail(NGDBF_ERR_INVALID_ARG, "job buffers must be device memory");
             }
         }
-        n_max = std::max(n_max, q.code->n);
-        m_max = std::max(m_max, q.code->m);
-        t_max = std::max(t_max, q.params.t_max);
-        dv_max = std::max(dv_max, q.code->dv_max);
-        dc_max = std::max(dc_max, q.code->dc_max);
-        thr_words += (size_t)q.params.t_max + 1;
     }
     ngdbf_batch* B = new (std::nothrow) ngdbf_batch;
     if (!B) return fail(NGDBF_ERR_OOM, "host allocation");
     B->device = dev;
     B->n_jobs = n_jobs;
-    int smem_optin = 0;
-    e = cudaDeviceGetAttribute(&B->sm_count, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    if (e != cudaSuccess) { batch_free(B); return cuda_fail(e, "cudaDeviceGetAttribute"); }
-    // shared memory for the largest code and T; state, then tables, move out when needed
-    const bool state = (variant & 3) != 0, adapt = (variant & NGDBF_ADAPT) != 0, wide = dv_max > 7;
-    bool st_smem = state, tables_smem = true;
-    auto layout = [&]() { return smem_layout(n_max, m_max, t_max, dv_max, dc_max, adapt, st_smem, tables_smem); };
-    void* fn = multi_kernel_fn(variant, precision, st_smem, wide);
-    cudaFuncAttributes fa;
-    e = cudaFuncGetAttributes(&fa, fn);
-    if (e != cudaSuccess) { batch_free(B); return cuda_fail(e, "cudaFuncGetAttributes"); }
-    const int limit = smem_optin - (int)fa.sharedSizeBytes;
-    SmemLayout L = layout();
-    if (L.total > limit) { tables_smem = false; L = layout(); }
-    if (L.total > limit && st_smem) {
-        st_smem = false; tables_smem = true; L = layout();
-        if (L.total > limit) { tables_smem = false; L = layout(); }
-    }
-    if (L.total > limit) { batch_free(B); return fail(NGDBF_ERR_UNSUPPORTED, "largest code too large for shared memory"); }
-    fn = multi_kernel_fn(variant, precision, st_smem, wide);
-    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, L.total);
-    if (e != cudaSuccess) { batch_free(B); return cuda_fail(e, "cudaFuncSetAttribute"); }
-    B->fn = fn;
-    B->smem = L.total;
-    B->state_in_smem = st_smem ? 1 : 0;
-    // candidate block sizes and the largest grid any of them needs
-    std::vector<std::pair<int, int>> shapes;
+    B->sm_count = T.sm_count;
+    B->fn = T.fn;
+    B->smem = T.smem;
+    B->state_in_smem = T.st_smem ? 1 : 0;
+    std::vector<std::pair<int, int>> shapes = T.shapes;
     int max_bps = 0;
-    for (int block : {1024, 512, 256}) {
-        int bps = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, (const void*)fn, block, L.total);
-        if (e != cudaSuccess) { batch_free(B); return cuda_fail(e, "occupancy"); }
-        if (bps > 0) { shapes.push_back({block, bps}); max_bps = std::max(max_bps, bps); }
-    }
-    if (shapes.empty()) { batch_free(B); return fail(NGDBF_ERR_UNSUPPORTED, "job-table kernel does not fit on an SM"); }
-    const size_t grid_max = (size_t)B->sm_count * max_bps;
-    const size_t per_slot_y = (size_t)n_max * kSlots * held_bytes(precision);
-    const size_t per_slot_st = (state && !st_smem) ? (size_t)n_max * kSlots * 2 : 0;
-    const size_t off_jobs = 0, off_thr = align256(sizeof(Job) * n_jobs), off_q = off_thr + align256(thr_words * 4);
+    for (const auto& sh : shapes) max_bps = std::max(max_bps, sh.second);
+    const size_t grid_max = (size_t)T.sm_count * max_bps;
+    const size_t per_slot_y = (size_t)T.n_max * kSlots * held_bytes(T.precision);
+    const size_t per_slot_st = T.state_global ? (size_t)T.n_max * kSlots * 2 : 0;
+    const size_t off_jobs = 0, off_thr = align256(sizeof(Job) * n_jobs), off_q = off_thr + align256(T.thr_words * 4);
     const size_t off_first = off_q + align256(8 * (size_t)n_jobs), off_y = off_first + align256(4 * grid_max);
     const size_t off_st = off_y + align256(grid_max * per_slot_y);
     const size_t total = off_st + align256(grid_max * per_slot_st);
@@ -807,7 +838,7 @@ extern "C" ngdbf_status ngdbf_batch_create(const ngdbf_job* jobs, int32_t n_jobs
     B->d_first = reinterpret_cast<int32_t*>(B->d_mem + off_first);
     // job table and thresholds
     std::vector<Job> hjobs(n_jobs);
-    std::vector<uint32_t> hthr(thr_words);
+    std::vector<uint32_t> hthr(T.thr_words);
     size_t tpos = 0;
     B->frames.resize(n_jobs);
     B->weight.resize(n_jobs);
@@ -828,8 +859,8 @@ extern "C" ngdbf_status ngdbf_batch_create(const ngdbf_job* jobs, int32_t n_jobs
     A.jobs = reinterpret_cast<const Job*>(B->d_mem + off_jobs);
     A.n_jobs = n_jobs;
     A.first_job = B->d_first;
-    A.n_max = n_max; A.m_max = m_max; A.t_max = t_max; A.dv_max = dv_max; A.dc_max = dc_max;
-    A.tables_smem = tables_smem ? 1 : 0;
+    A.n_max = T.n_max; A.m_max = T.m_max; A.t_max = T.t_max; A.dv_max = T.dv_max; A.dc_max = T.dc_max;
+    A.tables_smem = T.tables_smem ? 1 : 0;
     A.yslots = B->d_mem + off_y;
     A.st_global = per_slot_st ? reinterpret_cast<uint16_t*>(B->d_mem + off_st) : nullptr;
     host_gen_consts(seed, A.G);
@@ -885,12 +916,7 @@ extern "C" ngdbf_status ngdbf_batch_launch(ngdbf_batch_t* B, void* stream_ptr) {
     if (dev != B->device) return fail(NGDBF_ERR_INVALID_ARG, "batch belongs to another device");
     e = B->exec ? cudaGraphLaunch(B->exec, stream) : batch_enqueue(B, stream);
     if (e != cudaSuccess) return cuda_fail(e, "job table launch");
-    g_last_launch.grid = B->grid;
-    g_last_launch.block = B->block;
-    g_last_launch.smem_bytes = B->smem;
-    g_last_launch.state_in_smem = B->state_in_smem;
-    g_last_launch.kernels = 1;
-    g_last_launch.sm_count = B->sm_count;
+    set_last_launch(B->grid, B->block, B->smem, B->state_in_smem, 1, B->sm_count);
     return NGDBF_OK;
 }
 

@@ -1,0 +1,61 @@
+// ngdbf_host.h -- host-side pieces shared by the translation units of the C ABI
+// (single decodes and job tables in ngdbf_decode.cu, the serving loop in ngdbf_server.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "../../include/ngdbf.h"
+#include "ngdbf_kernels.cuh"
+#include "ngdbf_multi.h"
+
+// Device-resident tables of one parity-check matrix.
+struct ngdbf_code {
+    int32_t n, m, dv_max, dc_max;
+    int device;
+    uint16_t* d_chk_cols;   // [dc_max][m] N(i) column-major, padded with n
+    uint16_t* d_sym_chks;   // [n][dv_max] M(k) row-major, padded with m
+    uint8_t* d_sym_deg;     // [n]
+};
+
+namespace ngdbf {
+namespace host {
+
+// Error text for the calling thread; returns s.
+ngdbf_status fail(ngdbf_status s, const std::string& msg);
+ngdbf_status cuda_fail(cudaError_t e, const char* what);
+// Launch shape reported by ngdbf_last_launch on the calling thread.
+void set_last_launch(int grid, int block, int smem, int state_in_smem, int kernels, int sm_count);
+size_t align256(size_t v);
+// The library's stream-ordered pool of a device (kept warm across calls).
+ngdbf_status get_pool(int dev, cudaMemPool_t* out);
+// Philox round keys and series coefficients of the perturbation generator.
+void host_gen_consts(uint64_t seed, GenConsts& G);
+// Bytes of one held sample of a precision.
+size_t held_bytes(int precision);
+ngdbf_status check_params(const ngdbf_params* P, float sigma);
+// Job fields and its threshold words thr[0..t_max].
+void fill_job(const ngdbf_code* C, const ngdbf_params* P, const float* y, int64_t n_frames, float sigma,
+              uint64_t frame_offset, uint8_t* bits, int32_t* iters, uint8_t* pass,
+              unsigned long long* queue, Job* out, uint32_t* thr);
+
+// Shared-memory plan of a job table: launch maxima, kernel, and candidate
+// (block, CTAs per SM) shapes.
+struct TablePlan {
+    int n_max = 0, m_max = 0, t_max = 0, dv_max = 0, dc_max = 0;
+    int variant = 0, precision = 0, sm_count = 0, smem = 0;
+    bool st_smem = false, tables_smem = false, wide = false, state_global = false;
+    size_t thr_words = 0;
+    void* fn = nullptr;
+    std::vector<std::pair<int, int>> shapes;
+};
+ngdbf_status plan_table(const ngdbf_job* jobs, int32_t n_jobs, int dev, TablePlan* out);
+// First job of every CTA, in proportion to the estimated work of each job.
+std::vector<int32_t> assign_ctas(const std::vector<int64_t>& frames, const std::vector<int64_t>& weight, int grid);
+
+}  // namespace host
+}  // namespace ngdbf

@@ -20,6 +20,7 @@ NGDBF_ERR_INVALID_ARG = 1
 NGDBF_ERR_OOM = 2
 NGDBF_ERR_CUDA = 3
 NGDBF_ERR_UNSUPPORTED = 4
+NGDBF_ERR_TIMEOUT = 5
 NGDBF_ADAPT = 1
 NGDBF_SMOOTH = 2
 NGDBF_FP32 = 0
@@ -54,6 +55,12 @@ class ngdbf_job(ctypes.Structure):
 
 NGDBF_BATCH_TUNE = 1
 NGDBF_BATCH_GRAPH = 2
+
+
+class ngdbf_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("failed", ctypes.c_int64),
+                ("launches", ctypes.c_int64), ("frames", ctypes.c_int64), ("peak_bytes_in_use", ctypes.c_int64),
+                ("peak_concurrent_launches", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class ngdbf_launch_info(ctypes.Structure):
@@ -95,12 +102,22 @@ def load(path: str | None = None) -> ctypes.CDLL:
                                        ctypes.c_int32, vp, ctypes.POINTER(vp)]
     lib.ngdbf_batch_launch.argtypes = [vp, vp]
     lib.ngdbf_batch_destroy.argtypes = [vp]
+    lib.ngdbf_server_create.argtypes = [ctypes.c_size_t, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64,
+                                        ctypes.POINTER(vp)]
+    lib.ngdbf_server_submit.argtypes = [vp, vp, vp, ctypes.c_int64, ctypes.c_float, ctypes.POINTER(ngdbf_params),
+                                        ctypes.c_uint64, vp, vp, vp, ctypes.POINTER(ctypes.c_uint64)]
+    lib.ngdbf_server_poll.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_double),
+                                      ctypes.POINTER(ctypes.c_int32), ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]
+    lib.ngdbf_server_wait.argtypes = [vp, ctypes.c_double]
+    lib.ngdbf_server_get_stats.argtypes = [vp, ctypes.POINTER(ngdbf_server_stats)]
+    lib.ngdbf_server_destroy.argtypes = [vp]
     lib.ngdbf_last_launch.argtypes = [ctypes.POINTER(ngdbf_launch_info)]
     lib.ngdbf_last_error.argtypes = []
     lib.ngdbf_last_error.restype = ctypes.c_char_p
     for fn in ("ngdbf_code_create", "ngdbf_code_destroy", "ngdbf_code_info", "ngdbf_decode",
                "ngdbf_decode_host", "ngdbf_decode_noalloc", "ngdbf_last_launch", "ngdbf_batch_create",
-               "ngdbf_batch_launch", "ngdbf_batch_destroy"):
+               "ngdbf_batch_launch", "ngdbf_batch_destroy", "ngdbf_server_create", "ngdbf_server_submit",
+               "ngdbf_server_poll", "ngdbf_server_wait", "ngdbf_server_get_stats", "ngdbf_server_destroy"):
         getattr(lib, fn).restype = ctypes.c_int
     if path is None:
         _lib = lib
@@ -189,6 +206,49 @@ def ngdbf_batch_launch(batch: int, stream: int = 0) -> None:
 def ngdbf_batch_destroy(batch: int) -> None:
     lib = load()
     _check(lib, lib.ngdbf_batch_destroy(batch))
+
+
+def ngdbf_server_create(budget_bytes: int, max_inflight: int = 4, max_jobs: int = 256, seed: int = 1) -> int:
+    lib = load()
+    h = ctypes.c_void_p()
+    _check(lib, lib.ngdbf_server_create(budget_bytes, max_inflight, max_jobs, seed, ctypes.byref(h)))
+    return h.value
+
+
+def ngdbf_server_submit(server: int, code: int, y_ptr: int, n_frames: int, sigma: float, params: ngdbf_params,
+                        frame_offset: int, bits_ptr: int, iters_ptr: int, pass_ptr: int) -> int:
+    lib = load()
+    rid = ctypes.c_uint64()
+    _check(lib, lib.ngdbf_server_submit(server, code, y_ptr, n_frames, sigma, ctypes.byref(params), frame_offset,
+                                        bits_ptr, iters_ptr, pass_ptr, ctypes.byref(rid)))
+    return rid.value
+
+
+def ngdbf_server_poll(server: int, capacity: int = 4096):
+    lib = load()
+    ids = (ctypes.c_uint64 * capacity)()
+    lat = (ctypes.c_double * capacity)()
+    st = (ctypes.c_int32 * capacity)()
+    n = ctypes.c_int32()
+    _check(lib, lib.ngdbf_server_poll(server, ids, lat, st, capacity, ctypes.byref(n)))
+    return [(ids[i], lat[i], st[i]) for i in range(n.value)]
+
+
+def ngdbf_server_wait(server: int, timeout_s: float) -> None:
+    lib = load()
+    _check(lib, lib.ngdbf_server_wait(server, timeout_s))
+
+
+def ngdbf_server_get_stats(server: int) -> dict:
+    lib = load()
+    st = ngdbf_server_stats()
+    _check(lib, lib.ngdbf_server_get_stats(server, ctypes.byref(st)))
+    return {f: getattr(st, f) for f, _ in st._fields_ if f != "reserved"}
+
+
+def ngdbf_server_destroy(server: int) -> None:
+    lib = load()
+    _check(lib, lib.ngdbf_server_destroy(server))
 
 
 def ngdbf_last_launch() -> dict:
@@ -287,6 +347,51 @@ class Batch:
         if self.handle:
             ngdbf_batch_destroy(self.handle)
             self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-batching decode server over host buffers (numpy arrays or pinned CPU tensors)."""
+
+    def __init__(self, budget_bytes: int, max_inflight: int = 4, max_jobs: int = 256, seed: int = 1):
+        self.handle = ngdbf_server_create(budget_bytes, max_inflight, max_jobs, seed)
+        self._live = {}
+
+    @staticmethod
+    def _ptr(a):
+        return a.ctypes.data if isinstance(a, np.ndarray) else a.data_ptr()
+
+    def submit(self, code: "DeviceCode", y, sigma: float, params: ngdbf_params, frame_offset: int = 0, out=None):
+        F = y.shape[0]
+        if out is None:
+            out = (np.empty((F, (code.n + 7) // 8), np.uint8), np.empty(F, np.int32), np.empty(F, np.uint8))
+        rid = ngdbf_server_submit(self.handle, code.handle, self._ptr(y), F, float(sigma), params,
+                                  int(frame_offset), *[self._ptr(o) for o in out])
+        self._live[rid] = (y, out, code)          # keep buffers alive until completion
+        return rid, out
+
+    def poll(self):
+        done = ngdbf_server_poll(self.handle)
+        for rid, _, _ in done:
+            self._live.pop(rid, None)
+        return done
+
+    def wait(self, timeout_s: float = 600.0):
+        ngdbf_server_wait(self.handle, timeout_s)
+
+    def stats(self) -> dict:
+        return ngdbf_server_get_stats(self.handle)
+
+    def close(self):
+        if self.handle:
+            ngdbf_server_destroy(self.handle)
+            self.handle = None
+            self._live.clear()
 
     def __del__(self):
         try:

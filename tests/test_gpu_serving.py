@@ -1,0 +1,120 @@
+"""Serving loop: requests of different codes and sizes admitted under a memory budget, packed
+into overlapping job-table launches; every result equals the request decoded alone."""
+import os
+import threading
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1402_2773_gb300 import ngdbf, workload as wl
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+THREADS = os.cpu_count() or 1
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1402_2773_gb300 import _build
+    _build.build_cuda()
+    ngdbf.load()
+    torch.cuda.set_device(0)
+
+
+@pytest.fixture(scope="module")
+def codes():
+    return [wl.peg_code(504, 252, 3, seed=1), wl.code_c1(), wl.peg_code(1024, 512, 4, seed=1), wl.code_c2()]
+
+
+def requests(codes, count, seed):
+    rng = np.random.default_rng(seed)
+    out = []
+    for r in range(count):
+        c = int(rng.integers(len(codes)))
+        code = codes[c]
+        F = int(rng.integers(1, 300))
+        eb = float(rng.uniform(3.0, 4.5))
+        T = int(rng.integers(60, 200))
+        y, _, sig = wl.frames(code, F, eb, seed=1000 + r)
+        kw = dict(w=0.75 if c < 3 else 0.1875, theta=-0.9 if c < 3 else -0.7, eta=0.9 if c < 3 else 0.65,
+                  lam=0.99, y_max=2.5 if c < 3 else 2.0, t_max=T, smooth_window=64, variant=3)
+        out.append(dict(c=c, y=torch.from_numpy(y).pin_memory(), sigma=sig, kw=kw, off=10_000 * r))
+    return out
+
+
+def decode_alone(dcs, reqs, seed):
+    res = []
+    for q in reqs:
+        dc = dcs[q["c"]]
+        b, i, p = dc.decode(q["y"].cuda(), q["sigma"], ngdbf.make_params(**q["kw"]), seed=seed, frame_offset=q["off"])
+        torch.cuda.synchronize()
+        res.append((b.cpu().numpy(), i.cpu().numpy(), p.cpu().numpy()))
+    return res
+
+
+def serve(dcs, reqs, budget, inflight, max_jobs, seed, threads=1):
+    srv = ngdbf.Server(budget, max_inflight=inflight, max_jobs=max_jobs, seed=seed)
+    outs = [None] * len(reqs)
+
+    def submit(idx):
+        for k in idx:
+            q = reqs[k]
+            F = q["y"].shape[0]
+            n = dcs[q["c"]].n
+            buf = (torch.empty((F, (n + 7) // 8), dtype=torch.uint8).pin_memory(),
+                   torch.empty(F, dtype=torch.int32).pin_memory(), torch.empty(F, dtype=torch.uint8).pin_memory())
+            _, outs[k] = srv.submit(dcs[q["c"]], q["y"], q["sigma"], ngdbf.make_params(**q["kw"]), q["off"], out=buf)
+
+    parts = [list(range(t, len(reqs), threads)) for t in range(threads)]
+    ths = [threading.Thread(target=submit, args=(p,)) for p in parts]
+    for t in ths:
+        t.start()
+    for t in ths:
+        t.join()
+    srv.wait(600)
+    done = srv.poll()
+    stats = srv.stats()
+    srv.close()
+    return [tuple(o.numpy() for o in out) for out in outs], done, stats
+
+
+def test_mix_equals_alone(codes):
+    dcs = [ngdbf.DeviceCode.from_code(c) for c in codes]
+    reqs = requests(codes, 60, seed=1)
+    alone = decode_alone(dcs, reqs, seed=5)
+    got, done, stats = serve(dcs, reqs, budget=2 << 30, inflight=4, max_jobs=16, seed=5, threads=3)
+    assert len(done) == len(reqs) and all(st == 0 for _, _, st in done)
+    for g, a in zip(got, alone):
+        assert all((x == y).all() for x, y in zip(g, a)), "served result differs from the request alone"
+    assert stats["completed"] == len(reqs) and stats["failed"] == 0
+    assert stats["launches"] >= 2 and stats["peak_concurrent_launches"] >= 2
+    assert stats["peak_bytes_in_use"] <= 2 << 30
+    # a few requests against the reference decoder
+    O = oracle.load()
+    for q, g in list(zip(reqs, got))[:6]:
+        ob, oi, op = O.decode_f32(codes[q["c"]], q["y"].numpy(), q["sigma"], oracle.make_params(**q["kw"]), seed=5,
+                                  frame_offset=q["off"], threads=THREADS)
+        assert (g[0] == ob).all() and (g[1] == oi).all() and (g[2] == op).all()
+    for dc in dcs:
+        dc.close()
+
+
+def test_tight_budget_and_oversized_request(codes):
+    dcs = [ngdbf.DeviceCode.from_code(c) for c in codes]
+    reqs = requests(codes, 12, seed=2)
+    alone = decode_alone(dcs, reqs, seed=6)
+    budget = 160 << 20                     # about one launch at a time
+    big = dict(c=3, y=torch.zeros((20000, codes[3].n), dtype=torch.float32).pin_memory(), sigma=0.5,
+               kw=reqs[0]["kw"] | dict(w=0.1875), off=0)
+    got, done, stats = serve(dcs, reqs + [big], budget=budget, inflight=3, max_jobs=4, seed=6)
+    status = {rid: st for rid, _, st in done}
+    assert len(done) == len(reqs) + 1
+    assert sorted(status.values()).count(ngdbf.NGDBF_ERR_OOM) == 1      # the oversized request only
+    for g, a in zip(got[:-1], alone):
+        assert all((x == y).all() for x, y in zip(g, a))
+    assert stats["peak_bytes_in_use"] <= budget and stats["failed"] == 1
+    for dc in dcs:
+        dc.close()
