@@ -59,8 +59,11 @@ typedef enum {
     NGDBF_ERR_TIMEOUT = 5        /* a wait ran out of time */
 } ngdbf_status;
 
-/* Variant bits (Sec. III-C/D/E).  0 = plain M-NGDBF with one threshold. */
-enum { NGDBF_ADAPT = 1, NGDBF_SMOOTH = 2 };
+/* Variant bits (Sec. III-C/D/E).  0 = plain M-NGDBF with one threshold.
+ * NGDBF_SINGLE: S-NGDBF, Step 3a of Sec. III-B with the noisy Step 2 of Sec. III-C:
+ * each iteration flips only the symbol with the least E_k (ties go to the lowest k);
+ * no threshold, so it excludes NGDBF_ADAPT; NGDBF_SMOOTH may be added. */
+enum { NGDBF_ADAPT = 1, NGDBF_SMOOTH = 2, NGDBF_SINGLE = 4 };
 
 /* Arithmetic of the held samples and the inversion function (Sec. IV-E); the
  * perturbation is always the FP32 generator output.
@@ -91,7 +94,7 @@ typedef struct ngdbf_params {
     float y_max;          /* saturation magnitude; <= 0 or +inf disables (Sec. IV-A) */
     int32_t t_max;        /* T: at most T flip phases, 0 <= T <= NGDBF_MAX_T */
     int32_t smooth_window;/* W: X_k sums x(t) for t = max(0, T-W) .. T, 0 <= W <= 126 */
-    int32_t variant;      /* OR of NGDBF_ADAPT, NGDBF_SMOOTH */
+    int32_t variant;      /* OR of NGDBF_ADAPT, NGDBF_SMOOTH, NGDBF_SINGLE (not with ADAPT) */
     int32_t precision;    /* NGDBF_FP32, NGDBF_FP16 or NGDBF_FIX */
     int32_t q_bits;       /* NGDBF_FIX: Q in 2..8 (needs a finite y_max > 0); otherwise 0 */
 } ngdbf_params;

@@ -26,6 +26,7 @@ CFLAGS = ["-O2", "-fPIC", "-shared", "-std=c11", "-ffp-contract=off", "-fno-fast
 
 ADAPT = 1
 SMOOTH = 2
+SINGLE = 4
 FP32 = 0
 FP16 = 1
 FIX = 2

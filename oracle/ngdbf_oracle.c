@@ -9,7 +9,8 @@
  *
  * Paper sections followed:
  *   Sec. III-A  notation: H, N(i), M(k), x(0) = sign(y), bipolar syndromes
- *   Sec. III-B  GDBF Steps 1-4 (Step 1 syndrome + stop, Step 3b multi-bit flip)
+ *   Sec. III-B  GDBF Steps 1-4 (Step 1 syndrome + stop, Step 3b multi-bit flip,
+ *               Step 3a single-bit flip of argmin E_k for S-NGDBF)
  *   Sec. III-C  NGDBF Step 2: E_k = x_k y_k + w sum_{i in M(k)} s_i + q_k,
  *               q_k ~ N(0, eta^2 N0/2)
  *   Sec. III-D  threshold adaptation Steps 0 and 3b (theta_k <- theta_k lambda
@@ -26,6 +27,8 @@
  *     T flip phases at most, iters = T and pass = 0 when T is reached.
  *   - Flooding schedule: every E_k of iteration t uses the syndromes of t.
  *   - Strict E_k < theta_k flips; a tie adapts (u_k += 1).
+ *   - Single-bit (Step 3a): the flipped symbol is the first k with the least
+ *     E_k (ties go to the lowest index); no threshold, no adaptation.
  *   - The smoothing sum covers x(t) for t = max(0, T-W) .. T; a zero sum keeps
  *     x_k(T).
  *   - Perturbation std = eta * sigma with sigma the channel std (N0/2 = sigma^2).
@@ -64,6 +67,7 @@
 
 #define ORC_ADAPT 1
 #define ORC_SMOOTH 2
+#define ORC_SINGLE 4
 #define ORC_FP32 0
 #define ORC_FP16 1
 #define ORC_FIX 2
@@ -371,6 +375,7 @@ static void decode_frame(const orc_ctx* X, const float* y, uint64_t frame_id,
     const int32_t n = C->n, m = C->m, T = P->t_max;
     const int adapt = (P->variant & ORC_ADAPT) != 0;
     const int smooth = (P->variant & ORC_SMOOTH) != 0;
+    const int single = (P->variant & ORC_SINGLE) != 0;
     int8_t* x = (int8_t*)ws;                       /* n bytes */
     int8_t* s = (int8_t*)(ws + (n + 3) / 4);       /* m bytes */
     int32_t* u = ws + (n + 3) / 4 + (m + 3) / 4;   /* n */
@@ -420,7 +425,12 @@ static void decode_frame(const orc_ctx* X, const float* y, uint64_t frame_id,
         if (t >= t_smooth)
             for (int32_t k = 0; k < n; ++k) Xs[k] += x[k];
         if (t == T) break;
-        /* Step 2 (noisy inversion function) and Step 3b (flip / adapt). */
+        /* Step 2 (noisy inversion function) and Step 3b (flip / adapt), or Step 3a
+         * (single-bit): find the first k with the least E_k, flip it after the sweep. */
+        int32_t best_k = -1;
+        double best64 = 0.0;
+        float best32 = 0.0f;
+        int32_t best_fix = 0;
         for (int32_t k = 0; k < n; ++k) {
             int S = 0;
             for (int32_t e = C->sym_ptr[k]; e < C->sym_ptr[k + 1]; ++e) S += s[C->chk_idx[e]];
@@ -430,6 +440,7 @@ static void decode_frame(const orc_ctx* X, const float* y, uint64_t frame_id,
                 double q = X->scale64 * z64[k & 3];
                 double E = oracle_metric_f64(x[k], ys64[k], S, (double)P->w, q);
                 flip = E < X->thr64[u[k]];
+                if (single && (best_k < 0 || E < best64)) { best_k = k; best64 = E; }
             } else {
                 float q;
                 if (X->q_in) {
@@ -441,18 +452,23 @@ static void decode_frame(const orc_ctx* X, const float* y, uint64_t frame_id,
                 if (X->precision == ORC_FP16) {
                     const float E = oracle_metric_f16(x[k], ys32[k], S, X->w16, q);
                     flip = E < X->thr16[u[k]];
+                    if (single && (best_k < 0 || E < best32)) { best_k = k; best32 = E; }
                 } else if (X->precision == ORC_FIX) {
                     /* Eq. 9 in units of Delta/2: exact integers */
                     const int32_t Eq = x[k] * yfix[k] + X->fix_W * S + fix_value(q, X->fix_R, X->fix_kmax);
                     flip = Eq < X->thr_fix[u[k]];
+                    if (single && (best_k < 0 || Eq < best_fix)) { best_k = k; best_fix = Eq; }
                 } else {
                     float E = oracle_metric_f32(x[k], ys32[k], S, P->w, q);
                     flip = E < X->thr32[u[k]];
+                    if (single && (best_k < 0 || E < best32)) { best_k = k; best32 = E; }
                 }
             }
+            if (single) continue;
             if (flip) x[k] = (int8_t)-x[k];
             else if (adapt) u[k] += 1;
         }
+        if (single) x[best_k] = (int8_t)-x[best_k];
     }
     /* T reached: smoothed decision sign(X_k) (Sec. III-E), zero keeps x_k(T). */
     if (smooth)
@@ -497,6 +513,7 @@ static int check_args(int32_t n, int32_t m, const int32_t* row_ptr, const int32_
     for (int32_t e = 0; e < row_ptr[m]; ++e) if (col_idx[e] < 0 || col_idx[e] >= n) return -1;
     if (P->t_max < 0 || P->smooth_window < 0) return -1;
     if (P->precision < ORC_FP32 || P->precision > ORC_FIX) return -1;
+    if ((P->variant & ORC_SINGLE) && (P->variant & ORC_ADAPT)) return -1;
     if (P->precision == ORC_FIX && (P->q_bits < 2 || P->q_bits > 8 || !(P->y_max > 0.0f) || !isfinite(P->y_max)))
         return -1;
     return 0;

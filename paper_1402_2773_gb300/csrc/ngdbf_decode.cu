@@ -223,6 +223,7 @@ void fill_job(const ngdbf_code* C, const ngdbf_params* P, const float* y, int64_
     J.t_max = P->t_max;
     J.t_smooth = std::max(0, P->t_max - P->smooth_window);
     J.queue = queue;
+    J.single = (P->variant & NGDBF_SINGLE) ? 1 : 0;
     if (P->precision == NGDBF_FIX) {
         J.fix_R = (float)(std::ldexp(1.0, P->q_bits) / (2.0 * (double)P->y_max));
         J.fix_kmax = (1 << (P->q_bits - 1)) - 1;
@@ -273,7 +274,9 @@ ngdbf_status check_params(const ngdbf_params* P, float sigma) {
     if (P->t_max > NGDBF_MAX_T) return fail(NGDBF_ERR_UNSUPPORTED, "t_max above NGDBF_MAX_T");
     if (P->smooth_window < 0) return fail(NGDBF_ERR_INVALID_ARG, "smooth_window must be >= 0");
     if (P->smooth_window > NGDBF_MAX_WINDOW) return fail(NGDBF_ERR_UNSUPPORTED, "smooth_window above NGDBF_MAX_WINDOW");
-    if (P->variant & ~3) return fail(NGDBF_ERR_INVALID_ARG, "unknown variant bits");
+    if (P->variant & ~7) return fail(NGDBF_ERR_INVALID_ARG, "unknown variant bits");
+    if ((P->variant & NGDBF_SINGLE) && (P->variant & NGDBF_ADAPT))
+        return fail(NGDBF_ERR_INVALID_ARG, "the single-bit variant has no threshold to adapt");
     if (P->precision < NGDBF_FP32 || P->precision > NGDBF_FIX) return fail(NGDBF_ERR_INVALID_ARG, "unknown precision");
     if (P->precision == NGDBF_FIX) {
         if (P->q_bits < 2 || P->q_bits > 8) return fail(NGDBF_ERR_INVALID_ARG, "fixed point needs 2 <= q_bits <= 8");

@@ -79,6 +79,7 @@ struct Job {
     // them inline instead)
     const uint32_t* thr;
     unsigned long long* queue;  // next unclaimed frame of this job
+    int32_t single;             // Step 3a: flip only the symbol with the least E_k (ties: lowest k)
 };
 
 // Launch of one job: the job and its thresholds travel as kernel parameters.
@@ -106,7 +107,8 @@ struct MultiArgs {
 };
 
 struct SmemLayout {
-    int32_t off_frame, off_start, off_ctl, off_xw, off_sw, off_cnt, off_thr, off_st, off_chk, off_sym, total;
+    int32_t off_frame, off_start, off_ctl, off_best, off_xw, off_sw, off_cnt, off_thr, off_st, off_chk, off_sym,
+        total;
 };
 
 // Offsets in bytes of the shared-memory arrays.  ctl holds: [0..1] unsatisfied
@@ -128,6 +130,7 @@ __host__ __device__ inline SmemLayout smem_layout(int n, int m, int t_max, int d
     L.off_frame = take(kSlots * 8, 16);
     L.off_start = take(kSlots * 4, 16);
     L.off_ctl = take(8 * 4, 16);
+    L.off_best = take(kSlots * 8, 16);     // single-bit variant: least (E key, k) per slot
     L.off_cnt = take(n * cnt_bytes, 16);
     L.off_xw = take((n + 1) * 4, 16);
     L.off_sw = take((m + 1) * 4, 16);
@@ -150,6 +153,13 @@ __host__ __device__ inline int32_t fix_code(float v, float R, int32_t kmax) {
     const int32_t k = (a < (float)kmax) ? (int32_t)std::floor(a) : kmax;
 #endif
     return v >= 0.0f ? k : -k - 1;
+}
+
+// Order-preserving 32-bit key of an FP32 value (-0 counts as +0, as a comparison would).
+__device__ __forceinline__ uint32_t order_key(float v) {
+    uint32_t b = __float_as_uint(v);
+    if (b == 0x80000000u) b = 0u;
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
 }
 
 // Rounds an FP32 value to binary16 (nearest even) and back.
@@ -179,6 +189,7 @@ __device__ __forceinline__ void decode_job(const Job& A, const uint32_t* thr_src
     uint4* cnt = reinterpret_cast<uint4*>(smem + L.off_cnt);
     uint32_t* xw = reinterpret_cast<uint32_t*>(smem + L.off_xw);
     uint32_t* sw = reinterpret_cast<uint32_t*>(smem + L.off_sw);
+    unsigned long long* best = reinterpret_cast<unsigned long long*>(smem + L.off_best);
     uint32_t* thr = ADAPT ? reinterpret_cast<uint32_t*>(smem + L.off_thr) : nullptr;
     uint16_t* st = nullptr;
     if constexpr (kState) {
@@ -209,6 +220,7 @@ __device__ __forceinline__ void decode_job(const Job& A, const uint32_t* thr_src
         for (int u = tid; u <= T; u += blockDim.x) thr[u] = thr_src[u];
     if constexpr (kState)
         for (int e = tid; e < n * kSlots; e += blockDim.x) st[e] = 0;
+    if (tid < kSlots) best[tid] = ~0ull;
     if (tid == 0) {
         for (int c = 0; c < 8; ++c) ctl[c] = 0u;
         const unsigned long long base = atomicAdd(A.queue, (unsigned long long)kSlots);
@@ -403,6 +415,8 @@ __device__ __forceinline__ void decode_job(const Job& A, const uint32_t* thr_src
             const uint32_t th0 = thr_src[0];    // threshold of the non-adaptive variants
             const float scale = A.scale, wgt = A.w, fix_R = A.fix_R;
             const int32_t fix_kmax = A.fix_kmax, fix_W = A.fix_W;
+            const bool single = !ADAPT && A.single;
+            unsigned long long my_best = ~0ull;      // single-bit variant: (E key << 32) | k
             for (int g = warp; g < groups; g += nwarps) {
                 const int k0 = 4 * g;
                 // issue the sample and state loads before the generator's arithmetic
@@ -458,6 +472,31 @@ __device__ __forceinline__ void decode_job(const Job& A, const uint32_t* thr_src
                             return (xneg ? -Y : Y) + fix_W * S + Qv < (int32_t)th_bits;
                         }
                     };
+                    if constexpr (!ADAPT) {
+                        if (single) {
+                            // Step 3a: remember this lane's least E_k; flips wait for all symbols
+                            uint32_t key;
+                            if constexpr (PREC == kFP32) {
+                                key = order_key(inversion_metric(xneg, yv[j], S, wgt, q));
+                            } else if constexpr (PREC == kFP16) {
+                                const float y16 = __half2float(yv[j]);
+                                const float xy = xneg ? -y16 : y16;
+                                const float ws = to_half(__fmul_rn(wgt, __int2float_rn(S)));
+                                const float e1 = to_half(__fadd_rn(xy, ws));
+                                key = order_key(to_half(__fadd_rn(e1, to_half(q))));
+                            } else {
+                                const int32_t Y = 2 * (int32_t)yv[j] + 1;
+                                const int32_t Qv = 2 * fix_code(q, fix_R, fix_kmax) + 1;
+                                key = (uint32_t)((xneg ? -Y : Y) + fix_W * S + Qv) ^ 0x80000000u;
+                            }
+                            const unsigned long long cand = ((unsigned long long)key << 32) | (uint32_t)k;
+                            my_best = cand < my_best ? cand : my_best;
+                            if constexpr (SMOOTH) {
+                                if (window && xneg) st[k * kSlots + lane] = (uint16_t)(sv[j] + (1u << kCShift));
+                            }
+                            continue;
+                        }
+                    }
                     bool flip;
                     if constexpr (kState) {
                         const uint32_t s0 = sv[j];
@@ -474,6 +513,19 @@ __device__ __forceinline__ void decode_job(const Job& A, const uint32_t* thr_src
                     }
                     const uint32_t fm = __ballot_sync(0xFFFFFFFFu, flip);
                     if (lane == 0 && fm) xw[k] = xword ^ fm;
+                }
+            }
+            if constexpr (!ADAPT) {
+                if (single && act) atomicMin(best + lane, my_best);
+            }
+        }
+        if constexpr (!ADAPT) {
+            if (!ADAPT && A.single) {
+                __syncthreads();
+                // each live slot flips its least-E_k symbol (the lowest k among equal values)
+                if (tid < kSlots) {
+                    if ((live >> tid) & 1u) atomicXor(xw + (uint32_t)best[tid], 1u << tid);
+                    best[tid] = ~0ull;
                 }
             }
         }

@@ -23,6 +23,7 @@ NGDBF_ERR_UNSUPPORTED = 4
 NGDBF_ERR_TIMEOUT = 5
 NGDBF_ADAPT = 1
 NGDBF_SMOOTH = 2
+NGDBF_SINGLE = 4
 NGDBF_FP32 = 0
 NGDBF_FP16 = 1
 NGDBF_FIX = 2

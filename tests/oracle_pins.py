@@ -291,6 +291,55 @@ def _pin_code():
     return wl.peg_code(96, 48, 3, seed=11)
 
 
+def pin_trace_single_bit(O):
+    """Case J (Step 3a), dyadic samples y = (0.75, 0.875, 1.125, -0.25, 0.75, 1, 0.625), w = 0.5.
+    t = 0, s = (-1,-1,-1): E = (-0.25, -0.125, 0.125, -1.25, 0.25, 0.5, 0.125); argmin k = 3 alone,
+    so x_3 flips and t = 1 is valid (output 0, 1 iteration).  With q_0(0) = -1 the least value
+    -1.25 is shared by k = 0 and k = 3 and goes to the lower index: x_0 flips, x(1) = (-,+,+,-,+,+,+)
+    gives s = (+1,+1,-1) and E = (0.25, 0.875, 1.125, 0.75, 1.25, 1.5, 0.125), so x_6 flips and
+    t = 2 is valid with the codeword whose bits 0, 3, 6 are set (0x49)."""
+    C = hamming_code()
+    y = np.array([0.75, 0.875, 1.125, -0.25, 0.75, 1.0, 0.625], np.float32)
+    p = oracle_pkg.make_params(w=0.5, theta=-0.6, eta=0.0, lam=1.0, y_max=2.5, t_max=10, variant=oracle_pkg.SINGLE)
+    bits, it, ps = O.decode_f32_qin(C, y, p, np.zeros((10, 7), np.float32))
+    assert (_bits_byte(bits), it, ps) == (0, 1, 1)
+    q = np.zeros((10, 7), np.float32)
+    q[0, 0] = -1.0
+    bits, it, ps = O.decode_f32_qin(C, y, p, q)
+    assert (_bits_byte(bits), it, ps) == (0x49, 2, 1)
+
+
+def _sgdbf_dense(H, y, w, T, y_max):
+    """Textbook S-GDBF (Wadayama et al. 2010, single-bit): flip argmin E_k (first on ties), FP64."""
+    ys = np.clip(y.astype(np.float64), -y_max, y_max)
+    x = np.where(ys >= 0, 1, -1)
+    Hi = H.astype(np.int64)
+    for t in range(T + 1):
+        s = 1 - 2 * ((Hi @ (x < 0).astype(np.int64)) % 2)
+        if (s == 1).all():
+            return x, t, 1
+        if t == T:
+            break
+        E = x * ys + w * (Hi.T @ s)
+        k = int(np.argmin(E))
+        x[k] = -x[k]
+    return x, T, 0
+
+
+def pin_eta0_is_single_bit_gdbf(O):
+    """eta = 0 with the single-bit variant equals textbook S-GDBF evaluated densely."""
+    C = _pin_code()
+    H = C.dense()
+    y, _, sig = wl.frames(C, 60, 3.0, seed=19)
+    p = oracle_pkg.make_params(w=0.75, theta=-0.9, eta=0.0, lam=1.0, y_max=2.5, t_max=60, variant=oracle_pkg.SINGLE)
+    bits, it, ps = O.decode_f64(C, y, sig, p, seed=1)
+    xs = wl.unpack_bits(bits, C.n)
+    for f in range(y.shape[0]):
+        x, t, pa = _sgdbf_dense(H, y[f], float(np.float32(0.75)), 60, 2.5)
+        assert it[f] == t and ps[f] == pa and (xs[f] == (x < 0)).all(), f"frame {f}"
+    assert (ps == 1).any() and (ps == 0).any()
+
+
 def pin_noiseless(O):
     """A transmitted codeword (y = 1 - 2c) satisfies every check: iters = 0, pass = 1, output c."""
     C = _pin_code()
@@ -583,7 +632,8 @@ ALL_PINS = [
     pin_philox_kat, pin_ln_f32, pin_sincos_f32, pin_gauss_f32_vs_library, pin_gauss_statistics,
     pin_noise_variance, pin_threshold_table, pin_table2, pin_fig20, pin_quantizer,
     pin_trace_gdbf, pin_trace_injected_noise, pin_trace_adaptation, pin_trace_smoothing,
-    pin_trace_clamp_sign_tie, pin_noiseless, pin_eta0_is_gdbf, pin_codeword_and_ml,
+    pin_trace_clamp_sign_tie, pin_trace_single_bit, pin_noiseless, pin_eta0_is_gdbf,
+    pin_eta0_is_single_bit_gdbf, pin_codeword_and_ml,
     pin_f32_matches_injected_noise, pin_frame_independence, pin_f32_f64_statistics,
     pin_round_half, pin_metric_f16, pin_fix_quantizer, pin_trace_fixed_point, pin_table2_fixed_point, pin_fp16_reduces_to_fp32,
     pin_fix_reduces_to_fp32, pin_precision_statistics,

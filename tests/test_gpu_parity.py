@@ -253,6 +253,36 @@ def test_precision_variants_global_state_and_wide(O, prec):
     assert_parity(O, code, y, sig, seed=3, variant=3, lam=0.97, t_max=40, smooth_window=9, **prec)
 
 
+@pytest.mark.parametrize("prec", [dict(), *PRECISIONS[:2]], ids=["fp32", *PREC_IDS[:2]])
+@pytest.mark.parametrize("variant", [4, 6])
+def test_single_bit_variant(O, variant, prec):
+    """S-NGDBF (Step 3a): one flip per iteration, the least E_k (lowest k on ties)."""
+    code = wl.peg_code(504, 252, 3, seed=3)
+    y, _, sig = wl.frames(code, 70, 4.0, seed=41)
+    assert_parity(O, code, y, sig, seed=6, variant=variant, eta=1.0, t_max=100, smooth_window=20, **prec)
+    code = wl.code_c1()
+    y, _, sig = wl.frames(code, 100, 4.5, seed=42)
+    assert_parity(O, code, y, sig, seed=6, variant=variant, eta=1.0, t_max=100, smooth_window=20, **prec)
+
+
+def test_single_bit_ties_and_wide_and_global_state(O):
+    # eta = 0 with dyadic samples makes equal E_k common: ties must go to the lowest k
+    code = wl.peg_code(504, 252, 3, seed=3)
+    rng = np.random.default_rng(43)
+    y, _, _ = wl.frames(code, 64, None, seed=43)
+    y = (y + rng.integers(-12, 13, size=y.shape) / 8).astype(np.float32)
+    assert_parity(O, code, y, 0.5, seed=2, variant=4, eta=0.0, w=0.5, t_max=60)
+    code = irregular_code(203, 101, seed=5)
+    H = code.dense()
+    H[:9, 0] = 1
+    code = wl.code_from_dense(H)
+    y, _, sig = wl.frames(code, 40, 3.5, seed=44)
+    assert_parity(O, code, y, sig, seed=3, variant=6, eta=1.0, t_max=50, smooth_window=9)
+    code = wl.peg_code(8192, 1639, 3, seed=1)
+    y, _, sig = wl.frames(code, 8, 5.0, seed=45)
+    assert_parity(O, code, y, sig, seed=3, variant=6, eta=1.0, t_max=30, smooth_window=9, w=0.5, theta=-0.7)
+
+
 def test_invalid_arguments_report_status():
     code = wl.peg_code(504, 252, 3, seed=3)
     dc = ngdbf.DeviceCode.from_code(code)
@@ -267,7 +297,7 @@ def test_invalid_arguments_report_status():
         dc.decode(y, -1.0, ngdbf.make_params())
     assert e.value.status == ngdbf.NGDBF_ERR_INVALID_ARG
     for bad in (dict(precision=ngdbf.NGDBF_FIX, q_bits=9), dict(precision=ngdbf.NGDBF_FIX, q_bits=8, y_max=0.0),
-                dict(precision=ngdbf.NGDBF_FP16, q_bits=4), dict(precision=7)):
+                dict(precision=ngdbf.NGDBF_FP16, q_bits=4), dict(precision=7), dict(variant=5), dict(variant=8)):
         with pytest.raises(ngdbf.NgdbfError) as e:
             dc.decode(y, 0.5, ngdbf.make_params(**bad))
         assert e.value.status == ngdbf.NGDBF_ERR_INVALID_ARG

@@ -66,6 +66,9 @@ MUTANTS = [
     ("fix negative code", "return v >= 0.0f ? k : -k - 1;", "return v >= 0.0f ? k : -k;"),
     ("fix value", "return 2 * oracle_fix_code(v, R, kmax) + 1;", "return 2 * oracle_fix_code(v, R, kmax);"),
     ("fix weight", "X.fix_W = fix_value(P->w, X.fix_R, X.fix_kmax);", "X.fix_W = fix_value(P->w, X.fix_R, X.fix_kmax) + 2;"),
+    ("single-bit tie to the higher index", "if (single && (best_k < 0 || E < best32)) { best_k = k; best32 = E; }\n                }\n            }",
+     "if (single && (best_k < 0 || E <= best32)) { best_k = k; best32 = E; }\n                }\n            }"),
+    ("single-bit flips every symbol", "            if (single) continue;\n", ""),
     ("fix metric sign", "const int32_t Eq = x[k] * yfix[k] + X->fix_W * S", "const int32_t Eq = x[k] * yfix[k] - X->fix_W * S"),
 ]
 
