@@ -82,6 +82,10 @@ class Oracle:
         lib.oracle_noise_f32.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
                                          ctypes.c_float, ctypes.c_float]
         lib.oracle_noise_f32.restype = ctypes.c_float
+        lib.oracle_rho_all.argtypes = [f32p]
+        lib.oracle_rho_all.restype = None
+        lib.oracle_sincos_all.argtypes = [f32p, f32p]
+        lib.oracle_sincos_all.restype = None
         lib.oracle_threshold_table_f32.argtypes = [ctypes.c_float, ctypes.c_float, ctypes.c_int32, f32p]
         lib.oracle_threshold_table_f32.restype = None
         lib.oracle_metric_f32.argtypes = [ctypes.c_int, ctypes.c_float, ctypes.c_int, ctypes.c_float,
@@ -144,6 +148,20 @@ class Oracle:
 
     def noise_f32(self, seed, frame, t, k, eta, sigma) -> np.float32:
         return np.float32(self.lib.oracle_noise_f32(seed, frame, t, k, eta, sigma))
+
+    def rho_all(self) -> np.ndarray:
+        """rho(a) = sqrt(-2 ln u(a)) for every 23-bit a."""
+        out = np.empty(1 << 23, dtype=np.float32)
+        self.lib.oracle_rho_all(out.ctypes.data_as(ctypes.POINTER(ctypes.c_float)))
+        return out
+
+    def sincos_all(self):
+        """(sin, cos)(2 pi u(a)) for every 23-bit a."""
+        sn = np.empty(1 << 23, dtype=np.float32)
+        cs = np.empty(1 << 23, dtype=np.float32)
+        self.lib.oracle_sincos_all(sn.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                   cs.ctypes.data_as(ctypes.POINTER(ctypes.c_float)))
+        return sn, cs
 
     # -- thresholds / metric / quantizer ---------------------------------------
     def threshold_table_f32(self, theta, lam, t_max) -> np.ndarray:

@@ -192,6 +192,17 @@ void oracle_gauss4_f32(uint64_t seed, uint64_t frame, uint32_t t, uint32_t g, fl
     }
 }
 
+/* The generator's two factors over their whole input range a = 0 .. 2^23 - 1:
+ * rho(a) = sqrt(-2 ln u), (sin, cos)(2 pi u) with u = (a + 1/2) 2^-23. */
+void oracle_rho_all(float* rho) {
+    for (uint32_t a = 0; a < (1u << 23); ++a)
+        rho[a] = sqrtf(-2.0f * oracle_ln_f32(((float)a + 0.5f) * 0x1.0p-23f));
+}
+
+void oracle_sincos_all(float* sn, float* cs) {
+    for (uint32_t a = 0; a < (1u << 23); ++a) oracle_sincos2pi_f32(a, sn + a, cs + a);
+}
+
 void oracle_gauss4_f64(uint64_t seed, uint64_t frame, uint32_t t, uint32_t g, double z[4]) {
     uint32_t ctr[4] = {g, t, (uint32_t)frame, (uint32_t)(frame >> 32)};
     uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};

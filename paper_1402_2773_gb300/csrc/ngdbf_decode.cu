@@ -18,6 +18,14 @@
 
 namespace ngdbf {
 
+// The generator's two factors for every 23-bit input (verification entry point).
+__global__ void generator_factors_kernel(const __grid_constant__ GenConsts G, float* rho, float* sn, float* cs) {
+    const uint32_t a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= (1u << 23)) return;
+    rho[a] = __fsqrt_rn(__fmul_rn(-2.0f, ln_series(half_offset_fraction(a), G)));
+    sincos_2pi(a, G, sn[a], cs[a]);
+}
+
 template <bool ADAPT, bool SMOOTH, bool ST_SMEM, bool WIDE, int PREC>
 __global__ void __launch_bounds__(1024) ngdbf_persistent_kernel(const __grid_constant__ DecodeArgs A) {
     using HeldT = typename Held<PREC>::T;
@@ -925,5 +933,23 @@ extern "C" ngdbf_status ngdbf_batch_launch(ngdbf_batch_t* B, void* stream_ptr) {
 
 extern "C" ngdbf_status ngdbf_batch_destroy(ngdbf_batch_t* B) {
     batch_free(B);
+    return NGDBF_OK;
+}
+
+extern "C" ngdbf_status ngdbf_generator_factors(float* rho, float* sin_2pi, float* cos_2pi, void* stream) {
+    if (!rho || !sin_2pi || !cos_2pi) return fail(NGDBF_ERR_INVALID_ARG, "NULL buffer");
+    for (const void* p : {(const void*)rho, (const void*)sin_2pi, (const void*)cos_2pi}) {
+        cudaPointerAttributes a;
+        cudaError_t e = cudaPointerGetAttributes(&a, p);
+        if (e != cudaSuccess || !(a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged)) {
+            cudaGetLastError();
+            return fail(NGDBF_ERR_INVALID_ARG, "buffers must be device memory");
+        }
+    }
+    GenConsts G;
+    host_gen_consts(0, G);
+    generator_factors_kernel<<<(1u << 23) / 256, 256, 0, static_cast<cudaStream_t>(stream)>>>(G, rho, sin_2pi, cos_2pi);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "generator factors");
     return NGDBF_OK;
 }

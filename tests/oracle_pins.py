@@ -628,6 +628,25 @@ def pin_precision_statistics(O):
         assert (res[prec][1] == res[oracle_pkg.FP32][1]).mean() > 0.3
 
 
+def pin_generator_factors_whole_domain(O):
+    """Over all 2^23 inputs: rho within 1.5 ulp of fp64 sqrt(-2 ln u), sin/cos(2 pi u) within
+    2^-23 of fp64, exact quarter-turn symmetry, and the batch evaluators equal the single ones."""
+    rho = O.rho_all().astype(np.float64)
+    sn, cs = O.sincos_all()
+    a = np.arange(1 << 23)
+    u = (a + 0.5) * 2.0 ** -23
+    ulp = np.spacing(rho.astype(np.float32)).astype(np.float64)
+    assert np.max(np.abs(rho - np.sqrt(-2.0 * np.log(u))) / ulp) <= 1.5
+    assert np.max(np.abs(sn - np.sin(2 * np.pi * u))) <= 2.0 ** -23
+    assert np.max(np.abs(cs - np.cos(2 * np.pi * u))) <= 2.0 ** -23
+    q = (a + (1 << 21)) % (1 << 23)
+    assert (sn[q] == cs).all() and (cs[q] == -sn).all()
+    for ai in (0, 1, 77777, 1 << 21, (1 << 23) - 1):
+        u32 = float(np.float32((ai + 0.5) * 2.0 ** -23))
+        assert np.float32(np.sqrt(np.float32(-2.0) * O.ln_f32(u32))) == np.float32(rho[ai])
+        assert O.sincos2pi_f32(ai) == (sn[ai], cs[ai])
+
+
 ALL_PINS = [
     pin_philox_kat, pin_ln_f32, pin_sincos_f32, pin_gauss_f32_vs_library, pin_gauss_statistics,
     pin_noise_variance, pin_threshold_table, pin_table2, pin_fig20, pin_quantizer,
@@ -636,5 +655,5 @@ ALL_PINS = [
     pin_eta0_is_single_bit_gdbf, pin_codeword_and_ml,
     pin_f32_matches_injected_noise, pin_frame_independence, pin_f32_f64_statistics,
     pin_round_half, pin_metric_f16, pin_fix_quantizer, pin_trace_fixed_point, pin_table2_fixed_point, pin_fp16_reduces_to_fp32,
-    pin_fix_reduces_to_fp32, pin_precision_statistics,
+    pin_fix_reduces_to_fp32, pin_precision_statistics, pin_generator_factors_whole_domain,
 ]
