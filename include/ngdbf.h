@@ -296,16 +296,16 @@ ngdbf_status ngdbf_server_get_stats(ngdbf_server_t* server, ngdbf_server_stats* 
 ngdbf_status ngdbf_server_destroy(ngdbf_server_t* server);
 
 /*
- * Verification of the perturbation generator: evaluates its two factors over
- * their whole input range a = 0 .. 2^23 - 1 with u = (a + 1/2) 2^-23, exactly as
- * the decode kernels compute them: rho[a] = sqrt(-2 ln u) (the Box-Muller radius
- * of an output r with r >> 9 = a) and sin_2pi[a], cos_2pi[a] = sin and cos of
- * 2 pi u (the angle of an output r with r >> 9 = a).  Every perturbation is
- * fl32(eta sigma) * fl32(rho * sin or cos), so comparing these 3 x 2^23 values
- * with an independent evaluation covers every value the generator can produce.
- * rho, sin_2pi, cos_2pi: DEVICE float[2^23] each; asynchronous on `stream`.
+ * Verification of the perturbation generator: z[i] = the standard normal deviate that
+ * Philox output r = start + i (mod 2^32) gives, exactly as the decode kernels compute
+ * it (inverse normal CDF, Sec. III-C draws q_k ~ N(0, eta^2 sigma^2); q_k = fl32(eta
+ * sigma) * z).  Sweeping r over all 2^32 values and comparing with an independent
+ * evaluation covers every deviate the generator can produce.  The paper has no
+ * counterpart: its hardware draws from one shared Gaussian source (Sec. V-B).
+ * z: DEVICE float[count]; asynchronous on `stream`; count = 0 is a no-op.
+ * INVALID_ARG for a NULL or host z.
  */
-ngdbf_status ngdbf_generator_factors(float* rho, float* sin_2pi, float* cos_2pi, void* stream);
+ngdbf_status ngdbf_gaussian_range(uint32_t start, uint32_t count, float* z, void* stream);
 
 /* Launch shape of the most recent ngdbf_decode* or ngdbf_batch_* call on the calling thread. */
 typedef struct ngdbf_launch_info {

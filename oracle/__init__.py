@@ -71,10 +71,16 @@ class Oracle:
         u8p = ctypes.POINTER(ctypes.c_uint8)
         lib.oracle_philox4x32_10.argtypes = [u32p, u32p, u32p]
         lib.oracle_philox4x32_10.restype = None
-        lib.oracle_ln_f32.argtypes = [ctypes.c_float]
-        lib.oracle_ln_f32.restype = ctypes.c_float
-        lib.oracle_sincos2pi_f32.argtypes = [ctypes.c_uint32, f32p, f32p]
-        lib.oracle_sincos2pi_f32.restype = None
+        lib.oracle_gauss_f32.argtypes = [ctypes.c_uint32]
+        lib.oracle_gauss_f32.restype = ctypes.c_float
+        lib.oracle_gauss_f64.argtypes = [ctypes.c_uint32]
+        lib.oracle_gauss_f64.restype = ctypes.c_double
+        lib.oracle_gauss_range_f32.argtypes = [ctypes.c_uint32, ctypes.c_uint32, f32p]
+        lib.oracle_gauss_range_f32.restype = None
+        lib.oracle_gauss_many_f32.argtypes = [u32p, ctypes.c_uint32, f32p]
+        lib.oracle_gauss_many_f32.restype = None
+        lib.oracle_icdf_table.argtypes = [f32p]
+        lib.oracle_icdf_table.restype = None
         for nm, zt in (("oracle_gauss4_f32", f32p), ("oracle_gauss4_f64", f64p)):
             fn = getattr(lib, nm)
             fn.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, zt]
@@ -82,10 +88,6 @@ class Oracle:
         lib.oracle_noise_f32.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
                                          ctypes.c_float, ctypes.c_float]
         lib.oracle_noise_f32.restype = ctypes.c_float
-        lib.oracle_rho_all.argtypes = [f32p]
-        lib.oracle_rho_all.restype = None
-        lib.oracle_sincos_all.argtypes = [f32p, f32p]
-        lib.oracle_sincos_all.restype = None
         lib.oracle_threshold_table_f32.argtypes = [ctypes.c_float, ctypes.c_float, ctypes.c_int32, f32p]
         lib.oracle_threshold_table_f32.restype = None
         lib.oracle_metric_f32.argtypes = [ctypes.c_int, ctypes.c_float, ctypes.c_int, ctypes.c_float,
@@ -128,13 +130,32 @@ class Oracle:
         self.lib.oracle_philox4x32_10(c, k, o)
         return np.array(list(o), dtype=np.uint32)
 
-    def ln_f32(self, u: float) -> np.float32:
-        return np.float32(self.lib.oracle_ln_f32(ctypes.c_float(u)))
+    def gauss_f32(self, r: int) -> np.float32:
+        """FP32 standard normal deviate of one Philox output r (inverse normal CDF)."""
+        return np.float32(self.lib.oracle_gauss_f32(ctypes.c_uint32(int(r) & 0xFFFFFFFF)))
 
-    def sincos2pi_f32(self, a: int):
-        s, c = ctypes.c_float(), ctypes.c_float()
-        self.lib.oracle_sincos2pi_f32(ctypes.c_uint32(a), ctypes.byref(s), ctypes.byref(c))
-        return np.float32(s.value), np.float32(c.value)
+    def gauss_f64(self, r: int) -> float:
+        return float(self.lib.oracle_gauss_f64(ctypes.c_uint32(int(r) & 0xFFFFFFFF)))
+
+    def gauss_range_f32(self, start: int, count: int) -> np.ndarray:
+        """Deviates of r = start .. start + count - 1."""
+        out = np.empty(count, dtype=np.float32)
+        self.lib.oracle_gauss_range_f32(start, count, out.ctypes.data_as(ctypes.POINTER(ctypes.c_float)))
+        return out
+
+    def gauss_many_f32(self, r) -> np.ndarray:
+        """Deviates of the outputs in the array r."""
+        r = np.ascontiguousarray(r, dtype=np.uint32)
+        out = np.empty(r.shape[0], dtype=np.float32)
+        self.lib.oracle_gauss_many_f32(r.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)), r.shape[0],
+                                       out.ctypes.data_as(ctypes.POINTER(ctypes.c_float)))
+        return out
+
+    def icdf_table(self) -> np.ndarray:
+        """[32, 8, 4] FP32 cubic coefficients, segment (level j, sub-interval s)."""
+        out = np.empty((32, 8, 4), dtype=np.float32)
+        self.lib.oracle_icdf_table(out.ctypes.data_as(ctypes.POINTER(ctypes.c_float)))
+        return out
 
     def gauss4_f32(self, seed, frame, t, g) -> np.ndarray:
         z = (ctypes.c_float * 4)()
@@ -148,20 +169,6 @@ class Oracle:
 
     def noise_f32(self, seed, frame, t, k, eta, sigma) -> np.float32:
         return np.float32(self.lib.oracle_noise_f32(seed, frame, t, k, eta, sigma))
-
-    def rho_all(self) -> np.ndarray:
-        """rho(a) = sqrt(-2 ln u(a)) for every 23-bit a."""
-        out = np.empty(1 << 23, dtype=np.float32)
-        self.lib.oracle_rho_all(out.ctypes.data_as(ctypes.POINTER(ctypes.c_float)))
-        return out
-
-    def sincos_all(self):
-        """(sin, cos)(2 pi u(a)) for every 23-bit a."""
-        sn = np.empty(1 << 23, dtype=np.float32)
-        cs = np.empty(1 << 23, dtype=np.float32)
-        self.lib.oracle_sincos_all(sn.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
-                                   cs.ctypes.data_as(ctypes.POINTER(ctypes.c_float)))
-        return sn, cs
 
     # -- thresholds / metric / quantizer ---------------------------------------
     def threshold_table_f32(self, theta, lam, t_max) -> np.ndarray:

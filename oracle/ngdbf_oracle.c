@@ -38,13 +38,11 @@
  * The perturbation q_k is drawn by a counter-based generator (the paper's own
  * hardware used one Gaussian RNG and a shift-register chain, Sec. V-B):
  *   Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), key = (seed_lo,
- *   seed_hi), counter = (k/4, t, frame_lo, frame_hi);  r -> a = r >> 9,
- *   u = (a + 1/2) 2^-23;  Box-Muller (1958): outputs (r0,r1) give symbols
- *   4g, 4g+1 as rho cos(2 pi u1), rho sin(2 pi u1) with rho = sqrt(-2 ln u0);
- *   (r2,r3) give 4g+2, 4g+3 the same way.
- * The FP32 form evaluates ln and sin/cos with its own series (below) so that
- * the same definition can be evaluated bit-identically elsewhere; the FP64
- * form uses the C library's log/sin/cos on the same uniforms.
+ *   seed_hi), counter = (k/4, t, frame_lo, frame_hi); output k mod 4 gives
+ *   q_k's standard normal deviate by inversion of the normal CDF (below).
+ * The FP32 form replaces Phi^{-1} by piecewise cubics with a fixed table, so
+ * that the same definition can be evaluated bit-identically elsewhere; the
+ * FP64 form refines it to double accuracy with the C library's erfc.
  *
  * Reduced-precision forms of the inversion function (Sec. IV-E), on the same
  * FP32 perturbation q_k:
@@ -100,107 +98,121 @@ void oracle_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t
 }
 
 /* ------------------------------------------------------------------------ */
-/* FP32 elementary functions used by the Gaussian generator                  */
+/* Standard normal deviates by inversion of the normal CDF                   */
 /* ------------------------------------------------------------------------ */
 
-/* Series coefficients computed from their definitions (not fitted):
- *   ln:  ln m = 2 atanh(s), s = (m-1)/(m+1), atanh s = sum s^(2j+1)/(2j+1)
- *   sin/cos(h xi), h = pi/2:  a_n = (-1)^((n-1)/2) h^n / n!  (odd n),
- *                             b_n = (-1)^(n/2) h^n / n!      (even n)
- * with h^n/n! formed in double as t_n = (t_{n-1} * h) / n, t_0 = 1. */
-static float inv_odd[12];       /* inv_odd[n] = fl32(1/n) for odd n */
-static float sin_c[12], cos_c[13];
-static pthread_once_t coef_once = PTHREAD_ONCE_INIT;
+/* One Philox output r gives one deviate.  Bit 31 is the sign; the other 31
+ * bits give the lower-tail probability p = (2 (r mod 2^31) + 1) 2^-33, which
+ * lies in (0, 1/2) and is exact in double; the deviate is -Phi^{-1}(p) when bit
+ * 31 is set and Phi^{-1}(p) otherwise (the inversion method applied to the
+ * symmetric uniform u = p or 1 - p).
+ *
+ * FP32 form: with a = 2 (r mod 2^31) + 1 and j the number of leading zeros of
+ * the 32-bit a, p lies in the dyadic interval [2^-(j+2), 2^-(j+1)); the three
+ * bits after the leading one of a pick one of eight equal sub-intervals
+ * (segment (j, s), 32 x 8 segments), and the next 23 bits give the position
+ * v in [-1/2, 1/2) inside it, so p = (8 + s + 1/2 + v) 2^-(j+5) (bits of a
+ * beyond those are dropped).  On each segment Phi^{-1} is replaced by the
+ * cubic in v that interpolates it at the four Chebyshev nodes
+ * v_i = cos((2i+1) pi / 8) / 2, with FP32 coefficients (table below), and
+ * evaluated by Horner's rule with fused multiply-adds.
+ *
+ * FP64 form: two Newton steps on Phi(z) = p from the FP32 value, with Phi
+ * from the C library's erfc. */
 
-static void coef_init(void) {
-    for (int n = 1; n < 12; n += 2) inv_odd[n] = 1.0f / (float)n;
-    const double h = 1.5707963267948966;  /* pi/2 */
-    double t = 1.0;
-    for (int n = 1; n <= 12; ++n) {
-        t = (t * h) / (double)n;
-        if (n & 1) sin_c[n] = (float)((((n - 1) / 2) & 1) ? -t : t);
-        else cos_c[n] = (float)(((n / 2) & 1) ? -t : t);
+/* Phi(z) = erfc(-z / sqrt 2) / 2 */
+static double phi_cdf(double z) { return 0.5 * erfc(-z * 0.70710678118654752); }
+
+/* Phi^{-1}(p) for 0 < p < 1/2 in double: 100 bisection steps of Phi(z) = p on
+ * [-40, 0], which end on adjacent doubles. */
+static double inv_phi_bisect(double p) {
+    double lo = -40.0, hi = 0.0;
+    for (int it = 0; it < 100; ++it) {
+        double mid = 0.5 * (lo + hi);
+        if (phi_cdf(mid) < p) lo = mid; else hi = mid;
     }
+    return 0.5 * (lo + hi);
 }
 
-/* Natural log for a positive normal float.  u = m 2^e with m in (1/sqrt2, sqrt2]. */
-float oracle_ln_f32(float u) {
-    pthread_once(&coef_once, coef_init);
-    uint32_t bits;
-    memcpy(&bits, &u, 4);
-    int32_t e = (int32_t)((bits >> 23) & 0xFFu) - 127;
-    uint32_t mb = (bits & 0x007FFFFFu) | 0x3F800000u;
-    float m;
-    memcpy(&m, &mb, 4);
-    if (m > 1.41421354f) { m = m * 0.5f; e = e + 1; }
-    float s = (m - 1.0f) / (m + 1.0f);
-    float z = s * s;
-    float p = inv_odd[11];
-    p = fmaf(p, z, inv_odd[9]);
-    p = fmaf(p, z, inv_odd[7]);
-    p = fmaf(p, z, inv_odd[5]);
-    p = fmaf(p, z, inv_odd[3]);
-    float r = fmaf(s * z, p, s);            /* atanh(s) */
-    return fmaf((float)e, 0.693147182f, 2.0f * r);
+/* icdf_tab[j][s] = FP32 coefficients c0..c3 of segment (j, s).  The cubic
+ * through (v_i, g_i), g_i = Phi^{-1}(p(v_i)), in the Chebyshev basis
+ * T_n(2v): b0 = sum g_i / 4, b_n = sum g_i T_n(x_i) / 2 (x_i = 2 v_i), with
+ * T_1(x_i) = x_i, T_2(x_i) = +-sqrt(2)/2, T_3(x_i) = (C3, -C1, C1, -C3) for
+ * C1 = cos(pi/8), C3 = cos(3pi/8); then T_1(2v) = 2v, T_2(2v) = 8v^2 - 1,
+ * T_3(2v) = 32v^3 - 6v give c0 = b0 - b2, c1 = 2 b1 - 6 b3, c2 = 8 b2,
+ * c3 = 32 b3.  All in double, in this order, then rounded to FP32. */
+static float icdf_tab[32][8][4];
+static pthread_once_t icdf_once = PTHREAD_ONCE_INIT;
+
+static void icdf_init(void) {
+    const double C1 = 0.5 * sqrt(2.0 + sqrt(2.0)), C3 = 0.5 * sqrt(2.0 - sqrt(2.0));
+    const double R = 0.5 * sqrt(2.0);
+    const double node[4] = {0.5 * C1, 0.5 * C3, -0.5 * C3, -0.5 * C1};
+    for (int j = 0; j < 32; ++j)
+        for (int s = 0; s < 8; ++s) {
+            double g[4];
+            for (int i = 0; i < 4; ++i)
+                g[i] = inv_phi_bisect(ldexp(8.0 + s + 0.5 + node[i], -(j + 5)));
+            double d03 = g[0] - g[3], d12 = g[1] - g[2], s03 = g[0] + g[3], s12 = g[1] + g[2];
+            double b0 = (s03 + s12) * 0.25;
+            double b1 = (d03 * C1 + d12 * C3) * 0.5;
+            double b2 = ((s03 - s12) * R) * 0.5;
+            double b3 = (d03 * C3 - d12 * C1) * 0.5;
+            icdf_tab[j][s][0] = (float)(b0 - b2);
+            icdf_tab[j][s][1] = (float)(2.0 * b1 - 6.0 * b3);
+            icdf_tab[j][s][2] = (float)(8.0 * b2);
+            icdf_tab[j][s][3] = (float)(32.0 * b3);
+        }
 }
 
-/* sin and cos of 2 pi u for u = (a + 1/2) 2^-23, a a 23-bit integer.
- * 4u = quadrant + xi with xi in [-1/2, 1/2], exact in FP32. */
-void oracle_sincos2pi_f32(uint32_t a, float* sin_out, float* cos_out) {
-    pthread_once(&coef_once, coef_init);
-    uint32_t quadrant = (a >> 21) & 3u;
-    int32_t rem = (int32_t)(a & 0x1FFFFFu);
-    if (rem >= (1 << 20)) { rem -= (1 << 21); quadrant = (quadrant + 1u) & 3u; }
-    float xi = ((float)rem + 0.5f) * 0x1.0p-21f;
-    float zz = xi * xi;
-    float ps = sin_c[11];
-    ps = fmaf(ps, zz, sin_c[9]);
-    ps = fmaf(ps, zz, sin_c[7]);
-    ps = fmaf(ps, zz, sin_c[5]);
-    ps = fmaf(ps, zz, sin_c[3]);
-    ps = fmaf(ps, zz, sin_c[1]);
-    float S = xi * ps;                       /* sin(pi xi / 2) */
-    float pc = cos_c[12];
-    pc = fmaf(pc, zz, cos_c[10]);
-    pc = fmaf(pc, zz, cos_c[8]);
-    pc = fmaf(pc, zz, cos_c[6]);
-    pc = fmaf(pc, zz, cos_c[4]);
-    pc = fmaf(pc, zz, cos_c[2]);
-    float C = fmaf(zz, pc, 1.0f);            /* cos(pi xi / 2) */
-    switch (quadrant) {
-        case 0: *sin_out = S; *cos_out = C; break;
-        case 1: *sin_out = C; *cos_out = -S; break;
-        case 2: *sin_out = -S; *cos_out = -C; break;
-        default: *sin_out = -C; *cos_out = S; break;
-    }
+void oracle_icdf_table(float* out) {
+    pthread_once(&icdf_once, icdf_init);
+    memcpy(out, icdf_tab, sizeof icdf_tab);
 }
 
-static inline float uniform_f32(uint32_t r) { return ((float)(r >> 9) + 0.5f) * 0x1.0p-23f; }
+/* The FP32 deviate of one Philox output. */
+float oracle_gauss_f32(uint32_t r) {
+    pthread_once(&icdf_once, icdf_init);
+    uint32_t a = ((r & 0x7FFFFFFFu) << 1) | 1u;
+    int j = 0;
+    while (!(a & 0x80000000u)) { a <<= 1; ++j; }       /* a is now normalized */
+    int s = (int)((a >> 28) & 7u);
+    uint32_t vbits = 0x3F800000u | ((a >> 5) & 0x007FFFFFu);
+    float one_plus_f;
+    memcpy(&one_plus_f, &vbits, 4);
+    float v = one_plus_f - 1.5f;                          /* exact */
+    const float* c = icdf_tab[j][s];
+    float g = fmaf(fmaf(fmaf(c[3], v, c[2]), v, c[1]), v, c[0]);
+    return (r & 0x80000000u) ? -g : g;
+}
 
-/* Four standard normals for (seed, frame, t, symbol group g): symbols 4g..4g+3. */
+/* The FP64 deviate of one Philox output. */
+double oracle_gauss_f64(uint32_t r) {
+    double p = ((double)(r & 0x7FFFFFFFu) * 2.0 + 1.0) * 0x1.0p-33;
+    double z = (double)oracle_gauss_f32(r & 0x7FFFFFFFu);
+    for (int it = 0; it < 2; ++it)
+        z -= (phi_cdf(z) - p) / (exp(-0.5 * z * z) * 0.39894228040143268);
+    return (r & 0x80000000u) ? -z : z;
+}
+
+/* Deviates of the outputs r[0 .. n-1] (verification). */
+void oracle_gauss_many_f32(const uint32_t* r, uint32_t n, float* out) {
+    for (uint32_t i = 0; i < n; ++i) out[i] = oracle_gauss_f32(r[i]);
+}
+
+/* Deviates of consecutive outputs r = start .. start + count - 1 (verification). */
+void oracle_gauss_range_f32(uint32_t start, uint32_t count, float* out) {
+    for (uint32_t i = 0; i < count; ++i) out[i] = oracle_gauss_f32(start + i);
+}
+
+/* Four standard normals for (seed, frame, t, symbol group g): symbol 4g + i
+ * takes Philox output i of counter (g, t, frame_lo, frame_hi). */
 void oracle_gauss4_f32(uint64_t seed, uint64_t frame, uint32_t t, uint32_t g, float z[4]) {
     uint32_t ctr[4] = {g, t, (uint32_t)frame, (uint32_t)(frame >> 32)};
     uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
     uint32_t r[4];
     oracle_philox4x32_10(ctr, key, r);
-    for (int h = 0; h < 2; ++h) {
-        float rho = sqrtf(-2.0f * oracle_ln_f32(uniform_f32(r[2 * h])));
-        float sn, cs;
-        oracle_sincos2pi_f32(r[2 * h + 1] >> 9, &sn, &cs);
-        z[2 * h] = rho * cs;
-        z[2 * h + 1] = rho * sn;
-    }
-}
-
-/* The generator's two factors over their whole input range a = 0 .. 2^23 - 1:
- * rho(a) = sqrt(-2 ln u), (sin, cos)(2 pi u) with u = (a + 1/2) 2^-23. */
-void oracle_rho_all(float* rho) {
-    for (uint32_t a = 0; a < (1u << 23); ++a)
-        rho[a] = sqrtf(-2.0f * oracle_ln_f32(((float)a + 0.5f) * 0x1.0p-23f));
-}
-
-void oracle_sincos_all(float* sn, float* cs) {
-    for (uint32_t a = 0; a < (1u << 23); ++a) oracle_sincos2pi_f32(a, sn + a, cs + a);
+    for (int i = 0; i < 4; ++i) z[i] = oracle_gauss_f32(r[i]);
 }
 
 void oracle_gauss4_f64(uint64_t seed, uint64_t frame, uint32_t t, uint32_t g, double z[4]) {
@@ -208,13 +220,7 @@ void oracle_gauss4_f64(uint64_t seed, uint64_t frame, uint32_t t, uint32_t g, do
     uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
     uint32_t r[4];
     oracle_philox4x32_10(ctr, key, r);
-    for (int h = 0; h < 2; ++h) {
-        double u0 = ((double)(r[2 * h] >> 9) + 0.5) * 0x1.0p-23;
-        double u1 = ((double)(r[2 * h + 1] >> 9) + 0.5) * 0x1.0p-23;
-        double rho = sqrt(-2.0 * log(u0));
-        z[2 * h] = rho * cos(6.283185307179586 * u1);
-        z[2 * h + 1] = rho * sin(6.283185307179586 * u1);
-    }
+    for (int i = 0; i < 4; ++i) z[i] = oracle_gauss_f64(r[i]);
 }
 
 /* Standard deviation of q_k: eta * sigma (Sec. III-C, variance eta^2 N0/2 with

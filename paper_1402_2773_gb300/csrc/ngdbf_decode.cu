@@ -18,12 +18,14 @@
 
 namespace ngdbf {
 
-// The generator's two factors for every 23-bit input (verification entry point).
-__global__ void generator_factors_kernel(const __grid_constant__ GenConsts G, float* rho, float* sn, float* cs) {
-    const uint32_t a = blockIdx.x * blockDim.x + threadIdx.x;
-    if (a >= (1u << 23)) return;
-    rho[a] = __fsqrt_rn(__fmul_rn(-2.0f, ln_series(half_offset_fraction(a), G)));
-    sincos_2pi(a, G, sn[a], cs[a]);
+// Deviates of consecutive Philox outputs r = start + i (verification entry point).
+__global__ void gaussian_range_kernel(const __grid_constant__ GenConsts G, uint32_t start, uint32_t count,
+                                      float* z) {
+    __shared__ float4 tab[256];
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) tab[i] = G.icdf[i];
+    __syncthreads();
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x)
+        z[i] = gauss_icdf(start + i, tab);
 }
 
 template <bool ADAPT, bool SMOOTH, bool ST_SMEM, bool WIDE, int PREC>
@@ -98,7 +100,55 @@ ngdbf_status get_pool(int dev, cudaMemPool_t* out) {
     return NGDBF_OK;
 }
 
+namespace {
+
+// Phi(z) = erfc(-z / sqrt 2) / 2 in double (C library erfc).
+double phi_cdf(double z) { return 0.5 * std::erfc(-z * 0.70710678118654752); }
+
+// Phi^{-1}(p), 0 < p < 1/2: 100 bisection steps of Phi(z) = p on [-40, 0].
+double inv_phi(double p) {
+    double lo = -40.0, hi = 0.0;
+    for (int it = 0; it < 100; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (phi_cdf(mid) < p) lo = mid;
+        else hi = mid;
+    }
+    return 0.5 * (lo + hi);
+}
+
+// Coefficients of the inverse normal CDF segments: segment (j, s) covers
+// p = (8 + s + 1/2 + v) 2^-(j+5), v in [-1/2, 1/2]; its cubic interpolates Phi^{-1} at the
+// Chebyshev nodes v_i = cos((2i+1) pi/8)/2.  In the basis T_n(2v) the coefficients are
+// b0 = sum g_i / 4 and b_n = sum g_i T_n(x_i) / 2; expanding T_1(2v) = 2v,
+// T_2(2v) = 8v^2 - 1, T_3(2v) = 32v^3 - 6v gives the monomial ones.  Double arithmetic in
+// a fixed order, rounded to FP32 at the end.
+struct IcdfTable {
+    float4 c[256];
+    IcdfTable() {
+        const double C1 = 0.5 * std::sqrt(2.0 + std::sqrt(2.0));   // cos(pi/8)
+        const double C3 = 0.5 * std::sqrt(2.0 - std::sqrt(2.0));   // cos(3 pi/8)
+        const double R = 0.5 * std::sqrt(2.0);                      // T_2 at the nodes: +-R
+        const double v[4] = {0.5 * C1, 0.5 * C3, -0.5 * C3, -0.5 * C1};
+        for (int j = 0; j < 32; ++j)
+            for (int s = 0; s < 8; ++s) {
+                double g[4];
+                for (int i = 0; i < 4; ++i) g[i] = inv_phi(std::ldexp(8.0 + s + 0.5 + v[i], -(j + 5)));
+                const double d03 = g[0] - g[3], d12 = g[1] - g[2];
+                const double s03 = g[0] + g[3], s12 = g[1] + g[2];
+                const double b0 = (s03 + s12) * 0.25;
+                const double b1 = (d03 * C1 + d12 * C3) * 0.5;
+                const double b2 = ((s03 - s12) * R) * 0.5;
+                const double b3 = (d03 * C3 - d12 * C1) * 0.5;   // T_3 at the nodes: C3, -C1, C1, -C3
+                c[8 * j + s] = make_float4((float)(b0 - b2), (float)(2.0 * b1 - 6.0 * b3), (float)(8.0 * b2),
+                                           (float)(32.0 * b3));
+            }
+    }
+};
+
+}  // namespace
+
 void host_gen_consts(uint64_t seed, GenConsts& G) {
+    static const IcdfTable table;     // built once per process (thread-safe static)
     uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
     for (int r = 0; r < 10; ++r) {
         G.rk0[r] = k0;
@@ -106,20 +156,7 @@ void host_gen_consts(uint64_t seed, GenConsts& G) {
         k0 += 0x9E3779B9u;
         k1 += 0xBB67AE85u;
     }
-    for (int j = 1; j <= 5; ++j) G.atanh_c[j - 1] = 1.0f / (float)(2 * j + 1);
-    // (pi/2)^n / n! in double by t_n = (t_{n-1} * (pi/2)) / n, then rounded to FP32
-    const double half_pi = 1.5707963267948966;
-    double t = 1.0;
-    for (int nn = 1; nn <= 12; ++nn) {
-        t = (t * half_pi) / (double)nn;
-        if (nn & 1) {
-            const int j = (nn - 1) / 2;
-            G.sin_c[j] = (float)((j & 1) ? -t : t);
-        } else {
-            const int j = nn / 2;
-            G.cos_c[j - 1] = (float)((j & 1) ? -t : t);
-        }
-    }
+    std::memcpy(G.icdf, table.c, sizeof(G.icdf));
 }
 
 struct LaunchPlan {
@@ -936,20 +973,20 @@ extern "C" ngdbf_status ngdbf_batch_destroy(ngdbf_batch_t* B) {
     return NGDBF_OK;
 }
 
-extern "C" ngdbf_status ngdbf_generator_factors(float* rho, float* sin_2pi, float* cos_2pi, void* stream) {
-    if (!rho || !sin_2pi || !cos_2pi) return fail(NGDBF_ERR_INVALID_ARG, "NULL buffer");
-    for (const void* p : {(const void*)rho, (const void*)sin_2pi, (const void*)cos_2pi}) {
-        cudaPointerAttributes a;
-        cudaError_t e = cudaPointerGetAttributes(&a, p);
-        if (e != cudaSuccess || !(a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged)) {
-            cudaGetLastError();
-            return fail(NGDBF_ERR_INVALID_ARG, "buffers must be device memory");
-        }
+extern "C" ngdbf_status ngdbf_gaussian_range(uint32_t start, uint32_t count, float* z, void* stream) {
+    if (count == 0) return NGDBF_OK;
+    if (!z) return fail(NGDBF_ERR_INVALID_ARG, "NULL buffer");
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, z);
+    if (e != cudaSuccess || !(a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged)) {
+        cudaGetLastError();
+        return fail(NGDBF_ERR_INVALID_ARG, "z must be device memory");
     }
     GenConsts G;
     host_gen_consts(0, G);
-    generator_factors_kernel<<<(1u << 23) / 256, 256, 0, static_cast<cudaStream_t>(stream)>>>(G, rho, sin_2pi, cos_2pi);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_fail(e, "generator factors");
+    const uint32_t blocks = std::min<uint32_t>((count + 255) / 256, 152u * 64u);
+    gaussian_range_kernel<<<blocks, 256, 0, static_cast<cudaStream_t>(stream)>>>(G, start, count, z);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "gaussian range");
     return NGDBF_OK;
 }

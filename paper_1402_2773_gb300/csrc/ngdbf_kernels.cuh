@@ -34,6 +34,7 @@
 
 #include <cmath>
 #include <cstdint>
+#include <type_traits>
 
 #include "../../include/ngdbf.h"
 #include "ngdbf_device.cuh"
@@ -107,8 +108,8 @@ struct MultiArgs {
 };
 
 struct SmemLayout {
-    int32_t off_frame, off_start, off_ctl, off_best, off_xw, off_sw, off_cnt, off_thr, off_st, off_chk, off_sym,
-        total;
+    int32_t off_frame, off_start, off_ctl, off_best, off_icdf, off_xw, off_sw, off_cnt, off_thr, off_st, off_chk,
+        off_sym, total;
 };
 
 // Offsets in bytes of the shared-memory arrays.  ctl holds: [0..1] unsatisfied
@@ -131,6 +132,7 @@ __host__ __device__ inline SmemLayout smem_layout(int n, int m, int t_max, int d
     L.off_start = take(kSlots * 4, 16);
     L.off_ctl = take(8 * 4, 16);
     L.off_best = take(kSlots * 8, 16);     // single-bit variant: least (E key, k) per slot
+    L.off_icdf = take(256 * 16, 16);       // inverse normal CDF coefficients
     L.off_cnt = take(n * cnt_bytes, 16);
     L.off_xw = take((n + 1) * 4, 16);
     L.off_sw = take((m + 1) * 4, 16);
@@ -190,6 +192,7 @@ __device__ __forceinline__ void decode_job(const Job& A, const uint32_t* thr_src
     uint32_t* xw = reinterpret_cast<uint32_t*>(smem + L.off_xw);
     uint32_t* sw = reinterpret_cast<uint32_t*>(smem + L.off_sw);
     unsigned long long* best = reinterpret_cast<unsigned long long*>(smem + L.off_best);
+    float4* icdf = reinterpret_cast<float4*>(smem + L.off_icdf);
     uint32_t* thr = ADAPT ? reinterpret_cast<uint32_t*>(smem + L.off_thr) : nullptr;
     uint16_t* st = nullptr;
     if constexpr (kState) {
@@ -213,7 +216,8 @@ __device__ __forceinline__ void decode_job(const Job& A, const uint32_t* thr_src
         sym_deg = d;
     }
 
-    // ---- set-up: zero the state, sentinels, thresholds, first 32 frames ----
+    // ---- set-up: generator table, zero the state, sentinels, thresholds, first 32 frames ----
+    for (int i = tid; i < 256; i += blockDim.x) icdf[i] = G.icdf[i];
     for (int k = tid; k <= n; k += blockDim.x) xw[k] = 0u;
     for (int i = tid; i <= m; i += blockDim.x) sw[i] = 0u;
     if constexpr (ADAPT)
@@ -417,23 +421,25 @@ __device__ __forceinline__ void decode_job(const Job& A, const uint32_t* thr_src
             const int32_t fix_kmax = A.fix_kmax, fix_W = A.fix_W;
             const bool single = !ADAPT && A.single;
             unsigned long long my_best = ~0ull;      // single-bit variant: (E key << 32) | k
-            for (int g = warp; g < groups; g += nwarps) {
+            // one group of four symbols; only the last group of a code with n % 4 != 0 is partial
+            auto group = [&](const int g, auto partial_tag) {
+                constexpr bool kPartial = decltype(partial_tag)::value;
                 const int k0 = 4 * g;
                 // issue the sample and state loads before the generator's arithmetic
                 HeldT yv[4];
-                uint32_t sv[4];
+                [[maybe_unused]] uint32_t sv[4];
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
-                    const bool in = k0 + j < n;
+                    const bool in = !kPartial || k0 + j < n;
                     yv[j] = in ? ys[(k0 + j) * kSlots + lane] : HeldT(0);
                     if constexpr (kState) sv[j] = in ? (uint32_t)st[(k0 + j) * kSlots + lane] : 0u;
                 }
                 float z[4];
-                gauss4((uint32_t)g, (uint32_t)t, flo, fhi, G, z);
+                gauss4((uint32_t)g, (uint32_t)t, flo, fhi, G, icdf, z);
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
                     const int k = k0 + j;
-                    if (k >= n) break;
+                    if (kPartial && k >= n) break;
                     int unsat_cnt, deg;
                     if constexpr (!WIDE) {
                         const uint4 c = cnt[k];
@@ -506,15 +512,18 @@ __device__ __forceinline__ void decode_job(const Job& A, const uint32_t* thr_src
                         flip = act && lower;
                         const uint32_t nv = s0 + ((ADAPT && act && !flip) ? 1u : 0u) +
                                             ((window && xneg) ? (1u << kCShift) : 0u);
-                        if (nv != s0) st[k * kSlots + lane] = (uint16_t)nv;
+                        if (ADAPT || nv != s0) st[k * kSlots + lane] = (uint16_t)nv;
                     } else {
                         const bool lower = below(th0);
                         flip = act && lower;
                     }
                     const uint32_t fm = __ballot_sync(0xFFFFFFFFu, flip);
-                    if (lane == 0 && fm) xw[k] = xword ^ fm;
+                    if (lane == 0) xw[k] = xword ^ fm;
                 }
-            }
+            };
+            const int full = n >> 2;
+            for (int g = warp; g < full; g += nwarps) group(g, std::false_type{});
+            if (full < groups && warp == full % nwarps) group(full, std::true_type{});
             if constexpr (!ADAPT) {
                 if (single && act) atomicMin(best + lane, my_best);
             }

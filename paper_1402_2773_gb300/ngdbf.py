@@ -112,7 +112,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.ngdbf_server_wait.argtypes = [vp, ctypes.c_double]
     lib.ngdbf_server_get_stats.argtypes = [vp, ctypes.POINTER(ngdbf_server_stats)]
     lib.ngdbf_server_destroy.argtypes = [vp]
-    lib.ngdbf_generator_factors.argtypes = [vp, vp, vp, vp]
+    lib.ngdbf_gaussian_range.argtypes = [ctypes.c_uint32, ctypes.c_uint32, vp, vp]
     lib.ngdbf_last_launch.argtypes = [ctypes.POINTER(ngdbf_launch_info)]
     lib.ngdbf_last_error.argtypes = []
     lib.ngdbf_last_error.restype = ctypes.c_char_p
@@ -120,7 +120,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
                "ngdbf_decode_host", "ngdbf_decode_noalloc", "ngdbf_last_launch", "ngdbf_batch_create",
                "ngdbf_batch_launch", "ngdbf_batch_destroy", "ngdbf_server_create", "ngdbf_server_submit",
                "ngdbf_server_poll", "ngdbf_server_wait", "ngdbf_server_get_stats", "ngdbf_server_destroy",
-               "ngdbf_generator_factors"):
+               "ngdbf_gaussian_range"):
         getattr(lib, fn).restype = ctypes.c_int
     if path is None:
         _lib = lib
@@ -254,9 +254,9 @@ def ngdbf_server_destroy(server: int) -> None:
     _check(lib, lib.ngdbf_server_destroy(server))
 
 
-def ngdbf_generator_factors(rho_ptr: int, sin_ptr: int, cos_ptr: int, stream: int = 0) -> None:
+def ngdbf_gaussian_range(start: int, count: int, z_ptr: int, stream: int = 0) -> None:
     lib = load()
-    _check(lib, lib.ngdbf_generator_factors(rho_ptr, sin_ptr, cos_ptr, stream))
+    _check(lib, lib.ngdbf_gaussian_range(start & 0xFFFFFFFF, count, z_ptr, stream))
 
 
 def ngdbf_last_launch() -> dict:

@@ -56,48 +56,74 @@ def pin_philox_kat(O):
         assert list(got) == v[6:10], f"philox KAT mismatch: {got} vs {v[6:10]}"
 
 
-def pin_ln_f32(O):
-    """FP32 ln of the generator's uniforms within 2 ulp of the C library's double log."""
-    a = np.concatenate([np.arange(0, 4096), np.arange((1 << 23) - 4096, 1 << 23),
-                        np.linspace(0, (1 << 23) - 1, 6000).astype(np.int64),
-                        # around the sqrt(2) mantissa boundary of each binade
-                        np.array([int(math.sqrt(2) * 2 ** (23 - j)) - 1 + d for j in range(1, 20)
-                                  for d in range(3)])])
-    for ai in a:
-        u = np.float32((float(ai) + 0.5) * 2.0 ** -23)
-        got = float(O.ln_f32(float(u)))
-        ref = math.log(float(u))
-        ulp = float(np.spacing(np.float32(abs(ref))))
-        assert abs(got - ref) <= 2.0 * ulp, f"ln({u}) = {got}, libm {ref}"
+def _icdf_inputs():
+    """Philox outputs covering every segment densely: for each level j (leading zeros of
+    a = 2 (r mod 2^31) + 1) and sub-interval s, 1024 evenly spaced positions plus both ends,
+    and 2^18 uniformly random outputs; both signs."""
+    rng = np.random.default_rng(11)
+    rs = [rng.integers(0, 1 << 32, 1 << 18, dtype=np.uint64)]
+    for j in range(32):
+        lo, hi = (1 << (31 - j)), (1 << (32 - j))          # a in [lo, hi): j leading zeros
+        a = np.unique(np.concatenate([np.linspace(lo, hi - 1, 8 * 1024 + 1).astype(np.uint64),
+                                      lo + (hi - lo) // 8 * np.arange(8, dtype=np.uint64),
+                                      lo + (hi - lo) // 8 * np.arange(1, 9, dtype=np.uint64) - 1]))
+        a = a | np.uint64(1)
+        r = (a - np.uint64(1)) // np.uint64(2)
+        rs += [r, r | np.uint64(1 << 31)]
+    return np.unique(np.concatenate(rs)).astype(np.uint32)
 
 
-def pin_sincos_f32(O):
-    """FP32 sin/cos(2 pi u) within 2^-23 of the C library and exactly quarter-turn symmetric."""
-    rng = np.random.default_rng(5)
-    a = np.concatenate([np.arange(0, 64), rng.integers(0, 1 << 23, 4000),
-                        np.array([(q << 21) + d for q in range(4) for d in (-2, -1, 0, 1, (1 << 20) - 1,
-                                                                            1 << 20)]) % (1 << 23)])
-    for ai in a:
-        ai = int(ai)
-        s, c = O.sincos2pi_f32(ai)
-        u = (ai + 0.5) * 2.0 ** -23
-        assert abs(float(s) - math.sin(2 * math.pi * u)) <= 2.0 ** -23, f"sin(2pi {u})"
-        assert abs(float(c) - math.cos(2 * math.pi * u)) <= 2.0 ** -23, f"cos(2pi {u})"
-        # a quarter turn (a + 2^21) rotates (sin, cos) -> (cos, -sin) exactly
-        s2, c2 = O.sincos2pi_f32((ai + (1 << 21)) % (1 << 23))
-        assert s2 == c and c2 == -s, "quarter-turn symmetry"
+def _ndtri_of(r):
+    from scipy.special import ndtri
+    r = r.astype(np.uint64)
+    p = (2.0 * (r & np.uint64(0x7FFFFFFF)).astype(np.float64) + 1.0) * 2.0 ** -33
+    z = ndtri(p)
+    return np.where(r >> np.uint64(31) == 1, -z, z)
 
 
-def pin_gauss_f32_vs_library(O):
-    """FP32 Box-Muller pairs agree with the C library's double evaluation of the same uniforms."""
-    worst = 0.0
-    for f in range(8):
-        for t in (0, 1, 299):
-            for g in range(0, 600, 7):
-                z32 = O.gauss4_f32(12345, f, t, g).astype(np.float64)
-                z64 = O.gauss4_f64(12345, f, t, g)
-                worst = max(worst, float(np.max(np.abs(z32 - z64) / (1.0 + np.abs(z64)))))
-    assert worst < 4e-6, f"FP32 Gaussian deviates from the library evaluation by {worst}"
+def pin_icdf_vs_library(O):
+    """FP32 inverse-CDF deviate of every segment within 2.5 ulp of max(|z|, 1) of the library's
+    Phi^{-1} (scipy ndtri) at p = (2 (r mod 2^31) + 1) 2^-33, sign from bit 31."""
+    r = _icdf_inputs()
+    z = O.gauss_many_f32(r).astype(np.float64)
+    assert all(z[i] == O.gauss_f32(int(r[i])) for i in range(0, len(r), len(r) // 50))
+    ref = _ndtri_of(r)
+    ulp = np.spacing(np.maximum(np.abs(ref), 1.0).astype(np.float32)).astype(np.float64)
+    worst = float(np.max(np.abs(z - ref) / ulp))
+    assert worst <= 2.5, f"FP32 deviate off the library inverse CDF by {worst} ulp"
+    # the batch evaluator over consecutive outputs agrees, around segment and level edges
+    for start in (0, (1 << 30) - 64, (1 << 31) - 64, 0x80000000 - 64, 0xFFFFFFFF - 127, 12345678):
+        zz = O.gauss_range_f32(start, 128).astype(np.float64)
+        rr = (start + np.arange(128, dtype=np.uint64)).astype(np.uint32)
+        ref = _ndtri_of(rr)
+        ulp = np.spacing(np.maximum(np.abs(ref), 1.0).astype(np.float32)).astype(np.float64)
+        assert np.max(np.abs(zz - ref) / ulp) <= 2.5
+
+
+def pin_icdf_symmetry_and_range(O):
+    """z(r with bit 31 set) = -z(r) exactly; the extreme outputs give Phi^{-1}(2^-33) = -6.3379."""
+    for r in (0, 1, 77, 1 << 20, (1 << 30) + 5, (1 << 31) - 1):
+        assert O.gauss_f32(r | (1 << 31)) == -O.gauss_f32(r)
+        assert O.gauss_f64(r | (1 << 31)) == -O.gauss_f64(r)
+    assert abs(float(O.gauss_f32(0)) + 6.33795775455) < 1e-6
+    assert abs(O.gauss_f64(0) + 6.337957754553) < 1e-11
+
+
+def pin_gauss_f64_vs_library(O):
+    """The FP64 deviate equals the library's Phi^{-1} to 1e-13 (absolute, |z| <= 6.4)."""
+    r = _icdf_inputs()[::97]
+    z = np.array([O.gauss_f64(int(v)) for v in r])
+    assert np.max(np.abs(z - _ndtri_of(r))) < 1e-13
+
+
+def pin_gauss4_wiring(O):
+    """Symbol 4g + i takes Philox output i of counter (g, t, frame_lo, frame_hi), key (seed_lo, seed_hi)."""
+    for seed, f, t, g in ((12345, 0, 0, 0), (7, 3, 299, 511), ((5 << 32) | 9, (2 << 32) | 1, 17, 3)):
+        r = O.philox([g, t, f & 0xFFFFFFFF, f >> 32], [seed & 0xFFFFFFFF, seed >> 32])
+        z32 = O.gauss4_f32(seed, f, t, g)
+        z64 = O.gauss4_f64(seed, f, t, g)
+        for i in range(4):
+            assert z32[i] == O.gauss_f32(int(r[i])) and z64[i] == O.gauss_f64(int(r[i]))
 
 
 def pin_gauss_statistics(O):
@@ -627,33 +653,14 @@ def pin_precision_statistics(O):
         assert abs(res[prec][2].mean() - res[oracle_pkg.FP32][2].mean()) < 0.06
         assert (res[prec][1] == res[oracle_pkg.FP32][1]).mean() > 0.3
 
-
-def pin_generator_factors_whole_domain(O):
-    """Over all 2^23 inputs: rho within 1.5 ulp of fp64 sqrt(-2 ln u), sin/cos(2 pi u) within
-    2^-23 of fp64, exact quarter-turn symmetry, and the batch evaluators equal the single ones."""
-    rho = O.rho_all().astype(np.float64)
-    sn, cs = O.sincos_all()
-    a = np.arange(1 << 23)
-    u = (a + 0.5) * 2.0 ** -23
-    ulp = np.spacing(rho.astype(np.float32)).astype(np.float64)
-    assert np.max(np.abs(rho - np.sqrt(-2.0 * np.log(u))) / ulp) <= 1.5
-    assert np.max(np.abs(sn - np.sin(2 * np.pi * u))) <= 2.0 ** -23
-    assert np.max(np.abs(cs - np.cos(2 * np.pi * u))) <= 2.0 ** -23
-    q = (a + (1 << 21)) % (1 << 23)
-    assert (sn[q] == cs).all() and (cs[q] == -sn).all()
-    for ai in (0, 1, 77777, 1 << 21, (1 << 23) - 1):
-        u32 = float(np.float32((ai + 0.5) * 2.0 ** -23))
-        assert np.float32(np.sqrt(np.float32(-2.0) * O.ln_f32(u32))) == np.float32(rho[ai])
-        assert O.sincos2pi_f32(ai) == (sn[ai], cs[ai])
-
-
 ALL_PINS = [
-    pin_philox_kat, pin_ln_f32, pin_sincos_f32, pin_gauss_f32_vs_library, pin_gauss_statistics,
+    pin_philox_kat, pin_icdf_vs_library, pin_icdf_symmetry_and_range, pin_gauss_f64_vs_library,
+    pin_gauss4_wiring, pin_gauss_statistics,
     pin_noise_variance, pin_threshold_table, pin_table2, pin_fig20, pin_quantizer,
     pin_trace_gdbf, pin_trace_injected_noise, pin_trace_adaptation, pin_trace_smoothing,
     pin_trace_clamp_sign_tie, pin_trace_single_bit, pin_noiseless, pin_eta0_is_gdbf,
     pin_eta0_is_single_bit_gdbf, pin_codeword_and_ml,
     pin_f32_matches_injected_noise, pin_frame_independence, pin_f32_f64_statistics,
     pin_round_half, pin_metric_f16, pin_fix_quantizer, pin_trace_fixed_point, pin_table2_fixed_point, pin_fp16_reduces_to_fp32,
-    pin_fix_reduces_to_fp32, pin_precision_statistics, pin_generator_factors_whole_domain,
+    pin_fix_reduces_to_fp32, pin_precision_statistics,
 ]

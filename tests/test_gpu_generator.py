@@ -1,10 +1,13 @@
 """The decoder's perturbation generator against the reference decoder's, over every input.
 
-Each Box-Muller output is fl32(rho(a0) * cos or sin(a1)) with a0, a1 the 23-bit
-integers r >> 9 of two Philox outputs, so equality of rho and of (sin, cos) for all
-2^23 values of a, together with the Philox known-answer and parity tests, covers
-every perturbation either side can draw.
+Each perturbation is fl32(eta sigma) * z(r) with r one Philox output and z the
+inverse-CDF deviate of r, so equality of z(r) for all 2^32 values of r, together
+with the Philox known-answer and decode parity tests, covers every perturbation
+either side can draw.
 """
+from concurrent.futures import ThreadPoolExecutor
+import os
+
 import numpy as np
 import pytest
 
@@ -13,6 +16,8 @@ from paper_1402_2773_gb300 import ngdbf
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
+CHUNK = 1 << 27
+THREADS = max(1, min(16, os.cpu_count() or 1))
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -25,18 +30,24 @@ def _gpu():
     torch.cuda.set_device(0)
 
 
-def test_generator_factors_bit_exact_over_the_whole_domain():
+def test_deviates_bit_exact_over_every_philox_output():
     O = oracle.load()
-    rho = torch.empty(1 << 23, dtype=torch.float32, device="cuda")
-    sn = torch.empty_like(rho)
-    cs = torch.empty_like(rho)
-    ngdbf.ngdbf_generator_factors(rho.data_ptr(), sn.data_ptr(), cs.data_ptr(),
-                                  torch.cuda.current_stream().cuda_stream)
-    torch.cuda.synchronize()
-    want_rho = O.rho_all()
-    want_sn, want_cs = O.sincos_all()
-    for got, want, name in ((rho, want_rho, "rho"), (sn, want_sn, "sin"), (cs, want_cs, "cos")):
-        g = got.cpu().numpy().view(np.uint32)
-        w = want.view(np.uint32)
-        bad = np.nonzero(g != w)[0]
-        assert bad.size == 0, f"{name}: {bad.size} of 2^23 values differ, first a = {bad[:5]}"
+    buf = torch.empty(CHUNK, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    part = CHUNK // THREADS
+    with ThreadPoolExecutor(THREADS) as pool:
+        for c in range((1 << 32) // CHUNK):
+            start = c * CHUNK
+            ngdbf.ngdbf_gaussian_range(start, CHUNK, buf.data_ptr(), stream)
+            want = np.concatenate(list(pool.map(lambda i: O.gauss_range_f32(start + i * part, part),
+                                                range(THREADS))))
+            got = buf.cpu().numpy()
+            bad = np.nonzero(got.view(np.uint32) != want.view(np.uint32))[0]
+            assert bad.size == 0, f"{bad.size} deviates differ in chunk {c}, first r = {start + bad[:4]}"
+
+
+def test_zero_count_and_host_buffer():
+    ngdbf.ngdbf_gaussian_range(5, 0, 0)
+    host = np.zeros(4, np.float32)
+    with pytest.raises(RuntimeError):
+        ngdbf.ngdbf_gaussian_range(0, 4, host.ctypes.data)

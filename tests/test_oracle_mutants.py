@@ -20,15 +20,24 @@ MUTANTS = [
     ("philox key word", "^ c1 ^ k0;", "^ c1 ^ k1;"),
     ("philox multiplier", "mul0 = 0xD2511F53u", "mul0 = 0xD2511F57u"),
     ("philox rounds", "round < 10;", "round < 9;"),
-    ("ln series term", "p = fmaf(p, z, inv_odd[3]);", "p = fmaf(p, z, inv_odd[5]);"),
-    ("ln exponent", "fmaf((float)e, 0.693147182f, 2.0f * r)", "fmaf((float)e, 0.693147182f, r)"),
-    ("sincos quadrant", "case 1: *sin_out = C; *cos_out = -S;", "case 1: *sin_out = -C; *cos_out = S;"),
-    ("sin series sign", "sin_c[n] = (float)((((n - 1) / 2) & 1) ? -t : t);", "sin_c[n] = (float)t;"),
-    ("box-muller swap", "z[2 * h] = rho * cs;\n        z[2 * h + 1] = rho * sn;",
-     "z[2 * h] = rho * sn;\n        z[2 * h + 1] = rho * cs;"),
-    ("uniform offset", "((float)(r >> 9) + 0.5f) * 0x1.0p-23f", "((float)(r >> 9) + 1.0f) * 0x1.0p-23f"),
-    ("counter transposed", "uint32_t ctr[4] = {g, t, (uint32_t)frame, (uint32_t)(frame >> 32)};\n    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};\n    uint32_t r[4];\n    oracle_philox4x32_10(ctr, key, r);\n    for (int h = 0; h < 2; ++h) {\n        float rho",
-     "uint32_t ctr[4] = {t, g, (uint32_t)frame, (uint32_t)(frame >> 32)};\n    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};\n    uint32_t r[4];\n    oracle_philox4x32_10(ctr, key, r);\n    for (int h = 0; h < 2; ++h) {\n        float rho"),
+    ("icdf sign ignored", "return (r & 0x80000000u) ? -g : g;", "return g;"),
+    ("icdf level exponent", "ldexp(8.0 + s + 0.5 + node[i], -(j + 5))", "ldexp(8.0 + s + 0.5 + node[i], -(j + 4))"),
+    ("icdf sub-interval offset", "ldexp(8.0 + s + 0.5 + node[i]", "ldexp(8.0 + s + node[i]"),
+    ("icdf sub-interval bits", "int s = (int)((a >> 28) & 7u);", "int s = (int)((a >> 27) & 7u);"),
+    ("icdf centering", "float v = one_plus_f - 1.5f;", "float v = one_plus_f - 1.0f;"),
+    ("icdf fraction bits", "((a >> 5) & 0x007FFFFFu)", "((a >> 4) & 0x007FFFFFu)"),
+    ("chebyshev node", "const double node[4] = {0.5 * C1, 0.5 * C3, -0.5 * C3, -0.5 * C1};",
+     "const double node[4] = {0.5 * C3, 0.5 * C1, -0.5 * C1, -0.5 * C3};"),
+    ("chebyshev b3 sign", "double b3 = (d03 * C3 - d12 * C1) * 0.5;", "double b3 = (d03 * C3 + d12 * C1) * 0.5;"),
+    ("chebyshev c1", "(float)(2.0 * b1 - 6.0 * b3);", "(float)(2.0 * b1 + 6.0 * b3);"),
+    ("chebyshev c0", "(float)(b0 - b2);", "(float)(b0 + b2);"),
+    ("horner order", "fmaf(fmaf(fmaf(c[3], v, c[2]), v, c[1]), v, c[0])", "fmaf(fmaf(fmaf(c[3], v, c[1]), v, c[2]), v, c[0])"),
+    ("phi scale", "0.5 * erfc(-z * 0.70710678118654752)", "0.5 * erfc(-z * 1.4142135623730951)"),
+    ("no newton in f64", "for (int it = 0; it < 2; ++it)\n        z -=", "for (int it = 0; it < 0; ++it)\n        z -="),
+    ("gauss4 output order", "for (int i = 0; i < 4; ++i) z[i] = oracle_gauss_f32(r[i]);",
+     "for (int i = 0; i < 4; ++i) z[i] = oracle_gauss_f32(r[3 - i]);"),
+    ("counter transposed", "uint32_t ctr[4] = {g, t, (uint32_t)frame, (uint32_t)(frame >> 32)};\n    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};\n    uint32_t r[4];\n    oracle_philox4x32_10(ctr, key, r);\n    for (int i = 0; i < 4; ++i) z[i] = oracle_gauss_f32",
+     "uint32_t ctr[4] = {t, g, (uint32_t)frame, (uint32_t)(frame >> 32)};\n    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};\n    uint32_t r[4];\n    oracle_philox4x32_10(ctr, key, r);\n    for (int i = 0; i < 4; ++i) z[i] = oracle_gauss_f32"),
     ("noise scale", "return (float)((double)eta * (double)sigma);", "return (float)((double)eta * (double)sigma * (double)sigma);"),
     ("metric sign", "float e = xy + ws;", "float e = xy - ws;"),
     ("metric drops w", "float ws = w * (float)S;", "float ws = (float)S;"),
