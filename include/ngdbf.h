@@ -315,6 +315,7 @@ typedef struct ngdbf_launch_info {
     int32_t state_in_smem;   /* 1 if per-(symbol, slot) counters live in shared memory */
     int32_t kernels;         /* kernels launched by the call */
     int32_t sm_count;        /* SMs of the device */
+    int32_t tables_in_smem;  /* adjacency tables copied to shared memory: 1 N(i), 2 M(k), 3 both */
 } ngdbf_launch_info;
 
 ngdbf_status ngdbf_last_launch(ngdbf_launch_info* out);

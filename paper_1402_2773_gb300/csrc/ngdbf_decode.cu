@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -33,10 +34,10 @@ __global__ void __launch_bounds__(1024) ngdbf_persistent_kernel(const __grid_con
     using HeldT = typename Held<PREC>::T;
     const Job& J = A.J;
     const SmemLayout L = smem_layout(J.n, J.m, J.t_max, J.dv_max, J.dc_max, ADAPT,
-                                     ST_SMEM && (ADAPT || SMOOTH), A.tables_smem != 0);
+                                     ST_SMEM && (ADAPT || SMOOTH), A.placement);
     HeldT* ys = static_cast<HeldT*>(A.yslots) + (size_t)blockIdx.x * J.n * kSlots;
     uint16_t* st = A.st_global ? A.st_global + (size_t)blockIdx.x * J.n * kSlots : nullptr;
-    decode_job<ADAPT, SMOOTH, ST_SMEM, WIDE, PREC>(J, A.thr, A.G, L, A.tables_smem != 0, ys, st);
+    decode_job<ADAPT, SMOOTH, ST_SMEM, WIDE, PREC>(J, A.thr, A.G, L, A.placement, ys, st);
 }
 
 }  // namespace ngdbf
@@ -60,13 +61,15 @@ ngdbf_status fail(ngdbf_status s, const std::string& msg) {
     return s;
 }
 
-void set_last_launch(int grid, int block, int smem, int state_in_smem, int kernels, int sm_count) {
+void set_last_launch(int grid, int block, int smem, int state_in_smem, int tables_in_smem, int kernels,
+                     int sm_count) {
     g_last_launch.grid = grid;
     g_last_launch.block = block;
     g_last_launch.smem_bytes = smem;
     g_last_launch.state_in_smem = state_in_smem;
     g_last_launch.kernels = kernels;
     g_last_launch.sm_count = sm_count;
+    g_last_launch.tables_in_smem = tables_in_smem;
 }
 
 size_t align256(size_t v) { return (v + 255) / 256 * 256; }
@@ -161,7 +164,8 @@ void host_gen_consts(uint64_t seed, GenConsts& G) {
 
 struct LaunchPlan {
     int block, grid, blocks_per_sm, smem;
-    bool st_smem, tables_smem;
+    bool st_smem;
+    int placement;              // adjacency tables in shared memory: kTabChk | kTabSym
 };
 
 using KernelFn = void (*)(DecodeArgs);
@@ -193,6 +197,68 @@ KernelFn pick_kernel(int variant, int precision, bool st_smem, bool wide) {
 // Bytes of one held sample.
 size_t held_bytes(int precision) { return precision == NGDBF_FP16 ? 2 : (precision == NGDBF_FIX ? 1 : 4); }
 
+// Shared-memory placement of a launch: the per-slot state and the adjacency tables.  The
+// state stays in shared memory whenever some candidate fits with it there (it is read and
+// written for every symbol and slot); among those candidates the most resident warps per
+// SM win, then the most CTAs per SM, then more tables in shared memory (both, then the
+// N(i) table only).  fn_of(st) gives the kernel for a state placement.  Results are cached
+// per shape and device.
+struct PlacementChoice {
+    bool st_smem = false;
+    int placement = 0, block = 0, bps = 0;
+    SmemLayout L{};
+};
+
+template <class FnOf>
+ngdbf_status choose_placement(int dev, int n, int m, int t_max, int dv_max, int dc_max, bool adapt, bool state,
+                              int limit, FnOf fn_of, PlacementChoice* out) {
+    using Key = std::vector<int64_t>;
+    static std::mutex mu;
+    static std::map<Key, PlacementChoice> cache;
+    const Key key = {dev, n, m, t_max, dv_max, dc_max, adapt, state, limit,
+                     (int64_t)(intptr_t)fn_of(true), (int64_t)(intptr_t)fn_of(false)};
+    {
+        std::lock_guard<std::mutex> g(mu);
+        auto it = cache.find(key);
+        if (it != cache.end()) {
+            *out = it->second;
+            return NGDBF_OK;
+        }
+    }
+    PlacementChoice best;
+    int best_warps = 0;
+    for (const bool st : {true, false}) {
+        if (st && !state) continue;
+        const void* fn = fn_of(st);
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, limit);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+        if (best.bps > 0) break;                       // state fits in shared memory
+        for (const int tb : {kTabChk | kTabSym, kTabChk, 0}) {
+            const SmemLayout L = smem_layout(n, m, t_max, dv_max, dc_max, adapt, st, tb);
+            if (L.total > limit) continue;
+            for (const int block : {1024, 512, 256}) {
+                int bps = 0;
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, block, L.total);
+                if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+                const int warps = bps * block / 32;
+                if (bps > 0 && (warps > best_warps || (warps == best_warps && bps > best.bps))) {
+                    best_warps = warps;
+                    best.st_smem = st;
+                    best.placement = tb;
+                    best.block = block;
+                    best.bps = bps;
+                    best.L = L;
+                }
+            }
+        }
+    }
+    if (best.bps == 0) return fail(NGDBF_ERR_UNSUPPORTED, "code too large for the shared-memory decision words");
+    std::lock_guard<std::mutex> g(mu);
+    cache[key] = best;
+    *out = best;
+    return NGDBF_OK;
+}
+
 ngdbf_status plan_launch(const ngdbf_code* C, const ngdbf_params* P, int64_t n_frames, int dev,
                          LaunchPlan* plan, KernelFn* fn_out, int* sm_count_out) {
     int sm_count = 0, smem_optin = 0, smem_per_sm = 0;
@@ -202,49 +268,24 @@ ngdbf_status plan_launch(const ngdbf_code* C, const ngdbf_params* P, int64_t n_f
     if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
     const bool state = (P->variant & 3) != 0;
     const bool adapt = (P->variant & NGDBF_ADAPT) != 0;
-    // Prefer everything in shared memory; drop the adjacency tables, then the
-    // per-slot state, to global memory when the CTA would not fit.
-    bool st_smem = state, tables_smem = true;
-    SmemLayout L = smem_layout(C->n, C->m, P->t_max, C->dv_max, C->dc_max, adapt, st_smem, tables_smem);
-    if (L.total > smem_optin) {
-        tables_smem = false;
-        L = smem_layout(C->n, C->m, P->t_max, C->dv_max, C->dc_max, adapt, st_smem, tables_smem);
-    }
-    if (L.total > smem_optin && st_smem) {
-        st_smem = false;
-        tables_smem = true;
-        L = smem_layout(C->n, C->m, P->t_max, C->dv_max, C->dc_max, adapt, st_smem, tables_smem);
-        if (L.total > smem_optin) {
-            tables_smem = false;
-            L = smem_layout(C->n, C->m, P->t_max, C->dv_max, C->dc_max, adapt, st_smem, tables_smem);
-        }
-    }
-    if (L.total > smem_optin)
-        return fail(NGDBF_ERR_UNSUPPORTED, "code too large for the shared-memory decision words");
-    KernelFn fn = pick_kernel(P->variant, P->precision, st_smem, C->dv_max > 7);
-    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, L.total);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
-    // Most resident warps per SM; ties go to more CTAs (more slots in flight).
-    int best_block = 0, best_bps = 0, best_warps = -1;
-    for (int block : {1024, 512, 256}) {
-        int bps = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, block, L.total);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
-        const int warps = bps * block / 32;
-        if (bps > 0 && (warps > best_warps || (warps == best_warps && bps > best_bps))) {
-            best_block = block;
-            best_bps = bps;
-            best_warps = warps;
-        }
-    }
-    if (best_bps == 0) return fail(NGDBF_ERR_UNSUPPORTED, "decode kernel does not fit on an SM");
+    const bool wide = C->dv_max > 7;
+    PlacementChoice pc;
+    ngdbf_status s = choose_placement(dev, C->n, C->m, P->t_max, C->dv_max, C->dc_max, adapt, state, smem_optin,
+                                      [&](bool st) { return (const void*)pick_kernel(P->variant, P->precision, st, wide); },
+                                      &pc);
+    if (s != NGDBF_OK) return s;
+    KernelFn fn = pick_kernel(P->variant, P->precision, pc.st_smem, wide);
+    const int best_block = pc.block, best_bps = pc.bps;
+    const SmemLayout& L = pc.L;
+    const bool st_smem = pc.st_smem;
+    const int placement = pc.placement;
     const int64_t groups = (n_frames + kSlots - 1) / kSlots;
     plan->block = best_block;
     plan->blocks_per_sm = best_bps;
     plan->grid = (int)std::min<int64_t>((int64_t)sm_count * best_bps, groups);
     plan->smem = L.total;
     plan->st_smem = st_smem;
-    plan->tables_smem = tables_smem;
+    plan->placement = placement;
     *fn_out = fn;
     *sm_count_out = sm_count;
     (void)smem_per_sm;
@@ -301,7 +342,7 @@ void fill_args(const ngdbf_code* C, const ngdbf_params* P, const LaunchPlan& pla
     fill_job(C, P, y, n_frames, sigma, frame_offset, bits, iters, pass,
              reinterpret_cast<unsigned long long*>(base), &A.J, A.thr);
     A.J.thr = nullptr;                 // thresholds travel inline in the launch
-    A.tables_smem = plan.tables_smem ? 1 : 0;
+    A.placement = plan.placement;
     A.yslots = base + 256;
     A.st_global = st_global ? reinterpret_cast<uint16_t*>(st_base) : nullptr;
     host_gen_consts(seed, A.G);
@@ -390,12 +431,7 @@ ngdbf_status decode_impl(const ngdbf_code* C, const float* y, int64_t n_frames, 
     cudaError_t ef = cudaFreeAsync(ws, stream);
     if (e != cudaSuccess) return cuda_fail(e, "decode launch");
     if (ef != cudaSuccess) return cuda_fail(ef, "cudaFreeAsync");
-    g_last_launch.grid = plan.grid;
-    g_last_launch.block = plan.block;
-    g_last_launch.smem_bytes = plan.smem;
-    g_last_launch.state_in_smem = plan.st_smem ? 1 : 0;
-    g_last_launch.kernels = 1;
-    g_last_launch.sm_count = sm_count;
+    set_last_launch(plan.grid, plan.block, plan.smem, plan.st_smem ? 1 : 0, plan.placement, 1, sm_count);
     return NGDBF_OK;
 }
 
@@ -658,12 +694,7 @@ extern "C" ngdbf_status ngdbf_decode_noalloc(const ngdbf_code_t* C, const float*
     fn<<<grid, plan.block, plan.smem, stream>>>(A);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "decode launch");
-    g_last_launch.grid = grid;
-    g_last_launch.block = plan.block;
-    g_last_launch.smem_bytes = plan.smem;
-    g_last_launch.state_in_smem = plan.st_smem ? 1 : 0;
-    g_last_launch.kernels = 1;
-    g_last_launch.sm_count = sm_count;
+    set_last_launch(grid, plan.block, plan.smem, plan.st_smem ? 1 : 0, plan.placement, 1, sm_count);
     return NGDBF_OK;
 }
 
@@ -676,7 +707,7 @@ extern "C" ngdbf_status ngdbf_decode_noalloc(const ngdbf_code_t* C, const float*
 struct ngdbf_batch {
     int device = 0, n_jobs = 0, sm_count = 0;
     void* fn = nullptr;                 // job-table kernel
-    int grid = 0, block = 0, smem = 0, state_in_smem = 0;
+    int grid = 0, block = 0, smem = 0, state_in_smem = 0, tables_in_smem = 0;
     MultiArgs args;
     unsigned char* d_mem = nullptr;     // jobs | thresholds | queues | first_job | samples | state
     unsigned long long* d_queues = nullptr;
@@ -768,31 +799,24 @@ ngdbf_status plan_table(const ngdbf_job* jobs, int32_t n_jobs, int dev, TablePla
     // shared memory for the largest code and T; state, then tables, move out when needed
     const bool state = (variant & 3) != 0, adapt = (variant & NGDBF_ADAPT) != 0;
     T.wide = T.dv_max > 7;
-    bool st_smem = state, tables_smem = true;
-    auto layout = [&]() { return smem_layout(T.n_max, T.m_max, T.t_max, T.dv_max, T.dc_max, adapt, st_smem, tables_smem); };
-    void* fn = multi_kernel_fn(variant, precision, st_smem, T.wide);
     cudaFuncAttributes fa;
-    e = cudaFuncGetAttributes(&fa, fn);
+    e = cudaFuncGetAttributes(&fa, multi_kernel_fn(variant, precision, state, T.wide));
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncGetAttributes");
     const int limit = smem_optin - (int)fa.sharedSizeBytes;
-    SmemLayout L = layout();
-    if (L.total > limit) { tables_smem = false; L = layout(); }
-    if (L.total > limit && st_smem) {
-        st_smem = false; tables_smem = true; L = layout();
-        if (L.total > limit) { tables_smem = false; L = layout(); }
-    }
-    if (L.total > limit) return fail(NGDBF_ERR_UNSUPPORTED, "largest code too large for shared memory");
-    fn = multi_kernel_fn(variant, precision, st_smem, T.wide);
-    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, L.total);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+    PlacementChoice pc;
+    ngdbf_status s = choose_placement(dev, T.n_max, T.m_max, T.t_max, T.dv_max, T.dc_max, adapt, state, limit,
+                                      [&](bool st) { return (const void*)multi_kernel_fn(variant, precision, st, T.wide); },
+                                      &pc);
+    if (s != NGDBF_OK) return s;
+    void* fn = multi_kernel_fn(variant, precision, pc.st_smem, T.wide);
     T.fn = fn;
-    T.smem = L.total;
-    T.st_smem = st_smem;
-    T.tables_smem = tables_smem;
-    T.state_global = state && !st_smem;
+    T.smem = pc.L.total;
+    T.st_smem = pc.st_smem;
+    T.placement = pc.placement;
+    T.state_global = state && !pc.st_smem;
     for (int block : {1024, 512, 256}) {
         int bps = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, (const void*)fn, block, L.total);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, (const void*)fn, block, pc.L.total);
         if (e != cudaSuccess) return cuda_fail(e, "occupancy");
         if (bps > 0) T.shapes.push_back({block, bps});
     }
@@ -866,6 +890,7 @@ extern "C" ngdbf_status ngdbf_batch_create(const ngdbf_job* jobs, int32_t n_jobs
     B->fn = T.fn;
     B->smem = T.smem;
     B->state_in_smem = T.st_smem ? 1 : 0;
+    B->tables_in_smem = T.placement;
     std::vector<std::pair<int, int>> shapes = T.shapes;
     int max_bps = 0;
     for (const auto& sh : shapes) max_bps = std::max(max_bps, sh.second);
@@ -908,7 +933,7 @@ extern "C" ngdbf_status ngdbf_batch_create(const ngdbf_job* jobs, int32_t n_jobs
     A.n_jobs = n_jobs;
     A.first_job = B->d_first;
     A.n_max = T.n_max; A.m_max = T.m_max; A.t_max = T.t_max; A.dv_max = T.dv_max; A.dc_max = T.dc_max;
-    A.tables_smem = T.tables_smem ? 1 : 0;
+    A.placement = T.placement;
     A.yslots = B->d_mem + off_y;
     A.st_global = per_slot_st ? reinterpret_cast<uint16_t*>(B->d_mem + off_st) : nullptr;
     host_gen_consts(seed, A.G);
@@ -964,7 +989,7 @@ extern "C" ngdbf_status ngdbf_batch_launch(ngdbf_batch_t* B, void* stream_ptr) {
     if (dev != B->device) return fail(NGDBF_ERR_INVALID_ARG, "batch belongs to another device");
     e = B->exec ? cudaGraphLaunch(B->exec, stream) : batch_enqueue(B, stream);
     if (e != cudaSuccess) return cuda_fail(e, "job table launch");
-    set_last_launch(B->grid, B->block, B->smem, B->state_in_smem, 1, B->sm_count);
+    set_last_launch(B->grid, B->block, B->smem, B->state_in_smem, B->tables_in_smem, 1, B->sm_count);
     return NGDBF_OK;
 }
 

@@ -46,8 +46,8 @@ __device__ __forceinline__ void philox4x32_10(uint32_t c0, uint32_t c1, uint32_t
 // p = a 2^-33 in (0, 1/2).  With j = clz(a) and m = a << j, p lies in the j-th dyadic
 // interval below 1/2, bits 30..28 of m pick one of its eight equal sub-intervals and
 // bits 27..5 the position v in [-1/2, 1/2) inside it (exact in FP32), so that
-// p = (8 + s + 1/2 + v) 2^-(j+5).  Phi^{-1}(p) is the segment's cubic in v (tab, in
-// shared memory), evaluated by Horner's rule with fused multiply-adds.
+// p = (8 + s + 1/2 + v) 2^-(j+5).  Phi^{-1}(p) is the segment's cubic in v (entry 8 j + s
+// of tab, in shared memory), evaluated by Horner's rule with fused multiply-adds.
 __device__ __forceinline__ float gauss_icdf(uint32_t r, const float4* tab) {
     const uint32_t a = (r << 1) | 1u;
     const uint32_t j = (uint32_t)__clz((int)a);

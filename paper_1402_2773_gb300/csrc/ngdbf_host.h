@@ -29,7 +29,8 @@ namespace host {
 ngdbf_status fail(ngdbf_status s, const std::string& msg);
 ngdbf_status cuda_fail(cudaError_t e, const char* what);
 // Launch shape reported by ngdbf_last_launch on the calling thread.
-void set_last_launch(int grid, int block, int smem, int state_in_smem, int kernels, int sm_count);
+void set_last_launch(int grid, int block, int smem, int state_in_smem, int tables_in_smem, int kernels,
+                     int sm_count);
 size_t align256(size_t v);
 // The library's stream-ordered pool of a device (kept warm across calls).
 ngdbf_status get_pool(int dev, cudaMemPool_t* out);
@@ -48,7 +49,8 @@ void fill_job(const ngdbf_code* C, const ngdbf_params* P, const float* y, int64_
 struct TablePlan {
     int n_max = 0, m_max = 0, t_max = 0, dv_max = 0, dc_max = 0;
     int variant = 0, precision = 0, sm_count = 0, smem = 0;
-    bool st_smem = false, tables_smem = false, wide = false, state_global = false;
+    bool st_smem = false, wide = false, state_global = false;
+    int placement = 0;          // adjacency tables in shared memory: kTabChk | kTabSym
     size_t thr_words = 0;
     void* fn = nullptr;
     std::vector<std::pair<int, int>> shapes;

@@ -42,6 +42,9 @@
 namespace ngdbf {
 
 constexpr int kSlots = 32;
+constexpr int kTabChk = 1;              // N(i) table in shared memory
+constexpr int kTabSym = 2;              // M(k) table and degrees in shared memory
+
 constexpr int kMaxT = NGDBF_MAX_T;
 constexpr uint32_t kUMask = 0x1FFu;   // u_k: bits 0-8
 constexpr int kCShift = 9;            // smoothing count: bits 9-15
@@ -86,7 +89,7 @@ struct Job {
 // Launch of one job: the job and its thresholds travel as kernel parameters.
 struct DecodeArgs {
     Job J;
-    int32_t tables_smem;        // copy the adjacency tables into shared memory
+    int32_t placement;          // adjacency tables copied into shared memory: kTabChk | kTabSym
     void* yslots;               // [grid][n][32] held samples (4, 2 or 1 bytes each)
     uint16_t* st_global;        // [grid][n][32] when the state is not in shared memory
     GenConsts G;
@@ -101,7 +104,7 @@ struct MultiArgs {
     int32_t n_jobs;
     const int32_t* first_job;   // [grid]
     int32_t n_max, m_max, t_max, dv_max, dc_max;   // layout maxima over the jobs
-    int32_t tables_smem;
+    int32_t placement;
     void* yslots;               // [grid][n_max][32]
     uint16_t* st_global;        // [grid][n_max][32] when the state is not in shared memory
     GenConsts G;
@@ -114,11 +117,13 @@ struct SmemLayout {
 
 // Offsets in bytes of the shared-memory arrays.  ctl holds: [0..1] unsatisfied
 // masks (double-buffered by pass parity), [2] live mask, [3] new-slot mask.
-// cnt holds per symbol the bit-sliced count of unsatisfied checks (one word per
-// count bit, bit f for slot f) and d_v(k): 3 slices + degree in 16 bytes when
-// d_v <= 7 (narrow), 7 slices + degree in 32 bytes otherwise (wide).
+// When d_v <= 7 (narrow), sw holds per check four words with one 4-bit lane per slot
+// (lane f & 7 of word f >> 3: 1 when check i is unsatisfied for slot f), and cnt holds
+// per symbol, in the same lanes, S_k + 8 = d_v(k) + 8 - 2 (unsatisfied checks in M(k))
+// (16 bytes).  Otherwise (wide) sw holds the 32-bit unsatisfied mask of each check and
+// cnt the bit-sliced count (seven words, bit f for slot f) and d_v(k) (32 bytes).
 __host__ __device__ inline SmemLayout smem_layout(int n, int m, int t_max, int dv_max, int dc_max,
-                                                  bool need_thr, bool st_smem, bool tables_smem) {
+                                                  bool need_thr, bool st_smem, int tables) {
     SmemLayout L;
     int o = 0;
     auto take = [&](int bytes, int align) {
@@ -135,11 +140,11 @@ __host__ __device__ inline SmemLayout smem_layout(int n, int m, int t_max, int d
     L.off_icdf = take(256 * 16, 16);       // inverse normal CDF coefficients
     L.off_cnt = take(n * cnt_bytes, 16);
     L.off_xw = take((n + 1) * 4, 16);
-    L.off_sw = take((m + 1) * 4, 16);
+    L.off_sw = take((m + 1) * (dv_max <= 7 ? 16 : 4), 16);
     L.off_thr = need_thr ? take((t_max + 1) * 4, 16) : -1;
     L.off_st = st_smem ? take(n * kSlots * 2, 16) : -1;
-    L.off_chk = tables_smem ? take(dc_max * m * 2, 16) : -1;
-    L.off_sym = tables_smem ? take(n * dv_max * 2 + n, 16) : -1;
+    L.off_chk = (tables & kTabChk) ? take(dc_max * m * 2, 16) : -1;
+    L.off_sym = (tables & kTabSym) ? take(n * dv_max * 2 + n, 16) : -1;
     L.total = (o + 15) / 16 * 16;
     return L;
 }
@@ -167,6 +172,13 @@ __device__ __forceinline__ uint32_t order_key(float v) {
 // Rounds an FP32 value to binary16 (nearest even) and back.
 __device__ __forceinline__ float to_half(float v) { return __half2float(__float2half_rn(v)); }
 
+// Bits 0..7 of b moved to bits 0, 4, ..., 28 (one bit per 4-bit lane).
+__device__ __forceinline__ uint32_t spread_nibbles(uint32_t b) {
+    b = (b | (b << 12)) & 0x000F000Fu;
+    b = (b | (b << 6)) & 0x03030303u;
+    return (b | (b << 3)) & 0x11111111u;
+}
+
 // Position of the (j+1)-th set bit of mask (j < popc(mask)).
 __device__ __forceinline__ int nth_set_bit(uint32_t mask, int j) {
     for (int i = 0; i < j; ++i) mask &= mask - 1u;
@@ -179,7 +191,7 @@ __device__ __forceinline__ int nth_set_bit(uint32_t mask, int j) {
 // layout of the launch, `ys`/`st_cta` this CTA's slot scratch.
 template <bool ADAPT, bool SMOOTH, bool ST_SMEM, bool WIDE, int PREC>
 __device__ __forceinline__ void decode_job(const Job& A, const uint32_t* thr_src, const GenConsts& G,
-                                           const SmemLayout& L, bool tables_smem,
+                                           const SmemLayout& L, int tables,
                                            typename Held<PREC>::T* ys, uint16_t* st_cta) {
     constexpr bool kState = ADAPT || SMOOTH;
     using HeldT = typename Held<PREC>::T;
@@ -204,14 +216,16 @@ __device__ __forceinline__ void decode_job(const Job& A, const uint32_t* thr_src
     const uint16_t* chk_cols = A.chk_cols;
     const uint16_t* sym_chks = A.sym_chks;
     const uint8_t* sym_deg = A.sym_deg;
-    if (tables_smem) {
+    if (tables & kTabChk) {
         uint16_t* c = reinterpret_cast<uint16_t*>(smem + L.off_chk);
+        for (int i = tid; i < dc_max * m; i += blockDim.x) c[i] = A.chk_cols[i];
+        chk_cols = c;
+    }
+    if (tables & kTabSym) {
         uint16_t* s = reinterpret_cast<uint16_t*>(smem + L.off_sym);
         uint8_t* d = reinterpret_cast<uint8_t*>(s + n * dv_max);
-        for (int i = tid; i < dc_max * m; i += blockDim.x) c[i] = A.chk_cols[i];
         for (int i = tid; i < n * dv_max; i += blockDim.x) s[i] = A.sym_chks[i];
         for (int i = tid; i < n; i += blockDim.x) d[i] = A.sym_deg[i];
-        chk_cols = c;
         sym_chks = s;
         sym_deg = d;
     }
@@ -219,7 +233,7 @@ __device__ __forceinline__ void decode_job(const Job& A, const uint32_t* thr_src
     // ---- set-up: generator table, zero the state, sentinels, thresholds, first 32 frames ----
     for (int i = tid; i < 256; i += blockDim.x) icdf[i] = G.icdf[i];
     for (int k = tid; k <= n; k += blockDim.x) xw[k] = 0u;
-    for (int i = tid; i <= m; i += blockDim.x) sw[i] = 0u;
+    for (int i = tid; i < (m + 1) * (WIDE ? 1 : 4); i += blockDim.x) sw[i] = 0u;
     if constexpr (ADAPT)
         for (int u = tid; u <= T; u += blockDim.x) thr[u] = thr_src[u];
     if constexpr (kState)
@@ -297,7 +311,12 @@ __device__ __forceinline__ void decode_job(const Job& A, const uint32_t* thr_src
                     for (int j = sub; j < dc_max; j += 4) s ^= xw[chk_cols[j * m + i]];
                 s ^= __shfl_xor_sync(0xFFFFFFFFu, s, 1);
                 s ^= __shfl_xor_sync(0xFFFFFFFFu, s, 2);
-                if (i < m && sub == 0) sw[i] = s;
+                if constexpr (WIDE) {
+                    if (i < m && sub == 0) sw[i] = s;
+                } else {
+                    // byte `sub` of the word, one slot per 4-bit lane (slots 8 sub .. 8 sub + 7)
+                    if (i < m) sw[4 * i + sub] = spread_nibbles((s >> (8 * sub)) & 0xFFu);
+                }
                 acc |= s;
             }
             acc = __reduce_or_sync(0xFFFFFFFFu, acc);
@@ -376,20 +395,20 @@ __device__ __forceinline__ void decode_job(const Job& A, const uint32_t* thr_src
         }
         if (live == 0) break;
 
-        // ---- A'. per symbol, the bit-sliced count of unsatisfied checks in M(k) ----
+        // ---- A'. per symbol and slot, the count of unsatisfied checks in M(k) ----
         for (int k = tid; k < n; k += blockDim.x) {
             const uint16_t* row = sym_chks + k * dv_max;
             if constexpr (!WIDE) {
-                uint32_t b0 = 0, b1 = 0, b2 = 0;           // count <= 7: three slices
+                // d_v <= 7: one 4-bit lane per slot, counts added lane-wise without carries;
+                // stored as S_k + 8 = d_v + 8 - 2 count in [1, 15]
+                const uint4* sw4 = reinterpret_cast<const uint4*>(sw);
+                uint4 c = make_uint4(0u, 0u, 0u, 0u);
                 for (int e = 0; e < dv_max; ++e) {
-                    const uint32_t s = sw[row[e]];
-                    const uint32_t c0 = b0 & s;
-                    b0 ^= s;
-                    const uint32_t c1 = b1 & c0;
-                    b1 ^= c0;
-                    b2 ^= c1;
+                    const uint4 s = sw4[row[e]];
+                    c.x += s.x; c.y += s.y; c.z += s.z; c.w += s.w;
                 }
-                cnt[k] = make_uint4(b0, b1, b2, (uint32_t)sym_deg[k]);
+                const uint32_t D = ((uint32_t)sym_deg[k] + 8u) * 0x11111111u;
+                cnt[k] = make_uint4(D - 2u * c.x, D - 2u * c.y, D - 2u * c.z, D - 2u * c.w);
             } else {
                 uint32_t b[7] = {0, 0, 0, 0, 0, 0, 0};     // count <= 127: seven slices
                 for (int e = 0; e < dv_max; ++e) {
@@ -420,6 +439,7 @@ __device__ __forceinline__ void decode_job(const Job& A, const uint32_t* thr_src
             const float scale = A.scale, wgt = A.w, fix_R = A.fix_R;
             const int32_t fix_kmax = A.fix_kmax, fix_W = A.fix_W;
             const bool single = !ADAPT && A.single;
+            const uint32_t nib_shift = 4u * (lane & 7);
             unsigned long long my_best = ~0ull;      // single-bit variant: (E key << 32) | k
             // one group of four symbols; only the last group of a code with n % 4 != 0 is partial
             auto group = [&](const int g, auto partial_tag) {
@@ -440,21 +460,19 @@ __device__ __forceinline__ void decode_job(const Job& A, const uint32_t* thr_src
                 for (int j = 0; j < 4; ++j) {
                     const int k = k0 + j;
                     if (kPartial && k >= n) break;
-                    int unsat_cnt, deg;
+                    int S;
                     if constexpr (!WIDE) {
-                        const uint4 c = cnt[k];
-                        unsat_cnt = (int)(((c.x >> lane) & 1u) | (((c.y >> lane) & 1u) << 1) |
-                                          (((c.z >> lane) & 1u) << 2));
-                        deg = (int)c.w;
+                        // this slot's 4-bit lane of the symbol's count word: S_k + 8
+                        const uint32_t cw = reinterpret_cast<const uint32_t*>(cnt)[4 * k + (lane >> 3)];
+                        S = (int)((cw >> nib_shift) & 0xFu) - 8;
                     } else {
                         const uint4 c = cnt[2 * k], d = cnt[2 * k + 1];
-                        unsat_cnt = (int)(((c.x >> lane) & 1u) | (((c.y >> lane) & 1u) << 1) |
-                                          (((c.z >> lane) & 1u) << 2) | (((c.w >> lane) & 1u) << 3) |
-                                          (((d.x >> lane) & 1u) << 4) | (((d.y >> lane) & 1u) << 5) |
-                                          (((d.z >> lane) & 1u) << 6));
-                        deg = (int)d.w;
+                        const int unsat_cnt = (int)(((c.x >> lane) & 1u) | (((c.y >> lane) & 1u) << 1) |
+                                                    (((c.z >> lane) & 1u) << 2) | (((c.w >> lane) & 1u) << 3) |
+                                                    (((d.x >> lane) & 1u) << 4) | (((d.y >> lane) & 1u) << 5) |
+                                                    (((d.z >> lane) & 1u) << 6));
+                        S = (int)d.w - 2 * unsat_cnt;
                     }
-                    const int S = deg - 2 * unsat_cnt;
                     const uint32_t xword = xw[k];
                     const bool xneg = (xword >> lane) & 1u;
                     const float q = __fmul_rn(scale, z[j]);

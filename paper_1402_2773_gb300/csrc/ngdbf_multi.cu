@@ -11,14 +11,14 @@ __global__ void __launch_bounds__(1024) ngdbf_multi_kernel(const __grid_constant
     __shared__ Job job;
     __shared__ int32_t next_job;
     const SmemLayout L = smem_layout(A.n_max, A.m_max, A.t_max, A.dv_max, A.dc_max, ADAPT,
-                                     ST_SMEM && (ADAPT || SMOOTH), A.tables_smem != 0);
+                                     ST_SMEM && (ADAPT || SMOOTH), A.placement);
     HeldT* ys = static_cast<HeldT*>(A.yslots) + (size_t)blockIdx.x * A.n_max * kSlots;
     uint16_t* st = A.st_global ? A.st_global + (size_t)blockIdx.x * A.n_max * kSlots : nullptr;
     int j = A.first_job[blockIdx.x];
     while (j >= 0) {
         if (threadIdx.x == 0) job = A.jobs[j];
         __syncthreads();
-        decode_job<ADAPT, SMOOTH, ST_SMEM, WIDE, PREC>(job, job.thr, A.G, L, A.tables_smem != 0, ys, st);
+        decode_job<ADAPT, SMOOTH, ST_SMEM, WIDE, PREC>(job, job.thr, A.G, L, A.placement, ys, st);
         // the next job: the one with the most unclaimed frames (none left: done)
         if (threadIdx.x == 0) {
             long long best = 0;

@@ -192,7 +192,7 @@ ngdbf_status issue(ngdbf_server* S, Launch* Lc, const LaunchLayout& L, int si) {
     A.first_job = reinterpret_cast<const int32_t*>(base + L.off_first);
     A.n_max = L.plan.n_max; A.m_max = L.plan.m_max; A.t_max = L.plan.t_max;
     A.dv_max = L.plan.dv_max; A.dc_max = L.plan.dc_max;
-    A.tables_smem = L.plan.tables_smem ? 1 : 0;
+    A.placement = L.plan.placement;
     A.yslots = base + L.off_y;
     A.st_global = L.plan.state_global ? reinterpret_cast<uint16_t*>(base + L.off_st) : nullptr;
     host_gen_consts(S->seed, A.G);

@@ -77,7 +77,7 @@ int main(void) {
            sizeof(ngdbf_job), sizeof(ngdbf_launch_info));
     F(ngdbf_job, code) F(ngdbf_job, y) F(ngdbf_job, n_frames) F(ngdbf_job, sigma) F(ngdbf_job, params)
     F(ngdbf_job, frame_offset) F(ngdbf_job, bits) F(ngdbf_job, iters) F(ngdbf_job, pass)
-    F(ngdbf_params, q_bits) F(ngdbf_launch_info, sm_count)
+    F(ngdbf_params, q_bits) F(ngdbf_launch_info, sm_count) F(ngdbf_launch_info, tables_in_smem)
     return 0;
 }
 ''')
@@ -92,3 +92,4 @@ int main(void) {
     assert int(got["ngdbf_job.pass"]) == ngdbf.ngdbf_job.pass_.offset
     assert int(got["ngdbf_params.q_bits"]) == ngdbf.ngdbf_params.q_bits.offset
     assert int(got["ngdbf_launch_info.sm_count"]) == ngdbf.ngdbf_launch_info.sm_count.offset
+    assert int(got["ngdbf_launch_info.tables_in_smem"]) == ngdbf.ngdbf_launch_info.tables_in_smem.offset

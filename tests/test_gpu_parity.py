@@ -128,12 +128,15 @@ def test_global_state_path(O):
     assert ngdbf.ngdbf_last_launch()["state_in_smem"] == 0
 
 
-def test_tables_in_global_memory(O):
-    """State fits shared memory only once the adjacency tables are moved out."""
-    code = wl.peg_code(2600, 1300, 3, seed=2)
+@pytest.mark.parametrize("n", [2250, 2400])
+def test_tables_in_global_memory(O, n):
+    """The per-slot state fits shared memory only with the M(k) table (and, at N=2400,
+    the N(i) table too) in global memory."""
+    code = wl.peg_code(n, n // 2, 3, seed=2)
     y, _, sig = wl.frames(code, 40, 2.5, seed=1)
     assert_parity(O, code, y, sig, seed=4, lam=0.98, t_max=60, variant=1)
-    assert ngdbf.ngdbf_last_launch()["state_in_smem"] == 1
+    info = ngdbf.ngdbf_last_launch()
+    assert info["state_in_smem"] == 1 and info["tables_in_smem"] in ((0, 1) if n == 2250 else (0,))
 
 
 @pytest.mark.parametrize("kw", [
