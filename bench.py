@@ -42,15 +42,17 @@ PARAMS = dict(w=0.1875, theta=-0.7, eta=0.65, lam=0.993, y_max=2.0, t_max=300, s
 PRECISIONS = {"fp32": (0, 0, "f32"), "fp16": (1, 0, "f16"), "fix8": (2, 8, "i8")}
 DATA_SEED = 2014          # information bits and channel noise
 DECODER_SEED = 1          # Philox key of the perturbation
-# Algorithmic lane operations per (symbol, iteration) of the FP32 path: Philox 20 + uniforms 4
-# + ln 10.5 + sqrt 1 + sin/cos 13.5 + Box-Muller products 1 + perturbation 1 + inversion
-# function 5 + decision bit 1 + penalty sum (2 d_v + 2) + threshold, adaptation, window and
-# ballot 4 = 63 + 2 d_v, i.e. 75 for d_v = 6 (breakdown in the design doc).
-OPS_PER_SYMBOL_ITER = 75
-# DRAM bytes (read + write) per decoded frame of the decode kernel, from the ncu capture in
-# profiles/ngdbf_persistent_kernel_peg6x32_n2048_smngdbf.md (2*10^4 frames per Eb/N0 point,
-# samples 164 MB per launch; traffic scales with frames).  Set to None when the kernel changes.
-DRAM_BYTES_PER_FRAME = 10_460
+# Algorithmic lane operations per (symbol, iteration) of the FP32 path: Philox4x32-10 20 (per
+# 4 symbols: 10 rounds of two wide multiplies, counted as 4, and 4 XOR) + inverse-CDF deviate 13
+# (odd integer 1, leading zeros 1, normalize 1, segment index 2, table load 1, position v 3,
+# cubic 3, sign 1) + perturbation 1 + inversion function 5 + decision bit 1 + penalty sum
+# (2 d_v + 2) + threshold, adaptation, window and ballot 4 = 46 + 2 d_v, i.e. 58 for d_v = 6.
+OPS_PER_SYMBOL_ITER = 58
+# DRAM bytes (read + write) per decoded frame of the decode kernel, from an ncu capture of
+# this workload at 2*10^4 frames per Eb/N0 point (samples 164 MB per launch, larger than L2):
+# 183.29 MB read + 24.59 MB written per launch; traffic scales with frames, each frame's samples
+# being read once.  Set to None when the kernel changes without a new capture.
+DRAM_BYTES_PER_FRAME = 10_394
 
 
 def env_rank():
@@ -263,14 +265,18 @@ def run_ours(args):
     sm_count = launch.get("sm_count") or 152
     peak_ops = sm_count * 128 * peak_mhz * 1e6      # 4 schedulers x 32 lanes issue per SM-clock
     achieved = ops_per_launch / mean_launch_s
-    traffic = DRAM_BYTES_PER_FRAME * F if DRAM_BYTES_PER_FRAME else None
+    # the capture behind DRAM_BYTES_PER_FRAME is of the FP32 kernel
+    traffic = DRAM_BYTES_PER_FRAME * F if (DRAM_BYTES_PER_FRAME and args.precision == "fp32") else None
     rl = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12, "unit": "Tlane-op/s",
           "frac": achieved / peak_ops, "traffic": traffic,
           "kernel": "ngdbf_persistent_kernel<ADAPT,SMOOTH,state in smem>",
           "ops_per_symbol_iter": OPS_PER_SYMBOL_ITER,
+          "ops_basis": "FP32 path" if args.precision == "fp32" else
+                       "FP32 path count; the rounding or quantizing steps of this precision are not counted",
           "algorithmic_bytes_per_launch": F * (4 * code.n + nb + 5),
           "traffic_basis": "ncu dram__bytes_read.sum + dram__bytes_write.sum per frame on a 2*10^4-frame "
-                           "capture, scaled to the launch's frames",
+                           "capture, scaled to the launch's frames" if traffic else
+                           "no capture of this precision's kernel",
           "symbol_iters_per_launch": float(np.mean(sym_iters)), "mean_launch_ms": mean_launch_s * 1e3,
           "peak_basis": f"{sm_count} SMs x 128 lanes x {peak_mhz:.0f} MHz (max SM clock)"}
 

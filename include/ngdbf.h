@@ -155,7 +155,9 @@ ngdbf_status ngdbf_decode(const ngdbf_code_t* code, const float* y, int64_t n_fr
  * the next chunk is copied, copies the outputs back, and returns when the
  * host outputs are written.  Page-locked host buffers give overlapped
  * copies; pageable ones work but serialize.  Same layouts as ngdbf_decode.
- * chunk_frames <= 0 picks a chunk size automatically.
+ * chunk_frames <= 0 picks a chunk size automatically: a quarter of the call,
+ * between 256 MB and 2 GB of samples (at least 4096 frames); two chunks of
+ * device scratch are held at a time.
  */
 ngdbf_status ngdbf_decode_host(const ngdbf_code_t* code, const float* y_host, int64_t n_frames,
                                float sigma, const ngdbf_params* params, uint64_t seed,

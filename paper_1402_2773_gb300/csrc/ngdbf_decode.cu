@@ -554,8 +554,12 @@ ngdbf_status ngdbf_decode_host(const ngdbf_code_t* C, const float* y_host, int64
     if (!y_host || !bits_host || !iters_host || !pass_host) return fail(NGDBF_ERR_INVALID_ARG, "NULL buffer");
     const int64_t n = C->n, nb = (C->n + 7) / 8;
     if (chunk_frames <= 0) {
-        // about 256 MB of samples per chunk, at least 4096 frames
-        chunk_frames = std::max<int64_t>(4096, (int64_t)(256ll << 20) / (4 * n));
+        // A quarter of the call per chunk (so that copies overlap decoding and only the
+        // last chunk's tail, where a CTA waits for its slowest frame, is exposed), between
+        // 256 MB and 2 GB of samples, at least 4096 frames.
+        const int64_t lo = std::max<int64_t>(4096, (int64_t)(256ll << 20) / (4 * n));
+        const int64_t hi = std::max<int64_t>(lo, (int64_t)(2048ll << 20) / (4 * n));
+        chunk_frames = std::min(hi, std::max(lo, (n_frames + 3) / 4));
     }
     chunk_frames = std::min(chunk_frames, n_frames);
     int dev = 0;
