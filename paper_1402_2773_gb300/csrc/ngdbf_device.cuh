@@ -68,10 +68,4 @@ __device__ __forceinline__ void gauss4(uint32_t g, uint32_t t, uint32_t flo, uin
     for (int i = 0; i < 4; ++i) z[i] = gauss_icdf(r[i], tab);
 }
 
-// E_k = ((x_k y_k) + w S_k) + q_k, rounded after every operation (Sec. III-C, Step 2).
-__device__ __forceinline__ float inversion_metric(bool x_negative, float y, int S, float w, float q) {
-    const float xy = x_negative ? -y : y;
-    return __fadd_rn(__fadd_rn(xy, __fmul_rn(w, __int2float_rn(S))), q);
-}
-
 }  // namespace ngdbf

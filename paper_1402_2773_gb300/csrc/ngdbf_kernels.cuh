@@ -440,19 +440,30 @@ __device__ __forceinline__ void decode_job(const Job& A, const uint32_t* thr_src
             const int32_t fix_kmax = A.fix_kmax, fix_W = A.fix_W;
             const bool single = !ADAPT && A.single;
             const uint32_t nib_shift = 4u * (lane & 7);
+            const float wgt_m8 = -8.0f * wgt;       // exact
             unsigned long long my_best = ~0ull;      // single-bit variant: (E key << 32) | k
             // one group of four symbols; only the last group of a code with n % 4 != 0 is partial
             auto group = [&](const int g, auto partial_tag) {
                 constexpr bool kPartial = decltype(partial_tag)::value;
                 const int k0 = 4 * g;
-                // issue the sample and state loads before the generator's arithmetic
+                // issue the sample, state, count, decision-word and threshold loads before the
+                // generator's arithmetic, so that their latency overlaps it
                 HeldT yv[4];
-                [[maybe_unused]] uint32_t sv[4];
+                [[maybe_unused]] uint32_t sv[4], cwv[4], thv[4];
+                uint32_t xwv[4];
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
                     const bool in = !kPartial || k0 + j < n;
                     yv[j] = in ? ys[(k0 + j) * kSlots + lane] : HeldT(0);
                     if constexpr (kState) sv[j] = in ? (uint32_t)st[(k0 + j) * kSlots + lane] : 0u;
+                    if constexpr (!WIDE)
+                        cwv[j] = in ? reinterpret_cast<const uint32_t*>(cnt)[4 * (k0 + j) + (lane >> 3)] : 0u;
+                    xwv[j] = in ? xw[k0 + j] : 0u;
+                }
+                if constexpr (ADAPT) {
+                    // u_k <= t - 1 < T for a live slot (cleared on every refill)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) thv[j] = thr[sv[j] & kUMask];
                 }
                 float z[4];
                 gauss4((uint32_t)g, (uint32_t)t, flo, fhi, G, icdf, z);
@@ -461,10 +472,13 @@ __device__ __forceinline__ void decode_job(const Job& A, const uint32_t* thr_src
                     const int k = k0 + j;
                     if (kPartial && k >= n) break;
                     int S;
+                    float ws;           // fl(w S_k)
                     if constexpr (!WIDE) {
-                        // this slot's 4-bit lane of the symbol's count word: S_k + 8
-                        const uint32_t cw = reinterpret_cast<const uint32_t*>(cnt)[4 * k + (lane >> 3)];
-                        S = (int)((cw >> nib_shift) & 0xFu) - 8;
+                        // this slot's 4-bit lane of the symbol's count word: S_k + 8, and
+                        // w S_k = fl(w (S_k + 8) - 8 w) in one rounding (8 w is exact)
+                        const uint32_t nib = (cwv[j] >> nib_shift) & 0xFu;
+                        S = (int)nib - 8;
+                        ws = __fmaf_rn(wgt, __uint2float_rn(nib), wgt_m8);
                     } else {
                         const uint4 c = cnt[2 * k], d = cnt[2 * k + 1];
                         const int unsat_cnt = (int)(((c.x >> lane) & 1u) | (((c.y >> lane) & 1u) << 1) |
@@ -472,21 +486,28 @@ __device__ __forceinline__ void decode_job(const Job& A, const uint32_t* thr_src
                                                     (((d.x >> lane) & 1u) << 4) | (((d.y >> lane) & 1u) << 5) |
                                                     (((d.z >> lane) & 1u) << 6));
                         S = (int)d.w - 2 * unsat_cnt;
+                        ws = __fmul_rn(wgt, __int2float_rn(S));
                     }
-                    const uint32_t xword = xw[k];
-                    const bool xneg = (xword >> lane) & 1u;
+                    const uint32_t xword = xwv[j];
+                    // x_k = -1 as the sign bit of x_k y_k, and as a bool
+                    const uint32_t xsign = (xword << (31 - lane)) & 0x80000000u;
+                    [[maybe_unused]] const bool xneg = xsign != 0u;
                     const float q = __fmul_rn(scale, z[j]);
+                    // E_k = ((x_k y_k) + w S_k) + q_k, rounded after every operation (Step 2)
+                    auto metric32 = [&]() -> float {
+                        const float xy = __uint_as_float(__float_as_uint((float)yv[j]) ^ xsign);
+                        return __fadd_rn(__fadd_rn(xy, ws), q);
+                    };
                     // below_threshold(u): E_k < theta_k in the held arithmetic
                     auto below = [&](uint32_t th_bits) -> bool {
                         if constexpr (PREC == kFP32) {
-                            return inversion_metric(xneg, yv[j], S, wgt, q) < __uint_as_float(th_bits);
+                            return metric32() < __uint_as_float(th_bits);
                         } else if constexpr (PREC == kFP16) {
                             // each result rounded to binary16 (one FP32 operation on binary16
                             // operands, then one rounding, is the binary16 operation)
                             const float y16 = __half2float(yv[j]);
                             const float xy = xneg ? -y16 : y16;
-                            const float ws = to_half(__fmul_rn(wgt, __int2float_rn(S)));
-                            const float e1 = to_half(__fadd_rn(xy, ws));
+                            const float e1 = to_half(__fadd_rn(xy, to_half(ws)));
                             const float E = to_half(__fadd_rn(e1, to_half(q)));
                             return E < __uint_as_float(th_bits);
                         } else {
@@ -501,12 +522,11 @@ __device__ __forceinline__ void decode_job(const Job& A, const uint32_t* thr_src
                             // Step 3a: remember this lane's least E_k; flips wait for all symbols
                             uint32_t key;
                             if constexpr (PREC == kFP32) {
-                                key = order_key(inversion_metric(xneg, yv[j], S, wgt, q));
+                                key = order_key(metric32());
                             } else if constexpr (PREC == kFP16) {
                                 const float y16 = __half2float(yv[j]);
                                 const float xy = xneg ? -y16 : y16;
-                                const float ws = to_half(__fmul_rn(wgt, __int2float_rn(S)));
-                                const float e1 = to_half(__fadd_rn(xy, ws));
+                                const float e1 = to_half(__fadd_rn(xy, to_half(ws)));
                                 key = order_key(to_half(__fadd_rn(e1, to_half(q))));
                             } else {
                                 const int32_t Y = 2 * (int32_t)yv[j] + 1;
@@ -524,12 +544,12 @@ __device__ __forceinline__ void decode_job(const Job& A, const uint32_t* thr_src
                     bool flip;
                     if constexpr (kState) {
                         const uint32_t s0 = sv[j];
-                        // u_k <= t - 1 < T for a live slot (cleared on every refill)
-                        const uint32_t th = ADAPT ? thr[s0 & kUMask] : th0;
+                        const uint32_t th = ADAPT ? thv[j] : th0;
                         const bool lower = below(th);       // evaluated for every lane, no branch
                         flip = act && lower;
+                        // u_k += 1 when not flipped; the window counter counts x_k = -1
                         const uint32_t nv = s0 + ((ADAPT && act && !flip) ? 1u : 0u) +
-                                            ((window && xneg) ? (1u << kCShift) : 0u);
+                                            (window ? (xsign >> (31 - kCShift)) : 0u);
                         if (ADAPT || nv != s0) st[k * kSlots + lane] = (uint16_t)nv;
                     } else {
                         const bool lower = below(th0);
