@@ -201,8 +201,8 @@ size_t held_bytes(int precision) { return precision == NGDBF_FP16 ? 2 : (precisi
 // state stays in shared memory whenever some candidate fits with it there (it is read and
 // written for every symbol and slot); among those candidates the most resident warps per
 // SM win, then the most CTAs per SM, then more tables in shared memory (both, then the
-// N(i) table only).  fn_of(st) gives the kernel for a state placement.  Results are cached
-// per shape and device.
+// M(k) table, then the N(i) table).  fn_of(st) gives the kernel for a state placement.
+// Results are cached per shape and device.
 struct PlacementChoice {
     bool st_smem = false;
     int placement = 0, block = 0, bps = 0;
@@ -233,7 +233,7 @@ ngdbf_status choose_placement(int dev, int n, int m, int t_max, int dv_max, int 
         cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, limit);
         if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
         if (best.bps > 0) break;                       // state fits in shared memory
-        for (const int tb : {kTabChk | kTabSym, kTabChk, 0}) {
+        for (const int tb : {kTabChk | kTabSym, kTabSym, kTabChk, 0}) {
             const SmemLayout L = smem_layout(n, m, t_max, dv_max, dc_max, adapt, st, tb);
             if (L.total > limit) continue;
             for (const int block : {1024, 512, 256}) {
