@@ -27,15 +27,16 @@
  *     all checks were satisfied (the smoothed output is not re-checked).
  *   - q_k is drawn by Philox4x32-10 (Salmon et al., SC'11) keyed by
  *     (seed_lo, seed_hi) with counter (k/4, t, frame_lo, frame_hi), where
- *     frame = frame_offset + index of the frame in the call, and mapped by
- *     Box-Muller: u = ((r >> 9) + 1/2) 2^-23; symbols 4g, 4g+1 take
- *     rho cos(2 pi u1), rho sin(2 pi u1), rho = sqrt(-2 ln u0), from outputs
- *     (r0, r1); symbols 4g+2, 4g+3 take the same from (r2, r3).  ln, sin and
- *     cos are evaluated in FP32 from their series (atanh series of ln;
- *     Taylor series of sin/cos of (pi/2) xi, |xi| <= 1/2, after an exact
- *     quadrant split); the perturbation is fl32(eta * sigma) * z.  A frame's
- *     result therefore depends only on (y, sigma, params, seed, frame id):
- *     never on the other frames of the call or on the launch shape.
+ *     frame = frame_offset + index of the frame in the call; symbol 4g + i
+ *     takes output r_i, mapped to a standard normal deviate z by inversion
+ *     of the normal CDF: bit 31 of r is the sign, p = (2 (r mod 2^31) + 1)
+ *     2^-33, and Phi^{-1}(p) is evaluated in FP32 as a cubic in the position
+ *     of p inside one of 32 x 8 segments (dyadic intervals of p, each split
+ *     in eight), with coefficients that interpolate Phi^{-1} at the segment's
+ *     Chebyshev nodes (ngdbf_gaussian_range exposes the deviates).  The
+ *     perturbation is fl32(eta * sigma) * z.  A frame's result therefore
+ *     depends only on (y, sigma, params, seed, frame id): never on the other
+ *     frames of the call or on the launch shape.
  *   - Errors: every function returns a status and never aborts;
  *     ngdbf_last_error() gives a message for the calling thread.  CUDA
  *     errors raised by earlier asynchronous work may surface on a later call.

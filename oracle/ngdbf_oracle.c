@@ -598,7 +598,7 @@ int oracle_decode_f32(int32_t n, int32_t m, const int32_t* row_ptr, const int32_
                bits, iters, pass, n_threads);
 }
 
-/* FP64 decoder on the same uniforms: the statistical reference. */
+/* FP64 decoder on the same Philox outputs: the statistical reference. */
 int oracle_decode_f64(int32_t n, int32_t m, const int32_t* row_ptr, const int32_t* col_idx,
                       const float* y, int64_t n_frames, float sigma, const orc_params* P,
                       uint64_t seed, uint64_t frame_offset, uint8_t* bits, int32_t* iters,

@@ -11,12 +11,13 @@
 //   B. retires slots whose frame satisfied every check (pass) or reached T
 //      (smoothed output, Sec. III-E), writes their outputs, takes new frames
 //      from a global atomic queue for them and loads those frames,
-//   A'. adds, per symbol, the syndrome words of M(k) into a bit-sliced counter
-//      of unsatisfied checks (shared by the 32 slots), then
-//   C. runs Step 2 / Step 3b for every symbol of every live slot: a warp
-//      processes four symbols (one Philox call) at a time with lane = slot,
-//      reads the lane's count, forms E_k = x_k y_k + w S_k + q_k, compares it
-//      with theta lambda^{u_k}, adapts u_k, accumulates the smoothing counter,
+//   A'. adds, per symbol, the unsatisfied-check words of M(k) lane-wise (one
+//      4-bit lane per slot; bit-sliced for symbol degrees above 7) into the
+//      count of unsatisfied checks, shared by the 32 slots, then
+//   C. runs Step 2 / Step 3b (or Step 3a) for every symbol of every live slot:
+//      a warp processes four symbols (one Philox call) at a time with lane =
+//      slot, reads the lane's count, forms E_k = x_k y_k + w S_k + q_k, compares
+//      it with theta lambda^{u_k}, adapts u_k, accumulates the smoothing counter,
 //      and rebuilds the decision word with a warp ballot.
 // Slots therefore iterate independently (each frame has its own t), a
 // converged frame frees its slot at once, and the CTA only stops when the
@@ -26,7 +27,8 @@
 // [k][slot], L2-resident), and a 16-bit word holding u_k (bits 0-8) and
 // the number of -1 decisions inside the smoothing window (bits 9-15), in
 // shared memory when it fits, else in global scratch.  Decision and syndrome
-// words, the code adjacency, and the threshold table live in shared memory.
+// words, counts, the threshold and generator tables live in shared memory, the
+// adjacency tables there when they fit.
 #pragma once
 
 #include <cuda_fp16.h>

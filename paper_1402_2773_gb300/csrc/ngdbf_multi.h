@@ -7,9 +7,9 @@
 
 namespace ngdbf {
 
-// The job-table kernel for a variant (NGDBF_ADAPT | NGDBF_SMOOTH), a precision and the
-// placements of the per-slot state and the count slices; usable with cudaFuncSetAttribute
-// and the occupancy calculator.
+// The job-table kernel for a variant (NGDBF_ADAPT | NGDBF_SMOOTH | NGDBF_SINGLE), a precision,
+// the placement of the per-slot state and the count layout (4-bit lanes for symbol degrees up to
+// 7, bit slices above); usable with cudaFuncSetAttribute and the occupancy calculator.
 void* multi_kernel_fn(int variant, int precision, bool st_smem, bool wide);
 
 // Launches the job-table kernel `fn` on `stream`.

@@ -243,7 +243,7 @@ def test_precision_variants_workloads(O, prec):
 
 @pytest.mark.parametrize("prec", PRECISIONS[:2], ids=PREC_IDS[:2])
 def test_precision_variants_global_state_and_wide(O, prec):
-    """State in global memory (N=8192) and symbol degree above 7 (seven count slices)."""
+    """State in global memory (N=8192) and symbol degree above 7 (bit-sliced counts)."""
     code = wl.peg_code(8192, 1639, 3, seed=1)
     y, _, sig = wl.frames(code, 40, 3.0, seed=34)
     assert_parity(O, code, y, sig, seed=4, lam=0.99, t_max=80, smooth_window=20, variant=3, **prec)
