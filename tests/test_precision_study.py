@@ -1,17 +1,21 @@
 """Reduced-precision decoding against the FP64 reference decoder (FER/BER, 95 % intervals, Eb/N0 shift).
 
-The (3,6) N=1008 code with the plain M-NGDBF parameters (w = 0.75, theta = -0.9,
-eta = 0.96, T = 100, Y_max = 2.5) at Eb/N0 = 3.5, 4.0, 4.5 dB.  The FP64
-reference decoder and the GPU's FP32, FP16 and 8-bit fixed-point paths decode
-the same seeded frames with the same perturbation stream.  For each variant:
-the Eb/N0 shift -- the horizontal distance between the log-FER curves,
-interpolated linearly in Eb/N0 -- must be at most 0.1 dB; FP32 and FP16 must
-also lie inside the FP64 decoder's 95 % interval at every point.  The 8-bit
-fixed point moves theta and w to their level values (Eq. 8), to which the
+Two studies.  (1) The (3,6) N=1008 code with the plain M-NGDBF parameters
+(w = 0.75, theta = -0.9, eta = 0.96, T = 100, Y_max = 2.5) at Eb/N0 = 3.5, 4.0,
+4.5 dB, 2*10^4 frames per point.  (2) The (6,32) N=2048 code with the SM-NGDBF
+parameters of the throughput workload (adaptive thresholds, smoothing, T = 300)
+at 3.5, 3.75, 4.0 dB, 5*10^3 frames per point (the FP64 reference decoder runs
+on the host cores).  In each, the FP64 reference decoder and the GPU's FP32,
+FP16 and 8-bit fixed-point paths decode the same seeded frames with the same
+perturbation stream.  For each variant: the Eb/N0 shift -- the horizontal
+distance between the log-FER curves, interpolated linearly in Eb/N0, at the
+FP64 FER of the middle point -- must be at most 0.1 dB; FP32 and FP16 must also
+lie inside the FP64 decoder's 95 % interval at every point.  The 8-bit fixed
+point moves theta and w to their level values (Eq. 8), to which the
 non-adaptive decoder is sensitive (Sec. IV-C); the study records whether its
-FER is inside the FP64 interval and also compares it with the FP64 decoder
-run on those quantized parameters.  Set NGDBF_REPORT_DIR to also write the
-numbers to precision_study.json there.
+FER is inside the FP64 interval and also compares it with the FP64 decoder run
+on those quantized parameters.  Set NGDBF_REPORT_DIR to also write the numbers
+to precision_study.json there.
 """
 import json
 import math
@@ -26,9 +30,16 @@ from paper_1402_2773_gb300 import ngdbf, workload as wl
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-EBN0 = (3.5, 4.0, 4.5)
-FRAMES_FP64 = int(os.environ.get("NGDBF_STUDY_FP64_FRAMES", "20000"))
-PARAMS = dict(w=0.75, theta=-0.9, eta=0.96, lam=1.0, y_max=2.5, t_max=100, smooth_window=64, variant=0)
+STUDIES = {
+    "c1_plain": dict(code=wl.code_c1, name="peg(3,6) N=1008 M=504", ebn0=(3.5, 4.0, 4.5),
+                     frames=int(os.environ.get("NGDBF_STUDY_FP64_FRAMES", "20000")),
+                     params=dict(w=0.75, theta=-0.9, eta=0.96, lam=1.0, y_max=2.5, t_max=100,
+                                 smooth_window=64, variant=0)),
+    "c2_sm": dict(code=wl.code_c2, name="peg(6,32) N=2048 M=384", ebn0=(3.5, 3.75, 4.0),
+                  frames=int(os.environ.get("NGDBF_STUDY_FP64_FRAMES_C2", "5000")),
+                  params=dict(w=0.1875, theta=-0.7, eta=0.65, lam=0.993, y_max=2.0, t_max=300,
+                              smooth_window=64, variant=3)),
+}
 VARIANTS = {"fp32": (ngdbf.NGDBF_FP32, 0), "fp16": (ngdbf.NGDBF_FP16, 0), "fix8": (ngdbf.NGDBF_FIX, 8)}
 
 
@@ -40,14 +51,14 @@ def wilson(k, n, z=1.96):
     return max(0.0, c - h), min(1.0, c + h)
 
 
-def ebn0_at(fer_curve, target):
+def ebn0_at(ebn0, fer_curve, target):
     """Eb/N0 where the piecewise-linear log10(FER) curve reaches target."""
     lf = [math.log10(max(f, 1e-12)) for f in fer_curve]
     lt = math.log10(target)
-    for i in range(len(EBN0) - 1):
+    for i in range(len(ebn0) - 1):
         a, b = lf[i], lf[i + 1]
         if (a - lt) * (b - lt) <= 0 and a != b:
-            return EBN0[i] + (EBN0[i + 1] - EBN0[i]) * (a - lt) / (a - b)
+            return ebn0[i] + (ebn0[i + 1] - ebn0[i]) * (a - lt) / (a - b)
     return float("nan")
 
 
@@ -71,13 +82,15 @@ def quantized(v, q_bits, y_max):
     return (2 * b + 1) * float(y_max) / 2 ** q_bits
 
 
-def test_precision_variants_match_fp64_reference():
-    code = wl.code_c1()
+@pytest.mark.parametrize("study", list(STUDIES))
+def test_precision_variants_match_fp64_reference(study):
+    st = STUDIES[study]
+    EBN0, FRAMES_FP64, PARAMS = st["ebn0"], st["frames"], st["params"]
+    code = st["code"]()
     O = oracle.load()
     dc = ngdbf.DeviceCode.from_code(code)
     info = code.encoder().info_pos
-    report = {"code": "peg(3,6) N=1008 M=504", "params": PARAMS, "frames_per_point": FRAMES_FP64,
-              "points": {}}
+    report = {"code": st["name"], "params": PARAMS, "frames_per_point": FRAMES_FP64, "points": {}}
     refs = ["fp64", "fp64_fix8_params"]
     fer = {v: [] for v in [*refs, *VARIANTS]}
     # the FP64 decoder once more with theta and w replaced by their 8-bit fixed-point values:
@@ -127,18 +140,26 @@ def test_precision_variants_match_fp64_reference():
             pt["fix8"]["inside_fp64_fix8_params_ci95"] = bool(rlo <= pt["fix8"]["fer"] <= rhi)
             report["points"][str(eb)] = pt
         target = fer["fp64"][1]
-        e64 = ebn0_at(fer["fp64"], target)
+        e64 = ebn0_at(EBN0, fer["fp64"], target)
         report["shift_reference_fer"] = target
-        report["shift_db"] = {name: ebn0_at(fer[name], target) - e64 for name in VARIANTS}
-        report["shift_db_fix8_vs_fp64_fix8_params"] = (ebn0_at(fer["fix8"], target) -
-                                                       ebn0_at(fer["fp64_fix8_params"], target))
+        report["shift_db"] = {name: ebn0_at(EBN0, fer[name], target) - e64 for name in VARIANTS}
+        report["shift_db_fix8_vs_fp64_fix8_params"] = (ebn0_at(EBN0, fer["fix8"], target) -
+                                                       ebn0_at(EBN0, fer["fp64_fix8_params"], target))
     finally:
         dc.close()
         out = os.environ.get("NGDBF_REPORT_DIR")
         if out:
             os.makedirs(out, exist_ok=True)
-            with open(os.path.join(out, "precision_study.json"), "w") as f:
-                json.dump(report, f, indent=1)
+            path = os.path.join(out, "precision_study.json")
+            studies = {}
+            if os.path.exists(path):
+                with open(path) as f:
+                    studies = json.load(f)
+                if "points" in studies:
+                    studies = {}
+            studies[study] = report
+            with open(path, "w") as f:
+                json.dump(studies, f, indent=1)
     # FP32 is the FP64 method in single precision; FP16 keeps every decision within the
     # FP64 interval; every variant costs at most 0.1 dB
     for name in ("fp32", "fp16"):
