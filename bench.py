@@ -585,14 +585,16 @@ def run_reference(args):
     cores = os.cpu_count() or 1
     op = oracle.make_params(**PARAMS)
     # per step: a bounded sample of each Eb/N0 batch, sized so the run ends within minutes
-    per_point = max(cores, int(os.environ.get("NGDBF_REF_FRAMES", "0")) or 0)
+    per_point = int(os.environ.get("NGDBF_REF_FRAMES", "0"))
     ys, sig = [], []
-    if not per_point:
+    if per_point <= 0:
+        # about 6 s of decoding per step, from a timed probe at the middle Eb/N0
         y, _, s = wl.frames(code, 4 * cores, 4.0, seed=DATA_SEED + 1)
         t0 = time.perf_counter()
         O.decode_f32(code, y, s, op, seed=DECODER_SEED + 1, threads=cores)
         per_frame = (time.perf_counter() - t0) / (4 * cores)
-        per_point = int(max(cores, min(5000, 6.0 / max(per_frame, 1e-7) / len(EBN0_DB))))
+        per_point = int(min(5000, 6.0 / max(per_frame, 1e-7) / len(EBN0_DB)))
+    per_point = max(cores, per_point)
     for j, eb in enumerate(EBN0_DB):
         y, _, s = wl.frames(code, per_point, eb, seed=DATA_SEED + j)
         ys.append(y)
