@@ -106,7 +106,7 @@ struct MultiArgs {
     int32_t n_jobs;
     const int32_t* first_job;   // [grid]
     int32_t n_max, m_max, t_max, dv_max, dc_max;   // layout maxima over the jobs
-    int32_t placement;
+    int32_t placement;          // adjacency tables copied into shared memory: kTabChk | kTabSym
     void* yslots;               // [grid][n_max][32]
     uint16_t* st_global;        // [grid][n_max][32] when the state is not in shared memory
     GenConsts G;
