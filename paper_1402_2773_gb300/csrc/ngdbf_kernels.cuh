@@ -171,8 +171,6 @@ __device__ __forceinline__ uint32_t order_key(float v) {
     return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
 }
 
-// Rounds an FP32 value to binary16 (nearest even) and back.
-__device__ __forceinline__ float to_half(float v) { return __half2float(__float2half_rn(v)); }
 
 // Bits 0..7 of b moved to bits 0, 4, ..., 28 (one bit per 4-bit lane).
 __device__ __forceinline__ uint32_t spread_nibbles(uint32_t b) {
@@ -500,18 +498,24 @@ __device__ __forceinline__ void decode_job(const Job& A, const uint32_t* thr_src
                         const float xy = __uint_as_float(__float_as_uint((float)yv[j]) ^ xsign);
                         return __fadd_rn(__fadd_rn(xy, ws), q);
                     };
+                    // the same in binary16: each result rounded to binary16.  fl(w S_k) is the
+                    // exact product of a binary16 w and a small integer; the additions are
+                    // binary16 additions (a correctly rounded FP32 addition of binary16
+                    // operands rounded once more to binary16 gives the same value)
+                    [[maybe_unused]] auto metric16 = [&]() -> __half {
+                        if constexpr (PREC == kFP16) {
+                            const __half xy = __ushort_as_half(__half_as_ushort(yv[j]) ^ (uint16_t)(xsign >> 16));
+                            return __hadd(__hadd(xy, __float2half_rn(ws)), __float2half_rn(q));
+                        } else {
+                            return __float2half_rn(0.0f);
+                        }
+                    };
                     // below_threshold(u): E_k < theta_k in the held arithmetic
                     auto below = [&](uint32_t th_bits) -> bool {
                         if constexpr (PREC == kFP32) {
                             return metric32() < __uint_as_float(th_bits);
                         } else if constexpr (PREC == kFP16) {
-                            // each result rounded to binary16 (one FP32 operation on binary16
-                            // operands, then one rounding, is the binary16 operation)
-                            const float y16 = __half2float(yv[j]);
-                            const float xy = xneg ? -y16 : y16;
-                            const float e1 = to_half(__fadd_rn(xy, to_half(ws)));
-                            const float E = to_half(__fadd_rn(e1, to_half(q)));
-                            return E < __uint_as_float(th_bits);
+                            return __half2float(metric16()) < __uint_as_float(th_bits);
                         } else {
                             // Eq. 9 in units of Delta/2, exact integers
                             const int32_t Y = 2 * (int32_t)yv[j] + 1;
@@ -526,10 +530,7 @@ __device__ __forceinline__ void decode_job(const Job& A, const uint32_t* thr_src
                             if constexpr (PREC == kFP32) {
                                 key = order_key(metric32());
                             } else if constexpr (PREC == kFP16) {
-                                const float y16 = __half2float(yv[j]);
-                                const float xy = xneg ? -y16 : y16;
-                                const float e1 = to_half(__fadd_rn(xy, to_half(ws)));
-                                key = order_key(to_half(__fadd_rn(e1, to_half(q))));
+                                key = order_key(__half2float(metric16()));
                             } else {
                                 const int32_t Y = 2 * (int32_t)yv[j] + 1;
                                 const int32_t Qv = 2 * fix_code(q, fix_R, fix_kmax) + 1;
