@@ -143,6 +143,10 @@ ngdbf_status ngdbf_code_info(const ngdbf_code_t* code, int32_t* n, int32_t* m,
  * a work counter, about 160 * n bytes per 32 concurrently decoded frames)
  * is taken from a library-owned stream-ordered pool and returned on the
  * same stream.  All pointers must be device memory of the current device.
+ * The decision, syndrome and count words of one CTA's 32 frames must fit the
+ * device's shared memory per block (about 20 n + 16 m + 5 KB bytes for symbol
+ * degrees up to 7: n up to about 8,000 at rate 1/2 on a 227 KB device); larger
+ * codes are rejected with NGDBF_ERR_UNSUPPORTED.
  * Errors: INVALID_ARG, UNSUPPORTED, OOM, CUDA.
  */
 ngdbf_status ngdbf_decode(const ngdbf_code_t* code, const float* y, int64_t n_frames,

@@ -6,6 +6,7 @@ variant, both placements of the per-slot state (shared or global memory),
 the edge values of every parameter, and the full-size workloads on sampled
 frames.
 """
+import ctypes
 import os
 
 import numpy as np
@@ -313,6 +314,29 @@ def test_invalid_arguments_report_status():
                            out.data_ptr(), it.data_ptr(), ps.data_ptr(), 0)
     assert e.value.status == ngdbf.NGDBF_ERR_INVALID_ARG
     dc.close()
+
+
+def test_code_beyond_shared_memory_is_rejected():
+    """n = 12000, m = 6000: the code's tables build, but one CTA's decision, syndrome and count
+    words exceed shared memory, so decoding reports UNSUPPORTED (and nothing is launched)."""
+    n, m = 12000, 6000
+    row_ptr = np.arange(0, 2 * m + 1, 2, dtype=np.int32)
+    col_idx = np.arange(2 * m, dtype=np.int32)
+    h = ctypes.c_void_p()
+    i32p = ctypes.POINTER(ctypes.c_int32)
+    lib = ngdbf.load()
+    assert lib.ngdbf_code_create(n, m, row_ptr.ctypes.data_as(i32p), col_idx.ctypes.data_as(i32p),
+                                 ctypes.byref(h)) == ngdbf.NGDBF_OK
+    y = torch.zeros((4, n), dtype=torch.float32, device="cuda")
+    out = torch.empty((4, (n + 7) // 8), dtype=torch.uint8, device="cuda")
+    it = torch.empty(4, dtype=torch.int32, device="cuda")
+    ps = torch.empty(4, dtype=torch.uint8, device="cuda")
+    for variant in (0, 3):
+        with pytest.raises(ngdbf.NgdbfError) as e:
+            ngdbf.ngdbf_decode(h.value, y.data_ptr(), 4, 0.5, ngdbf.make_params(variant=variant), 1, 0,
+                               out.data_ptr(), it.data_ptr(), ps.data_ptr(), 0)
+        assert e.value.status == ngdbf.NGDBF_ERR_UNSUPPORTED and "too large" in str(e.value)
+    assert lib.ngdbf_code_destroy(h) == ngdbf.NGDBF_OK
 
 
 def test_full_size_c2_sampled(O):
