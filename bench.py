@@ -50,10 +50,9 @@ DECODER_SEED = 1          # Philox key of the perturbation
 OPS_PER_SYMBOL_ITER = 58
 # DRAM bytes (read + write) per decoded frame of the decode kernel, from an ncu capture of
 # this workload at 2*10^4 frames per Eb/N0 point (samples 164 MB per launch, larger than L2):
-# 174.5 / 173.2 / 173.9 MB per launch at 3.5 / 4.0 / 4.5 dB, mean 173.9 MB; traffic scales with
-# frames, each frame's samples being read once.  Set to None when the kernel changes without a
-# new capture.
-DRAM_BYTES_PER_FRAME = 8_693
+# 183.8 MB read + 24.9 MB written at 3.5 dB; traffic scales with frames, each frame's samples
+# being read once.  Set to None when the kernel changes without a new capture.
+DRAM_BYTES_PER_FRAME = 10_432
 
 
 def env_rank():

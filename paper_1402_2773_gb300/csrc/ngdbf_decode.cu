@@ -35,7 +35,7 @@ __global__ void __launch_bounds__(1024) ngdbf_persistent_kernel(const __grid_con
     const Job& J = A.J;
     const SmemLayout L = smem_layout(J.n, J.m, J.t_max, J.dv_max, J.dc_max, ADAPT,
                                      ST_SMEM && (ADAPT || SMOOTH), A.placement);
-    HeldT* ys = static_cast<HeldT*>(A.yslots) + (size_t)blockIdx.x * pad4(J.n) * kSlots;
+    HeldT* ys = static_cast<HeldT*>(A.yslots) + (size_t)blockIdx.x * J.n * kSlots;
     uint16_t* st = A.st_global ? A.st_global + (size_t)blockIdx.x * J.n * kSlots : nullptr;
     decode_job<ADAPT, SMOOTH, ST_SMEM, WIDE, PREC>(J, A.thr, A.G, L, A.placement, ys, st);
 }
@@ -201,8 +201,8 @@ size_t held_bytes(int precision) { return precision == NGDBF_FP16 ? 2 : (precisi
 // state stays in shared memory whenever some candidate fits with it there (it is read and
 // written for every symbol and slot); among those candidates the most resident warps per
 // SM win, then the most CTAs per SM, then more tables in shared memory (both, then the
-// M(k) table, then the N(i) table).  fn_of(st) gives the kernel for a state placement.
-// Results are cached per shape and device.
+// N(i) table alone).  fn_of(st) gives the kernel for a state placement.  Results are cached
+// per shape and device.
 struct PlacementChoice {
     bool st_smem = false;
     int placement = 0, block = 0, bps = 0;
@@ -233,7 +233,7 @@ ngdbf_status choose_placement(int dev, int n, int m, int t_max, int dv_max, int 
         cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, limit);
         if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
         if (best.bps > 0) break;                       // state fits in shared memory
-        for (const int tb : {kTabChk | kTabSym, kTabSym, kTabChk, 0}) {
+        for (const int tb : {kTabChk | kTabSym, kTabChk, 0}) {
             const SmemLayout L = smem_layout(n, m, t_max, dv_max, dc_max, adapt, st, tb);
             if (L.total > limit) continue;
             for (const int block : {1024, 512, 256}) {
@@ -406,9 +406,8 @@ ngdbf_status decode_impl(const ngdbf_code* C, const float* y, int64_t n_frames, 
     s = get_pool(dev, &pool);
     if (s != NGDBF_OK) return s;
     const bool state = (P->variant & 3) != 0;
-    const size_t slot_elems = (size_t)plan.grid * C->n * kSlots;          // state: [k][slot]
-    const size_t slot_elems_y = (size_t)plan.grid * pad4(C->n) * kSlots;  // samples: whole groups
-    const size_t bytes_y = (slot_elems_y * held_bytes(P->precision) + 255) / 256 * 256;
+    const size_t slot_elems = (size_t)plan.grid * C->n * kSlots;
+    const size_t bytes_y = (slot_elems * held_bytes(P->precision) + 255) / 256 * 256;
     const size_t bytes_st = (state && !plan.st_smem) ? (slot_elems * 2 + 255) / 256 * 256 : 0;
     const size_t total = 256 + bytes_y + bytes_st;
     void* ws = nullptr;
@@ -679,7 +678,7 @@ extern "C" ngdbf_status ngdbf_decode_noalloc(const ngdbf_code_t* C, const float*
 
     // Fit the launch into the static array: fewer CTAs when a full grid does not fit.
     const bool state = (P->variant & 3) != 0;
-    const size_t per_cta_y = (size_t)pad4(C->n) * kSlots * held_bytes(P->precision);
+    const size_t per_cta_y = (size_t)C->n * kSlots * held_bytes(P->precision);
     const size_t per_cta_st = (state && !plan.st_smem) ? (size_t)C->n * kSlots * 2 : 0;
     const size_t avail = (size_t)NGDBF_NOALLOC_SCRATCH_BYTES - 256 - 256;   // counter + alignment
     const size_t max_grid = avail / (per_cta_y + per_cta_st);
@@ -900,7 +899,7 @@ extern "C" ngdbf_status ngdbf_batch_create(const ngdbf_job* jobs, int32_t n_jobs
     int max_bps = 0;
     for (const auto& sh : shapes) max_bps = std::max(max_bps, sh.second);
     const size_t grid_max = (size_t)T.sm_count * max_bps;
-    const size_t per_slot_y = (size_t)pad4(T.n_max) * kSlots * held_bytes(T.precision);
+    const size_t per_slot_y = (size_t)T.n_max * kSlots * held_bytes(T.precision);
     const size_t per_slot_st = T.state_global ? (size_t)T.n_max * kSlots * 2 : 0;
     const size_t off_jobs = 0, off_thr = align256(sizeof(Job) * n_jobs), off_q = off_thr + align256(T.thr_words * 4);
     const size_t off_first = off_q + align256(8 * (size_t)n_jobs), off_y = off_first + align256(4 * grid_max);

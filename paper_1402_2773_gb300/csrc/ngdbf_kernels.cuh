@@ -48,14 +48,6 @@ constexpr int kTabChk = 1;              // N(i) table in shared memory
 constexpr int kTabSym = 2;              // M(k) table and degrees in shared memory
 
 constexpr int kMaxT = NGDBF_MAX_T;
-
-// Symbols rounded up to whole groups of four (the unit of the decision phase).
-__host__ __device__ constexpr int pad4(int n) { return (n + 3) & ~3; }
-// Held sample of symbol k, slot f: the four symbols of a group are adjacent for each slot.
-__host__ __device__ constexpr int ys_index(int k, int f) { return (((k >> 2) * 32 + f) << 2) | (k & 3); }
-// Count word of symbol k for slot group q = f / 8 (narrow codes): the four symbols of a group
-// are adjacent for each slot group.
-__host__ __device__ constexpr int cnt_index(int k, int q) { return (((k >> 2) * 4 + q) << 2) | (k & 3); }
 constexpr uint32_t kUMask = 0x1FFu;   // u_k: bits 0-8
 constexpr int kCShift = 9;            // smoothing count: bits 9-15
 
@@ -148,8 +140,8 @@ __host__ __device__ inline SmemLayout smem_layout(int n, int m, int t_max, int d
     L.off_ctl = take(8 * 4, 16);
     L.off_best = take(kSlots * 8, 16);     // single-bit variant: least (E key, k) per slot
     L.off_icdf = take(256 * 16, 16);       // inverse normal CDF coefficients
-    L.off_cnt = take((dv_max <= 7 ? pad4(n) : n) * cnt_bytes, 16);
-    L.off_xw = take((pad4(n) + 1) * 4, 16);
+    L.off_cnt = take(n * cnt_bytes, 16);
+    L.off_xw = take((n + 1) * 4, 16);
     L.off_sw = take((m + 1) * (dv_max <= 7 ? 16 : 4), 16);
     L.off_thr = need_thr ? take((t_max + 1) * 4, 16) : -1;
     L.off_st = st_smem ? take(n * kSlots * 2, 16) : -1;
@@ -178,7 +170,6 @@ __device__ __forceinline__ uint32_t order_key(float v) {
     if (b == 0x80000000u) b = 0u;
     return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
 }
-
 
 // Bits 0..7 of b moved to bits 0, 4, ..., 28 (one bit per 4-bit lane).
 __device__ __forceinline__ uint32_t spread_nibbles(uint32_t b) {
@@ -240,7 +231,7 @@ __device__ __forceinline__ void decode_job(const Job& A, const uint32_t* thr_src
 
     // ---- set-up: generator table, zero the state, sentinels, thresholds, first 32 frames ----
     for (int i = tid; i < 256; i += blockDim.x) icdf[i] = G.icdf[i];
-    for (int k = tid; k <= pad4(n); k += blockDim.x) xw[k] = 0u;
+    for (int k = tid; k <= n; k += blockDim.x) xw[k] = 0u;
     for (int i = tid; i < (m + 1) * (WIDE ? 1 : 4); i += blockDim.x) sw[i] = 0u;
     if constexpr (ADAPT)
         for (int u = tid; u <= T; u += blockDim.x) thr[u] = thr_src[u];
@@ -286,15 +277,15 @@ __device__ __forceinline__ void decode_job(const Job& A, const uint32_t* thr_src
                     }
                     bool negative;
                     if constexpr (PREC == kFP32) {
-                        ys[ys_index(k, f)] = v;
+                        ys[k * kSlots + f] = v;
                         negative = !(v >= 0.0f);
                     } else if constexpr (PREC == kFP16) {
                         const __half h = __float2half_rn(v);
-                        ys[ys_index(k, f)] = h;
+                        ys[k * kSlots + f] = h;
                         negative = !(__half2float(h) >= 0.0f);        // sign(-0) = +1
                     } else {
                         const int32_t b = fix_code(v, A.fix_R, A.fix_kmax);
-                        ys[ys_index(k, f)] = (int8_t)b;
+                        ys[k * kSlots + f] = (int8_t)b;
                         negative = b < 0;
                     }
                     if (negative) word |= 1u << f;
@@ -416,11 +407,7 @@ __device__ __forceinline__ void decode_job(const Job& A, const uint32_t* thr_src
                     c.x += s.x; c.y += s.y; c.z += s.z; c.w += s.w;
                 }
                 const uint32_t D = ((uint32_t)sym_deg[k] + 8u) * 0x11111111u;
-                uint32_t* cw = reinterpret_cast<uint32_t*>(cnt);
-                cw[cnt_index(k, 0)] = D - 2u * c.x;
-                cw[cnt_index(k, 1)] = D - 2u * c.y;
-                cw[cnt_index(k, 2)] = D - 2u * c.z;
-                cw[cnt_index(k, 3)] = D - 2u * c.w;
+                cnt[k] = make_uint4(D - 2u * c.x, D - 2u * c.y, D - 2u * c.z, D - 2u * c.w);
             } else {
                 uint32_t b[7] = {0, 0, 0, 0, 0, 0, 0};     // count <= 127: seven slices
                 for (int e = 0; e < dv_max; ++e) {
@@ -463,37 +450,15 @@ __device__ __forceinline__ void decode_job(const Job& A, const uint32_t* thr_src
                 HeldT yv[4];
                 [[maybe_unused]] uint32_t sv[4], cwv[4], thv[4];
                 uint32_t xwv[4];
-                [[maybe_unused]] const uint32_t* cntw = reinterpret_cast<const uint32_t*>(cnt);
-                if constexpr (!kPartial) {
-                    // whole group: one 16-byte load each for the decision words, this lane's
-                    // count words and (FP32) held samples of the four symbols
-                    const uint4 x4 = *reinterpret_cast<const uint4*>(xw + k0);
-                    xwv[0] = x4.x; xwv[1] = x4.y; xwv[2] = x4.z; xwv[3] = x4.w;
-                    if constexpr (!WIDE) {
-                        const uint4 c4 = *reinterpret_cast<const uint4*>(cntw + cnt_index(k0, lane >> 3));
-                        cwv[0] = c4.x; cwv[1] = c4.y; cwv[2] = c4.z; cwv[3] = c4.w;
-                    }
-                    if constexpr (PREC == kFP32) {
-                        const float4 y4 = *reinterpret_cast<const float4*>(ys + ys_index(k0, lane));
-                        yv[0] = y4.x; yv[1] = y4.y; yv[2] = y4.z; yv[3] = y4.w;
-                    } else {
 #pragma unroll
-                        for (int j = 0; j < 4; ++j) yv[j] = ys[ys_index(k0 + j, lane)];
-                    }
-#pragma unroll
-                    for (int j = 0; j < 4; ++j)
-                        if constexpr (kState) sv[j] = (uint32_t)st[(k0 + j) * kSlots + lane];
-                } else {
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        const bool in = k0 + j < n;
-                        yv[j] = in ? ys[ys_index(k0 + j, lane)] : HeldT(0);
-                        if constexpr (kState) sv[j] = in ? (uint32_t)st[(k0 + j) * kSlots + lane] : 0u;
-                        if constexpr (!WIDE) cwv[j] = in ? cntw[cnt_index(k0 + j, lane >> 3)] : 0u;
-                        xwv[j] = in ? xw[k0 + j] : 0u;
-                    }
+                for (int j = 0; j < 4; ++j) {
+                    const bool in = !kPartial || k0 + j < n;
+                    yv[j] = in ? ys[(k0 + j) * kSlots + lane] : HeldT(0);
+                    if constexpr (kState) sv[j] = in ? (uint32_t)st[(k0 + j) * kSlots + lane] : 0u;
+                    if constexpr (!WIDE)
+                        cwv[j] = in ? reinterpret_cast<const uint32_t*>(cnt)[4 * (k0 + j) + (lane >> 3)] : 0u;
+                    xwv[j] = in ? xw[k0 + j] : 0u;
                 }
-                uint32_t xnew[4] = {xwv[0], xwv[1], xwv[2], xwv[3]};   // decision words after the flips
                 if constexpr (ADAPT) {
                     // u_k <= t - 1 < T for a live slot (cleared on every refill)
 #pragma unroll
@@ -593,11 +558,8 @@ __device__ __forceinline__ void decode_job(const Job& A, const uint32_t* thr_src
                         flip = act && lower;
                     }
                     const uint32_t fm = __ballot_sync(0xFFFFFFFFu, flip);
-                    xnew[j] = xword ^ fm;
-                    if (kPartial && lane == 0) xw[k] = xnew[j];
+                    if (lane == 0) xw[k] = xword ^ fm;
                 }
-                if (!kPartial && lane == 0)
-                    *reinterpret_cast<uint4*>(xw + k0) = make_uint4(xnew[0], xnew[1], xnew[2], xnew[3]);
             };
             const int full = n >> 2;
             for (int g = warp; g < full; g += nwarps) group(g, std::false_type{});

@@ -12,7 +12,7 @@ __global__ void __launch_bounds__(1024) ngdbf_multi_kernel(const __grid_constant
     __shared__ int32_t next_job;
     const SmemLayout L = smem_layout(A.n_max, A.m_max, A.t_max, A.dv_max, A.dc_max, ADAPT,
                                      ST_SMEM && (ADAPT || SMOOTH), A.placement);
-    HeldT* ys = static_cast<HeldT*>(A.yslots) + (size_t)blockIdx.x * pad4(A.n_max) * kSlots;
+    HeldT* ys = static_cast<HeldT*>(A.yslots) + (size_t)blockIdx.x * A.n_max * kSlots;
     uint16_t* st = A.st_global ? A.st_global + (size_t)blockIdx.x * A.n_max * kSlots : nullptr;
     int j = A.first_job[blockIdx.x];
     while (j >= 0) {

@@ -113,7 +113,7 @@ ngdbf_status layout_launch(ngdbf_server* S, const std::vector<Request*>& reqs, L
     for (const ngdbf_job& q : jobs) groups += (q.n_frames + 31) / 32;
     L.block = L.plan.shapes[0].first;
     L.grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)L.plan.sm_count * L.plan.shapes[0].second, groups));
-    const size_t per_slot_y = (size_t)pad4(L.plan.n_max) * 32 * held_bytes(L.plan.precision);
+    const size_t per_slot_y = (size_t)L.plan.n_max * 32 * held_bytes(L.plan.precision);
     const size_t per_slot_st = L.plan.state_global ? (size_t)L.plan.n_max * 32 * 2 : 0;
     L.off_jobs = align256(8 * (size_t)J);                 // queues first
     L.off_thr = L.off_jobs + align256(sizeof(Job) * J);
@@ -230,6 +230,9 @@ void scheduler(ngdbf_server* S) {
     cudaSetDevice(S->device);
     std::unique_lock<std::mutex> lk(S->mu);
     for (;;) {
+        // requests completed or launches issued in this pass: waiters are woken after it
+        // (ngdbf_server_wait sleeps on the same condition until every request completed)
+        bool progressed = false;
         // retire finished launches
         for (size_t i = 0; i < S->inflight.size();) {
             Launch* L = S->inflight[i];
@@ -241,9 +244,9 @@ void scheduler(ngdbf_server* S) {
             finish_requests(S, L->reqs, L->t_done, NGDBF_OK);
             delete L;
             S->inflight.erase(S->inflight.begin() + i);
+            progressed = true;
         }
         // admit pending requests in arrival order into one launch per free stream
-        bool progressed = false;
         while (!S->pending.empty() && !S->stop) {
             int si = -1;
             for (int k = 0; k < (int)S->streams.size(); ++k)

@@ -62,8 +62,7 @@ def test_noalloc_matches_the_allocating_entry_point_on_two_calls():
         for a, b, name in zip(got[:3], ref[:3], ("bits", "iters", "pass")):
             assert np.array_equal(a, b), f"call {call}: {name} differ from ngdbf_decode"
         launch = got[3]
-        # held samples for whole groups of four symbols, per-slot state for the symbols
-        per_cta = (code.n + 3) // 4 * 4 * 32 * 4 + (0 if launch["state_in_smem"] else code.n * 32 * 2)
+        per_cta = code.n * 32 * 4 + (0 if launch["state_in_smem"] else code.n * 32 * 2)
         assert launch["grid"] * per_cta <= ngdbf.NGDBF_NOALLOC_SCRATCH_BYTES
         if call == 1:
             assert launch["state_in_smem"] == 0 and launch["grid"] < ref[3]["grid"]
