@@ -82,9 +82,12 @@ namespace {
 
 void CUDART_CB launch_finished(void* arg) {
     Launch* L = static_cast<Launch*>(arg);
+    // once `done` is set the scheduler may retire and delete L: read what is needed first.
+    // The server outlives this call (ngdbf_server_destroy synchronizes the streams).
+    ngdbf_server* S = static_cast<ngdbf_server*>(L->server);
     L->t_done = now_s();
     L->done.store(true);
-    static_cast<ngdbf_server*>(L->server)->cv.notify_all();
+    S->cv.notify_all();
 }
 
 // Device bytes of a request's own buffers.
