@@ -59,6 +59,31 @@ def test_host_validation_without_a_device(lib):
         ngdbf.NGDBF_ERR_INVALID_ARG
 
 
+def test_entry_points_check_arguments_before_any_device_call(lib):
+    """Argument errors of the other entry points are reported with a status and a message,
+    before any CUDA call (so they behave the same with or without a device)."""
+    p = ngdbf.make_params()
+    assert lib.ngdbf_decode_noalloc(None, None, 1, 0.5, ctypes.byref(p), 1, 0, None, None, None, None) == \
+        ngdbf.NGDBF_ERR_INVALID_ARG
+    assert lib.ngdbf_gaussian_range(0, 0, None, None) == ngdbf.NGDBF_OK            # nothing to do
+    assert lib.ngdbf_gaussian_range(0, 4, None, None) == ngdbf.NGDBF_ERR_INVALID_ARG
+    assert "NULL" in lib.ngdbf_last_error().decode()
+    out = ctypes.c_void_p()
+    for budget, inflight, jobs in ((0, 4, 16), (1 << 20, 0, 16), (1 << 20, 17, 16), (1 << 20, 4, 0),
+                                   (1 << 20, 4, 5000)):
+        assert lib.ngdbf_server_create(budget, inflight, jobs, 1, ctypes.byref(out)) == \
+            ngdbf.NGDBF_ERR_INVALID_ARG
+    assert lib.ngdbf_server_create(1 << 20, 4, 16, 1, None) == ngdbf.NGDBF_ERR_INVALID_ARG
+    job = ngdbf.ngdbf_job()
+    assert lib.ngdbf_batch_create(None, 0, 1, 0, None, ctypes.byref(out)) == ngdbf.NGDBF_ERR_INVALID_ARG
+    assert lib.ngdbf_batch_create(ctypes.byref(job), 1, 1, 1 << 8, None, ctypes.byref(out)) == \
+        ngdbf.NGDBF_ERR_INVALID_ARG
+    assert "flags" in lib.ngdbf_last_error().decode()
+    assert lib.ngdbf_batch_launch(None, None) == ngdbf.NGDBF_ERR_INVALID_ARG
+    assert lib.ngdbf_server_wait(None, 1.0) == ngdbf.NGDBF_ERR_INVALID_ARG
+    assert lib.ngdbf_code_destroy(None) == ngdbf.NGDBF_OK and lib.ngdbf_server_destroy(None) == ngdbf.NGDBF_OK
+
+
 def test_missing_library_fails_loudly(tmp_path):
     with pytest.raises(RuntimeError, match="not built"):
         ngdbf.load(str(tmp_path / "absent.so"))
