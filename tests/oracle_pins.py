@@ -540,6 +540,23 @@ def pin_metric_f16(O):
         assert got == float(want), (x, y16, S, w16, q, got, want)
 
 
+def pin_metric_f32_f64(O):
+    """E_k = ((x_k y_k) + w S_k) + q_k with one rounding per operation, in this order: FP32 equals
+    numpy float32 arithmetic and FP64 numpy float64 arithmetic on the same operands."""
+    rng = np.random.default_rng(7)
+    for _ in range(3000):
+        ys = np.float32(rng.normal() * 1.5)
+        w = np.float32(rng.uniform(0.0, 1.5))
+        S = int(rng.integers(-7, 8))
+        x = int(rng.choice([-1, 1]))
+        q = np.float32(rng.normal() * 0.7)
+        xy = ys if x > 0 else -ys
+        want = (xy + w * np.float32(S)) + q
+        assert np.float32(O.metric_f32(x, float(ys), S, float(w), float(q))) == want
+        want64 = (float(xy) + float(w) * S) + float(q)
+        assert O.metric_f64(x, float(ys), S, float(w), float(q)) == want64
+
+
 def pin_fix_quantizer(O):
     """The FP32-decided level code agrees with Eq. 8 (g in double) away from level boundaries;
     saturation, the missing zero level and the sign convention hold."""
@@ -661,6 +678,6 @@ ALL_PINS = [
     pin_trace_clamp_sign_tie, pin_trace_single_bit, pin_noiseless, pin_eta0_is_gdbf,
     pin_eta0_is_single_bit_gdbf, pin_codeword_and_ml,
     pin_f32_matches_injected_noise, pin_frame_independence, pin_f32_f64_statistics,
-    pin_round_half, pin_metric_f16, pin_fix_quantizer, pin_trace_fixed_point, pin_table2_fixed_point, pin_fp16_reduces_to_fp32,
+    pin_round_half, pin_metric_f16, pin_metric_f32_f64, pin_fix_quantizer, pin_trace_fixed_point, pin_table2_fixed_point, pin_fp16_reduces_to_fp32,
     pin_fix_reduces_to_fp32, pin_precision_statistics,
 ]

@@ -40,6 +40,7 @@ MUTANTS = [
      "uint32_t ctr[4] = {t, g, (uint32_t)frame, (uint32_t)(frame >> 32)};\n    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};\n    uint32_t r[4];\n    oracle_philox4x32_10(ctr, key, r);\n    for (int i = 0; i < 4; ++i) z[i] = oracle_gauss_f32"),
     ("noise scale", "return (float)((double)eta * (double)sigma);", "return (float)((double)eta * (double)sigma * (double)sigma);"),
     ("metric sign", "float e = xy + ws;", "float e = xy - ws;"),
+    ("metric reassociated", "float e = xy + ws;\n    return e + q;", "float e = ws + q;\n    return xy + e;"),
     ("metric drops w", "float ws = w * (float)S;", "float ws = (float)S;"),
     ("metric drops x", "float xy = x > 0 ? ys : -ys;", "float xy = ys;"),
     ("metric64 sign", "return (x > 0 ? ys : -ys) + w * (double)S + q;", "return (x > 0 ? ys : -ys) - w * (double)S + q;"),
