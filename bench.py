@@ -47,7 +47,14 @@ DECODER_SEED = 1          # Philox key of the perturbation
 # (odd integer 1, leading zeros 1, normalize 1, segment index 2, table load 1, position v 3,
 # cubic 3, sign 1) + perturbation 1 + inversion function 5 + decision bit 1 + penalty sum
 # (2 d_v + 2) + threshold, adaptation, window and ballot 4 = 46 + 2 d_v, i.e. 58 for d_v = 6.
-OPS_PER_SYMBOL_ITER = 58
+
+
+def ops_per_symbol_iter(dv: int) -> int:
+    """Algorithmic lane operations per (symbol, iteration) of the FP32 path for symbol degree dv."""
+    return 46 + 2 * int(dv)
+
+
+OPS_PER_SYMBOL_ITER = ops_per_symbol_iter(6)
 # DRAM bytes (read + write) per decoded frame of the decode kernel, from an ncu capture of
 # this workload at 2*10^4 frames per Eb/N0 point (samples 164 MB per launch, larger than L2):
 # 183.8 MB read + 24.9 MB written at 3.5 dB; traffic scales with frames, each frame's samples
@@ -419,7 +426,7 @@ def run_multicode(args):
     for jb, o in zip(jobs, host):
         it = o[1].astype(np.int64)
         dv = jb["code"].dense().sum(axis=0).max()
-        ops += float(it.sum()) * jb["code"].n * (63 + 2 * int(dv))
+        ops += float(it.sum()) * jb["code"].n * ops_per_symbol_iter(dv)
         per_code.append({"code": jb["code"].name, "frames": jb["frames"], "ebn0_db": round(jb["ebn0"], 3),
                          "t_max": jb["params"]["t_max"], "avg_iters": float(it.mean()),
                          "pass_rate": float(o[2].mean())})

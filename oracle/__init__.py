@@ -27,9 +27,12 @@ CFLAGS = ["-O2", "-fPIC", "-shared", "-std=c11", "-ffp-contract=off", "-fno-fast
 ADAPT = 1
 SMOOTH = 2
 SINGLE = 4
+UNIFORM = 8
 FP32 = 0
 FP16 = 1
 FIX = 2
+FIXACC = 3
+ACC_BITS = 8
 
 
 class Params(ctypes.Structure):
@@ -85,6 +88,14 @@ class Oracle:
             fn = getattr(lib, nm)
             fn.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, zt]
             fn.restype = None
+        lib.oracle_uniform_f32.argtypes = [ctypes.c_uint32]
+        lib.oracle_uniform_f32.restype = ctypes.c_float
+        lib.oracle_uniform4_f32.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, f32p]
+        lib.oracle_uniform4_f32.restype = None
+        lib.oracle_fixacc_scale.argtypes = [ctypes.c_int32, ctypes.c_float]
+        lib.oracle_fixacc_scale.restype = ctypes.c_float
+        lib.oracle_fixacc_steps.argtypes = [ctypes.c_float, ctypes.c_float]
+        lib.oracle_fixacc_steps.restype = ctypes.c_int32
         lib.oracle_noise_f32.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
                                          ctypes.c_float, ctypes.c_float]
         lib.oracle_noise_f32.restype = ctypes.c_float
@@ -116,6 +127,11 @@ class Oracle:
         for nm in ("oracle_decode_f32", "oracle_decode_f64"):
             fn = getattr(lib, nm)
             fn.argtypes = dec
+            fn.restype = ctypes.c_int
+        i64p = ctypes.POINTER(ctypes.c_int64)
+        for nm in ("oracle_decode_f32_trace", "oracle_decode_f64_trace"):
+            fn = getattr(lib, nm)
+            fn.argtypes = dec + [ctypes.c_int64, i32p, i64p]
             fn.restype = ctypes.c_int
         lib.oracle_decode_f32_qin.argtypes = [ctypes.c_int32, ctypes.c_int32, i32p, i32p, f32p,
                                               ctypes.POINTER(Params), f32p, u8p, i32p, u8p]
@@ -167,6 +183,22 @@ class Oracle:
         self.lib.oracle_gauss4_f64(seed, frame, t, g, z)
         return np.array(list(z), dtype=np.float64)
 
+    def uniform_f32(self, r: int) -> np.float32:
+        """Uniform deviate on (-1, 1) of one Philox output r (Sec. V-B variant)."""
+        return np.float32(self.lib.oracle_uniform_f32(ctypes.c_uint32(int(r) & 0xFFFFFFFF)))
+
+    def uniform4_f32(self, seed, frame, t, g) -> np.ndarray:
+        v = (ctypes.c_float * 4)()
+        self.lib.oracle_uniform4_f32(seed, frame, t, g, v)
+        return np.array(list(v), dtype=np.float32)
+
+    def fixacc_scale(self, q_bits: int, y_max: float) -> float:
+        """Rd = fl32(2^(Q+8) / Y_max), accumulator steps per unit of the FIXACC form."""
+        return float(np.float32(self.lib.oracle_fixacc_scale(q_bits, y_max)))
+
+    def fixacc_steps(self, v: float, Rd: float) -> int:
+        return int(self.lib.oracle_fixacc_steps(v, Rd))
+
     def noise_f32(self, seed, frame, t, k, eta, sigma) -> np.float32:
         return np.float32(self.lib.oracle_noise_f32(seed, frame, t, k, eta, sigma))
 
@@ -206,7 +238,7 @@ class Oracle:
         return list(zip(thr[:cnt].tolist(), tau[:cnt].tolist()))
 
     # -- decoders ----------------------------------------------------------------
-    def _decode(self, fn, code, y, sigma, params, seed, frame_offset, threads):
+    def _decode(self, fn, code, y, sigma, params, seed, frame_offset, threads, trace=None):
         y = np.ascontiguousarray(y, dtype=np.float32)
         F = y.shape[0]
         nb = (code.n + 7) // 8
@@ -215,15 +247,38 @@ class Oracle:
         pas = np.zeros(F, dtype=np.uint8)
         rp = np.ascontiguousarray(code.row_ptr, dtype=np.int32)
         ci = np.ascontiguousarray(code.col_idx, dtype=np.int32)
-        rc = fn(code.n, code.m, rp.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+        args = [code.n, code.m, rp.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
                 ci.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
                 y.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), F, sigma, ctypes.byref(params),
                 seed, frame_offset, bits.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
                 iters.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
-                pas.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), threads)
+                pas.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), threads]
+        if trace is not None:
+            tu, tc = trace
+            args += [tu.shape[0], tu.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                     tc.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))]
+        rc = fn(*args)
         if rc != 0:
             raise RuntimeError(f"oracle decode failed ({rc})")
         return bits, iters, pas
+
+    def _decode_trace(self, fn, code, y, sigma, params, seed, frame_offset, threads, trace_frames):
+        K = int(trace_frames)
+        tu = np.full((K, params.t_max + 1), -1, dtype=np.int32)
+        tc = np.zeros((K, params.t_max + 1), dtype=np.int64)
+        bits, iters, pas = self._decode(fn, code, y, sigma, params, seed, frame_offset, threads, (tu, tc))
+        return bits, iters, pas, tu, tc
+
+    def decode_f32_trace(self, code, y, sigma, params, trace_frames, seed=1, frame_offset=0, threads=1):
+        """FP32 decode with the objective trace of the first trace_frames frames: returns
+        (bits, iters, pass, U [K][T+1] int32, C [K][T+1] int64); entries after iters[f] stay -1 / 0.
+        f(x(t)) = C 2^-32 + m - 2 U (Sec. III-B objective)."""
+        return self._decode_trace(self.lib.oracle_decode_f32_trace, code, y, sigma, params, seed,
+                                  frame_offset, threads, trace_frames)
+
+    def decode_f64_trace(self, code, y, sigma, params, trace_frames, seed=1, frame_offset=0, threads=1):
+        return self._decode_trace(self.lib.oracle_decode_f64_trace, code, y, sigma, params, seed,
+                                  frame_offset, threads, trace_frames)
 
     def decode_f32(self, code, y, sigma, params, seed=1, frame_offset=0, threads=1):
         return self._decode(self.lib.oracle_decode_f32, code, y, sigma, params, seed, frame_offset, threads)

@@ -56,6 +56,29 @@
  *          signed code b = k (v >= 0) or -k-1 (v < 0), value 2b + 1 in units of
  *          Delta/2 = Y_max / 2^Q.  E~ = x Y~ + W~ S + Q~ in exact integers,
  *          compared with Theta~(u) = value of fl32(theta lambda^u).
+ *   FIXACC: the held sample is the Eq. 8 level code of y (Q bits) exactly as in
+ *          FIX, but the inversion function is accumulated in exact int32 in a
+ *          finer unit d = Y_max / 2^(Q+8) (256 accumulator steps per half level):
+ *          E = x (2b+1) 256 + W S + Qd with W = rint(fl32(w Rd)),
+ *          Qd = rint(fl32(q Rd)), Rd = fl32(2^(Q+8) / Y_max), compared with
+ *          Theta(u) = rint(fl32(fl32(theta lambda^u) Rd)).  Only the held sample
+ *          is quantized to Q bits; the perturbation, the weight and the
+ *          threshold keep the accumulator's resolution.
+ *
+ * Uniform perturbation (Sec. V-B: uniform samples may replace the Gaussian
+ * ones): with the UNIFORM variant bit, output r of the same Philox counter
+ * gives v = (2 (r >> 8) + 1 - 2^24) 2^-24, uniform on (-1, 1) and exact in
+ * FP32, and q_k = fl32(eta sigma sqrt 3) v (same variance eta^2 sigma^2 as the
+ * Gaussian perturbation; the paper does not state the variance, so equal
+ * variance is the reading taken).
+ *
+ * Objective trace (Sec. III-B, the GDBF objective f(x) = sum_k x_k y_k +
+ * sum_i s_i, tracked over iterations in Sec. VI): for traced frames, at every
+ * syndrome test t the decoder records U(t), the number of unsatisfied checks
+ * (so sum_i s_i = m - 2 U(t)), and C(t) = sum_k rint(x_k(t) y~_k 2^32), the
+ * correlation with the held samples y~ as an exact integer in units of 2^-32
+ * (each term is exact in double; rint only rounds terms below 2^-32, so
+ * |C(t) 2^-32 - sum_k x_k y~_k| <= n 2^-33).  f(x(t)) = C(t) 2^-32 + m - 2U(t).
  */
 #include <math.h>
 #include <pthread.h>
@@ -66,9 +89,12 @@
 #define ORC_ADAPT 1
 #define ORC_SMOOTH 2
 #define ORC_SINGLE 4
+#define ORC_UNIFORM 8
 #define ORC_FP32 0
 #define ORC_FP16 1
 #define ORC_FIX 2
+#define ORC_FIXACC 3
+#define ORC_ACC_BITS 8          /* accumulator steps per half level: 2^8 */
 
 typedef struct {
     float w, theta, eta, lambda, y_max;
@@ -223,6 +249,23 @@ void oracle_gauss4_f64(uint64_t seed, uint64_t frame, uint32_t t, uint32_t g, do
     for (int i = 0; i < 4; ++i) z[i] = oracle_gauss_f64(r[i]);
 }
 
+/* Uniform deviate of one Philox output (Sec. V-B): the top 24 bits a = r >> 8 give
+ * v = (2a + 1 - 2^24) 2^-24, an odd multiple of 2^-24 in (-1, 1): exact in FP32 and in
+ * double, symmetric (v(~r) = -v(r)), variance (1 - 2^-48) / 3. */
+float oracle_uniform_f32(uint32_t r) {
+    const int32_t odd = (int32_t)(2u * (r >> 8) + 1u) - (1 << 24);
+    return ldexpf((float)odd, -24);
+}
+
+/* Four uniform deviates for symbols 4g .. 4g+3: output i of counter (g, t, frame). */
+void oracle_uniform4_f32(uint64_t seed, uint64_t frame, uint32_t t, uint32_t g, float v[4]) {
+    uint32_t ctr[4] = {g, t, (uint32_t)frame, (uint32_t)(frame >> 32)};
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t r[4];
+    oracle_philox4x32_10(ctr, key, r);
+    for (int i = 0; i < 4; ++i) v[i] = oracle_uniform_f32(r[i]);
+}
+
 /* Standard deviation of q_k: eta * sigma (Sec. III-C, variance eta^2 N0/2 with
  * N0/2 = sigma^2 the channel variance), formed in double, rounded to FP32. */
 static float noise_scale_f32(float eta, float sigma) { return (float)((double)eta * (double)sigma); }
@@ -311,6 +354,24 @@ int32_t oracle_fix_code(float v, float R, int32_t kmax) {
 
 static inline int32_t fix_value(float v, float R, int32_t kmax) { return 2 * oracle_fix_code(v, R, kmax) + 1; }
 
+/* Rd = fl32(2^(Q+8) / Y_max): accumulator steps per unit of the FIXACC form. */
+float oracle_fixacc_scale(int32_t q_bits, float y_max) {
+    return (float)(ldexp(1.0, q_bits + ORC_ACC_BITS) / (double)y_max);
+}
+
+/* v in accumulator steps: the FP32 product v Rd rounded to the nearest integer (ties to even). */
+int32_t oracle_fixacc_steps(float v, float Rd) {
+    const float a = v * Rd;
+    return (int32_t)lrintf(a);
+}
+
+/* Whether the FIXACC integers stay far inside int32: |theta| Rd, w Rd 64 and the largest
+ * perturbation (8 scale) Rd below 2^28. */
+int oracle_fixacc_in_range(float theta, float w, float scale, float Rd) {
+    const double lim = ldexp(1.0, 28);
+    return fabs((double)theta) * Rd < lim && (double)w * Rd * 64.0 < lim && 8.0 * (double)scale * Rd < lim;
+}
+
 /* Adaptation events (theta~, tau~) of Sec. V-A: tau where g(theta lambda^u)
  * changes, for u = 0..t_max (Table II).  Returns the event count. */
 int32_t oracle_threshold_events(double theta, double lambda, int32_t t_max, int32_t q_bits,
@@ -381,18 +442,36 @@ typedef struct {
     const float* thr16;       /* [t_max + 1] binary16 thresholds */
     float fix_R;              /* fixed-point scale and limits */
     int32_t fix_kmax, fix_W;
-    const int32_t* thr_fix;   /* [t_max + 1] Theta~(u) */
+    const int32_t* thr_fix;   /* [t_max + 1] Theta~(u) (FIX) or Theta(u) in steps (FIXACC) */
+    float acc_R;              /* FIXACC: Rd and the weight in steps */
+    int32_t acc_W;
+    double y_unit;            /* FIX / FIXACC: value of one half level, Y_max 2^-Q */
 } orc_ctx;
 
-/* Decodes one frame.  ws must hold 4n + m + 16 int32 words. */
+/* Correlation sum_k rint(x_k y~_k 2^32) of the objective trace (exact integer). */
+static int64_t trace_corr(const orc_ctx* X, const int8_t* x, const double* ys64, const int32_t* yfix, int32_t n) {
+    int64_t c = 0;
+    for (int32_t k = 0; k < n; ++k) {
+        const double yv = (X->precision == ORC_FIX || X->precision == ORC_FIXACC) ? (double)yfix[k] * X->y_unit
+                                                                                  : ys64[k];
+        c += (int64_t)llrint(ldexp((double)x[k] * yv, 32));
+    }
+    return c;
+}
+
+/* Decodes one frame.  ws must hold 4n + m + 16 int32 words.  tr_u / tr_c (or NULL):
+ * objective trace U(t), C(t) for t = 0 .. iters. */
 static void decode_frame(const orc_ctx* X, const float* y, uint64_t frame_id,
-                         uint8_t* bits, int32_t* iters, uint8_t* pass, int32_t* ws) {
+                         uint8_t* bits, int32_t* iters, uint8_t* pass, int32_t* ws,
+                         int32_t* tr_u, int64_t* tr_c) {
     const orc_code* C = X->C;
     const orc_params* P = X->P;
     const int32_t n = C->n, m = C->m, T = P->t_max;
     const int adapt = (P->variant & ORC_ADAPT) != 0;
     const int smooth = (P->variant & ORC_SMOOTH) != 0;
     const int single = (P->variant & ORC_SINGLE) != 0;
+    const int uniform = (P->variant & ORC_UNIFORM) != 0;
+    const int fixed = X->precision == ORC_FIX || X->precision == ORC_FIXACC;
     int8_t* x = (int8_t*)ws;                       /* n bytes */
     int8_t* s = (int8_t*)(ws + (n + 3) / 4);       /* m bytes */
     int32_t* u = ws + (n + 3) / 4 + (m + 3) / 4;   /* n */
@@ -410,7 +489,7 @@ static void decode_frame(const orc_ctx* X, const float* y, uint64_t frame_id,
         ys32[k] = v;
         ys64[k] = (double)v;
         x[k] = v >= 0.0f ? 1 : -1;
-        if (X->precision == ORC_FIX) {
+        if (fixed) {
             yfix[k] = fix_value(v, X->fix_R, X->fix_kmax);
             x[k] = yfix[k] > 0 ? 1 : -1;
         }
@@ -424,11 +503,17 @@ static void decode_frame(const orc_ctx* X, const float* y, uint64_t frame_id,
     for (int32_t t = 0; t <= T; ++t) {
         /* Step 1: syndromes and the stopping test. */
         int all_satisfied = 1;
+        int32_t unsat = 0;
         for (int32_t i = 0; i < m; ++i) {
             int prod = 1;
             for (int32_t e = C->row_ptr[i]; e < C->row_ptr[i + 1]; ++e) prod *= x[C->col_idx[e]];
             s[i] = (int8_t)prod;
-            if (prod < 0) all_satisfied = 0;
+            if (prod < 0) { all_satisfied = 0; ++unsat; }
+        }
+        /* objective trace: f(x(t)) = C(t) 2^-32 + m - 2 U(t) */
+        if (tr_u) {
+            tr_u[t] = unsat;
+            tr_c[t] = trace_corr(X, x, ys64, yfix, n);
         }
         if (all_satisfied) {
             pack_bits(x, n, bits);
@@ -453,7 +538,14 @@ static void decode_frame(const orc_ctx* X, const float* y, uint64_t frame_id,
             for (int32_t e = C->sym_ptr[k]; e < C->sym_ptr[k + 1]; ++e) S += s[C->chk_idx[e]];
             int flip;
             if (X->use_f64) {
-                if ((k & 3) == 0) oracle_gauss4_f64(X->seed, frame_id, (uint32_t)t, (uint32_t)(k >> 2), z64);
+                if ((k & 3) == 0) {
+                    if (uniform) {
+                        oracle_uniform4_f32(X->seed, frame_id, (uint32_t)t, (uint32_t)(k >> 2), z32);
+                        for (int i = 0; i < 4; ++i) z64[i] = (double)z32[i];
+                    } else {
+                        oracle_gauss4_f64(X->seed, frame_id, (uint32_t)t, (uint32_t)(k >> 2), z64);
+                    }
+                }
                 double q = X->scale64 * z64[k & 3];
                 double E = oracle_metric_f64(x[k], ys64[k], S, (double)P->w, q);
                 flip = E < X->thr64[u[k]];
@@ -463,7 +555,10 @@ static void decode_frame(const orc_ctx* X, const float* y, uint64_t frame_id,
                 if (X->q_in) {
                     q = X->q_in[(size_t)t * n + k];
                 } else {
-                    if ((k & 3) == 0) oracle_gauss4_f32(X->seed, frame_id, (uint32_t)t, (uint32_t)(k >> 2), z32);
+                    if ((k & 3) == 0) {
+                        if (uniform) oracle_uniform4_f32(X->seed, frame_id, (uint32_t)t, (uint32_t)(k >> 2), z32);
+                        else oracle_gauss4_f32(X->seed, frame_id, (uint32_t)t, (uint32_t)(k >> 2), z32);
+                    }
                     q = X->scale32 * z32[k & 3];
                 }
                 if (X->precision == ORC_FP16) {
@@ -475,6 +570,13 @@ static void decode_frame(const orc_ctx* X, const float* y, uint64_t frame_id,
                     const int32_t Eq = x[k] * yfix[k] + X->fix_W * S + fix_value(q, X->fix_R, X->fix_kmax);
                     flip = Eq < X->thr_fix[u[k]];
                     if (single && (best_k < 0 || Eq < best_fix)) { best_k = k; best_fix = Eq; }
+                } else if (X->precision == ORC_FIXACC) {
+                    /* the held Eq. 8 level in accumulator steps (2^8 per half level), the
+                     * weight, the perturbation and the threshold in the same steps: exact int32 */
+                    const int32_t Ea = x[k] * yfix[k] * (1 << ORC_ACC_BITS) + X->acc_W * S +
+                                       oracle_fixacc_steps(q, X->acc_R);
+                    flip = Ea < X->thr_fix[u[k]];
+                    if (single && (best_k < 0 || Ea < best_fix)) { best_k = k; best_fix = Ea; }
                 } else {
                     float E = oracle_metric_f32(x[k], ys32[k], S, P->w, q);
                     flip = E < X->thr32[u[k]];
@@ -505,6 +607,9 @@ typedef struct {
     uint8_t* bits;
     int32_t* iters;
     uint8_t* pass;
+    int64_t trace_frames;     /* frames 0 .. trace_frames-1 of the call are traced */
+    int32_t* tr_u;            /* [trace_frames][t_max + 1] */
+    int64_t* tr_c;
     int status;
 } orc_job;
 
@@ -514,9 +619,13 @@ static void* decode_worker(void* arg) {
     const int32_t n = C->n, nb = (C->n + 7) / 8;
     int32_t* ws = (int32_t*)malloc(sizeof(int32_t) * (size_t)(4 * n + C->m + 16));
     if (!ws) { J->status = -1; return NULL; }
-    for (int64_t f = J->f0; f < J->f1; ++f)
+    const int64_t tl = (int64_t)J->X->P->t_max + 1;
+    for (int64_t f = J->f0; f < J->f1; ++f) {
+        const int traced = f < J->trace_frames;
         decode_frame(J->X, J->y + f * (int64_t)n, J->frame_offset + (uint64_t)f,
-                     J->bits + f * (int64_t)nb, J->iters + f, J->pass + f, ws);
+                     J->bits + f * (int64_t)nb, J->iters + f, J->pass + f, ws,
+                     traced ? J->tr_u + f * tl : NULL, traced ? J->tr_c + f * tl : NULL);
+    }
     free(ws);
     J->status = 0;
     return NULL;
@@ -529,9 +638,11 @@ static int check_args(int32_t n, int32_t m, const int32_t* row_ptr, const int32_
     for (int32_t i = 0; i < m; ++i) if (row_ptr[i + 1] < row_ptr[i]) return -1;
     for (int32_t e = 0; e < row_ptr[m]; ++e) if (col_idx[e] < 0 || col_idx[e] >= n) return -1;
     if (P->t_max < 0 || P->smooth_window < 0) return -1;
-    if (P->precision < ORC_FP32 || P->precision > ORC_FIX) return -1;
+    if (P->precision < ORC_FP32 || P->precision > ORC_FIXACC) return -1;
+    if (P->variant & ~(ORC_ADAPT | ORC_SMOOTH | ORC_SINGLE | ORC_UNIFORM)) return -1;
     if ((P->variant & ORC_SINGLE) && (P->variant & ORC_ADAPT)) return -1;
-    if (P->precision == ORC_FIX && (P->q_bits < 2 || P->q_bits > 8 || !(P->y_max > 0.0f) || !isfinite(P->y_max)))
+    if ((P->precision == ORC_FIX || P->precision == ORC_FIXACC) &&
+        (P->q_bits < 2 || P->q_bits > 8 || !(P->y_max > 0.0f) || !isfinite(P->y_max)))
         return -1;
     return 0;
 }
@@ -539,8 +650,10 @@ static int check_args(int32_t n, int32_t m, const int32_t* row_ptr, const int32_
 static int run(int use_f64, int32_t n, int32_t m, const int32_t* row_ptr, const int32_t* col_idx,
                const float* y, int64_t n_frames, float sigma, const orc_params* P, uint64_t seed,
                uint64_t frame_offset, const float* q_in, uint8_t* bits, int32_t* iters,
-               uint8_t* pass, int32_t n_threads) {
+               uint8_t* pass, int32_t n_threads, int64_t trace_frames, int32_t* tr_u, int64_t* tr_c) {
     if (check_args(n, m, row_ptr, col_idx, P) != 0 || n_frames < 0) return -1;
+    /* the trace needs bounded samples: a finite saturation level below 2^30 */
+    if (trace_frames > 0 && (!tr_u || !tr_c || !(P->y_max > 0.0f) || !(P->y_max < 1073741824.0f))) return -1;
     if (n_frames == 0) return 0;
     orc_code C;
     if (code_init(&C, n, m, row_ptr, col_idx) != 0) { code_free(&C); return -1; }
@@ -554,20 +667,35 @@ static int run(int use_f64, int32_t n, int32_t m, const int32_t* row_ptr, const 
     X.precision = use_f64 ? ORC_FP32 : P->precision;
     X.w16 = oracle_round_half(P->w);
     X.fix_R = 0.0f; X.fix_kmax = 0; X.fix_W = 0;
-    if (X.precision == ORC_FIX) {
+    X.acc_R = 0.0f; X.acc_W = 0; X.y_unit = 0.0;
+    if (X.precision == ORC_FIX || X.precision == ORC_FIXACC) {
         X.fix_R = oracle_fix_scale(P->q_bits, P->y_max);
         X.fix_kmax = (1 << (P->q_bits - 1)) - 1;
         X.fix_W = fix_value(P->w, X.fix_R, X.fix_kmax);
+        X.y_unit = ldexp((double)P->y_max, -P->q_bits);
+    }
+    const int uniform = (P->variant & ORC_UNIFORM) != 0;
+    /* perturbation scale: eta sigma (Gaussian) or eta sigma sqrt 3 (uniform on (-1, 1)) */
+    const double scale_d = uniform ? ((double)P->eta * (double)sigma) * sqrt(3.0) : (double)P->eta * (double)sigma;
+    if (X.precision == ORC_FIXACC) {
+        X.acc_R = oracle_fixacc_scale(P->q_bits, P->y_max);
+        X.acc_W = oracle_fixacc_steps(P->w, X.acc_R);
+        if (!oracle_fixacc_in_range(P->theta, P->w, (float)scale_d, X.acc_R)) {
+            free(thr32); free(thr64); free(thr16); free(thr_fix);
+            code_free(&C);
+            return -1;
+        }
     }
     for (int32_t u = 0; u <= P->t_max; ++u) {
         thr16[u] = oracle_round_half(thr32[u]);
-        thr_fix[u] = X.precision == ORC_FIX ? fix_value(thr32[u], X.fix_R, X.fix_kmax) : 0;
+        thr_fix[u] = X.precision == ORC_FIX ? fix_value(thr32[u], X.fix_R, X.fix_kmax)
+                   : X.precision == ORC_FIXACC ? oracle_fixacc_steps(thr32[u], X.acc_R) : 0;
     }
     X.thr16 = thr16;
     X.thr_fix = thr_fix;
     X.C = &C; X.P = P; X.use_f64 = use_f64;
-    X.scale32 = noise_scale_f32(P->eta, sigma);
-    X.scale64 = (double)P->eta * (double)sigma;
+    X.scale32 = (float)scale_d;
+    X.scale64 = scale_d;
     X.thr32 = thr32; X.thr64 = thr64; X.seed = seed; X.q_in = q_in;
     if (n_threads <= 0) n_threads = 1;
     if (n_threads > 512) n_threads = 512;
@@ -579,6 +707,7 @@ static int run(int use_f64, int32_t n, int32_t m, const int32_t* row_ptr, const 
         jobs[i].f0 = n_frames * i / n_threads; jobs[i].f1 = n_frames * (i + 1) / n_threads;
         jobs[i].frame_offset = frame_offset;
         jobs[i].bits = bits; jobs[i].iters = iters; jobs[i].pass = pass; jobs[i].status = 0;
+        jobs[i].trace_frames = trace_frames; jobs[i].tr_u = tr_u; jobs[i].tr_c = tr_c;
     }
     for (int32_t i = 1; i < n_threads; ++i) pthread_create(&th[i], NULL, decode_worker, &jobs[i]);
     decode_worker(&jobs[0]);
@@ -595,7 +724,18 @@ int oracle_decode_f32(int32_t n, int32_t m, const int32_t* row_ptr, const int32_
                       uint64_t seed, uint64_t frame_offset, uint8_t* bits, int32_t* iters,
                       uint8_t* pass, int32_t n_threads) {
     return run(0, n, m, row_ptr, col_idx, y, n_frames, sigma, P, seed, frame_offset, NULL,
-               bits, iters, pass, n_threads);
+               bits, iters, pass, n_threads, 0, NULL, NULL);
+}
+
+/* FP32 decoder with the objective trace of frames 0 .. trace_frames-1:
+ * tr_u / tr_c [trace_frames][t_max + 1], entries t = 0 .. iters[f] written. */
+int oracle_decode_f32_trace(int32_t n, int32_t m, const int32_t* row_ptr, const int32_t* col_idx,
+                            const float* y, int64_t n_frames, float sigma, const orc_params* P,
+                            uint64_t seed, uint64_t frame_offset, uint8_t* bits, int32_t* iters,
+                            uint8_t* pass, int32_t n_threads, int64_t trace_frames, int32_t* tr_u,
+                            int64_t* tr_c) {
+    return run(0, n, m, row_ptr, col_idx, y, n_frames, sigma, P, seed, frame_offset, NULL,
+               bits, iters, pass, n_threads, trace_frames, tr_u, tr_c);
 }
 
 /* FP64 decoder on the same Philox outputs: the statistical reference. */
@@ -604,12 +744,21 @@ int oracle_decode_f64(int32_t n, int32_t m, const int32_t* row_ptr, const int32_
                       uint64_t seed, uint64_t frame_offset, uint8_t* bits, int32_t* iters,
                       uint8_t* pass, int32_t n_threads) {
     return run(1, n, m, row_ptr, col_idx, y, n_frames, sigma, P, seed, frame_offset, NULL,
-               bits, iters, pass, n_threads);
+               bits, iters, pass, n_threads, 0, NULL, NULL);
+}
+
+int oracle_decode_f64_trace(int32_t n, int32_t m, const int32_t* row_ptr, const int32_t* col_idx,
+                            const float* y, int64_t n_frames, float sigma, const orc_params* P,
+                            uint64_t seed, uint64_t frame_offset, uint8_t* bits, int32_t* iters,
+                            uint8_t* pass, int32_t n_threads, int64_t trace_frames, int32_t* tr_u,
+                            int64_t* tr_c) {
+    return run(1, n, m, row_ptr, col_idx, y, n_frames, sigma, P, seed, frame_offset, NULL,
+               bits, iters, pass, n_threads, trace_frames, tr_u, tr_c);
 }
 
 /* FP32 decoder of ONE frame with the perturbations given: q[t][k], t < t_max. */
 int oracle_decode_f32_qin(int32_t n, int32_t m, const int32_t* row_ptr, const int32_t* col_idx,
                           const float* y, const orc_params* P, const float* q,
                           uint8_t* bits, int32_t* iters, uint8_t* pass) {
-    return run(0, n, m, row_ptr, col_idx, y, 1, 0.0f, P, 0, 0, q, bits, iters, pass, 1);
+    return run(0, n, m, row_ptr, col_idx, y, 1, 0.0f, P, 0, 0, q, bits, iters, pass, 1, 0, NULL, NULL);
 }

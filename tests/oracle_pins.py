@@ -670,6 +670,206 @@ def pin_precision_statistics(O):
         assert abs(res[prec][2].mean() - res[oracle_pkg.FP32][2].mean()) < 0.06
         assert (res[prec][1] == res[oracle_pkg.FP32][1]).mean() > 0.3
 
+
+# ---------------------------------------------------------------------------
+# uniform perturbation (Sec. V-B), accumulating fixed point, objective trace
+# ---------------------------------------------------------------------------
+
+def pin_uniform_deviate(O):
+    """v(r) = (2 (r >> 8) + 1 - 2^24) 2^-24: closed forms at the ends and the middle, odd multiples
+    of 2^-24, exact symmetry v(~r) = -v(r), and the uniform law on (-1, 1) with variance 1/3."""
+    from scipy import stats
+    two24 = 2.0 ** -24
+    for r, want in ((0, -1.0 + two24), (0xFFFFFFFF, 1.0 - two24), (0x80000000, two24),
+                    (0x7FFFFFFF, -two24), (0x800000FF, two24), (0x00000100, -1.0 + 3 * two24)):
+        assert float(O.uniform_f32(r)) == want, (hex(r), float(O.uniform_f32(r)), want)
+    rng = np.random.default_rng(31)
+    r = rng.integers(0, 2 ** 32, size=20000, dtype=np.uint64)
+    v = np.array([float(O.uniform_f32(int(x))) for x in r])
+    odd = v * 2 ** 24
+    assert (odd == np.round(odd)).all() and (np.mod(np.round(odd), 2) == 1).all()
+    assert all(float(O.uniform_f32(int(x) ^ 0xFFFFFFFF)) == -vv for x, vv in zip(r[:2000], v[:2000]))
+    assert stats.kstest(v, "uniform", args=(-1.0, 2.0)).pvalue > 1e-4
+    assert abs(v.mean()) < 0.02 and abs(v.var() - 1.0 / 3.0) < 0.01
+
+
+def pin_uniform4_wiring(O):
+    """Uniform deviate of symbol 4g + i = output i of Philox counter (g, t, frame_lo, frame_hi)."""
+    for seed, f, t, g in ((12345, 0, 0, 0), (7, 3, 299, 511), ((5 << 32) | 9, (2 << 32) | 1, 17, 3)):
+        r = O.philox([g, t, f & 0xFFFFFFFF, f >> 32], [seed & 0xFFFFFFFF, seed >> 32])
+        v = O.uniform4_f32(seed, f, t, g)
+        for i in range(4):
+            assert v[i] == O.uniform_f32(int(r[i]))
+
+
+def pin_uniform_noise_in_decoder(O):
+    """With the UNIFORM variant bit the FP32 decoder adds q_k = fl32(eta sigma sqrt 3) v_k each
+    iteration (variance eta^2 sigma^2, the Gaussian's), with v_k from the same Philox counter."""
+    C = _pin_code()
+    y, _, sig = wl.frames(C, 6, 1.0, seed=13)
+    eta = 0.96
+    scale = np.float32(float(np.float32(eta)) * float(np.float32(sig)) * math.sqrt(3.0))
+    assert abs(float(scale) / math.sqrt(3.0) - eta * sig) < 1e-6
+    for variant in (oracle_pkg.UNIFORM, oracle_pkg.UNIFORM | 3):
+        p = oracle_pkg.make_params(w=0.75, theta=-0.9, eta=eta, lam=0.97, t_max=25, smooth_window=9,
+                                   variant=variant)
+        b2, it2, ps2 = O.decode_f32(C, y, sig, p, seed=5, frame_offset=40)
+        for f in range(6):
+            v = np.array([np.concatenate([O.uniform4_f32(5, 40 + f, t, g) for g in range(C.n // 4)])
+                          for t in range(25)], np.float32)
+            q = (scale * v).astype(np.float32)
+            b1, it1, ps1 = O.decode_f32_qin(C, y[f], p, q)
+            assert (b1 == b2[f]).all() and it1 == it2[f] and ps1 == ps2[f], f"frame {f}"
+        # the Gaussian decoder on the same frames takes other decisions (the bit is honoured)
+        pg = oracle_pkg.make_params(w=0.75, theta=-0.9, eta=eta, lam=0.97, t_max=25, smooth_window=9,
+                                    variant=variant & ~oracle_pkg.UNIFORM)
+        bg, itg, _ = O.decode_f32(C, y, sig, pg, seed=5, frame_offset=40)
+        assert not ((bg == b2).all() and (itg == it2).all())
+
+
+def pin_fixacc_scale_and_steps(O):
+    """Rd = fl32(2^(Q+8) / Y_max) and steps(v) = rint(fl32(v Rd)) (ties to even)."""
+    assert O.fixacc_scale(8, 2.5) == float(np.float32(65536 / 2.5))
+    assert O.fixacc_scale(4, 2.0) == 2048.0
+    R = O.fixacc_scale(8, 2.5)
+    assert O.fixacc_steps(0.75, R) == 19661          # 19660.8
+    assert O.fixacc_steps(-0.9, R) == -23593         # -23592.96
+    assert O.fixacc_steps(0.5 / 2048, 2048.0) == 0   # 0.5 ties to even
+    assert O.fixacc_steps(1.5 / 2048, 2048.0) == 2   # 1.5 ties to even
+    assert O.fixacc_steps(-0.0003, 2048.0) == -1     # -0.6144
+
+
+def pin_trace_fixacc(O):
+    """Case K (Q = 4, Y_max = 2: Rd = 2048 steps per unit, 256 per half level of Delta/2 = 1/8):
+    y = (3,3,3,-3,3,3,3) holds level codes (7,7,7,-8,7,7,7), i.e. +-15 half levels = +-3840 steps;
+    w = 0.875 -> W = 1792; theta = -0.375 -> Theta = -768.  t = 0: s = (-1,-1,-1), E_3 =
+    3840 - 3 * 1792 = -1536 < -768 flips x_3; E_0,1,2 = 3840 - 3584 = 256 and E_4,5,6 = 2048 do not;
+    t = 1 is valid.  theta = -0.75 (Theta = -1536) makes E_3 a tie: nothing flips (T reached); an
+    injected q_3(0) = -0.0003 (-1 step) breaks the tie and x_3 flips, q_3(0) = +0.3 (614 steps) does not."""
+    C = hamming_code()
+    y = np.array([3, 3, 3, -3, 3, 3, 3], np.float32)
+
+    def run(theta, q3=None):
+        p = oracle_pkg.make_params(w=0.875, theta=theta, eta=0.0, lam=1.0, y_max=2.0, t_max=6,
+                                   precision=oracle_pkg.FIXACC, q_bits=4)
+        if q3 is None:
+            bits, it, ps = O.decode_f32(C, y[None, :], 0.5, p, seed=1)
+            return int(bits[0, 0]), int(it[0]), int(ps[0])
+        q = np.zeros((6, 7), np.float32)
+        q[0, 3] = q3
+        bits, it, ps = O.decode_f32_qin(C, y, p, q)
+        return _bits_byte(bits), it, ps
+    assert run(-0.375) == (0, 1, 1)
+    assert run(-0.75) == (0x08, 6, 0)
+    assert run(-0.75, -0.0003) == (0, 1, 1)
+    assert run(-0.75, 0.3) == (0x08, 6, 0)
+
+
+def _eq8_value(y, q_bits, y_max):
+    """g(y) of Eq. 8 with the saturating level index, in double (the level decided in FP32)."""
+    nq = 2 ** q_bits
+    a = np.abs(np.asarray(y, np.float32)) * np.float32(nq / (2.0 * y_max))
+    k = np.minimum(np.floor(a), nq // 2 - 1)
+    return np.where(np.asarray(y) >= 0, 1.0, -1.0) * (k + 0.5) * (2.0 * y_max / nq)
+
+
+def pin_fixacc_is_exact_on_its_grid(O):
+    """When w, theta and every perturbation are multiples of the accumulator step (Y_max = 2, Q = 8:
+    step 2^-15), the accumulating fixed point takes exactly the real-arithmetic decisions on the
+    quantized samples g(y): it equals the FP32 decoder fed g(y), whose sums are then exact."""
+    C = _pin_code()
+    y, _, sig = wl.frames(C, 8, 2.0, seed=24)
+    T = 30
+    rng = np.random.default_rng(25)
+    gy = _eq8_value(y, 8, 2.0).astype(np.float32)
+    for variant in (0, oracle_pkg.SMOOTH):
+        pacc = oracle_pkg.make_params(w=0.75, theta=-0.875, eta=0.0, lam=1.0, y_max=2.0, t_max=T,
+                                      smooth_window=8, variant=variant, precision=oracle_pkg.FIXACC, q_bits=8)
+        p32 = oracle_pkg.make_params(w=0.75, theta=-0.875, eta=0.0, lam=1.0, y_max=2.0, t_max=T,
+                                     smooth_window=8, variant=variant, precision=oracle_pkg.FP32)
+        passes = []
+        for f in range(y.shape[0]):
+            q = (np.round(rng.normal(0, 0.5, size=(T, C.n)) * 2 ** 15) / 2 ** 15).astype(np.float32)
+            a = O.decode_f32_qin(C, y[f], pacc, q)
+            b = O.decode_f32_qin(C, gy[f], p32, q)
+            assert (a[0] == b[0]).all() and a[1:] == b[1:], f"frame {f}"
+            passes.append(a[2])
+        assert 0 < sum(passes) < len(passes)
+
+
+def pin_fixacc_statistics(O):
+    """The 8-bit accumulating fixed point decodes the same frames almost always as FP32 does
+    (only the held sample is quantized; E keeps 2^-16 resolution relative to Y_max)."""
+    C = _pin_code()
+    y, _, sig = wl.frames(C, 300, 3.0, seed=23)
+    res = {}
+    for prec, qb in ((oracle_pkg.FP32, 0), (oracle_pkg.FIXACC, 8)):
+        p = oracle_pkg.make_params(w=0.75, theta=-0.9, eta=0.9, lam=0.95, t_max=50, variant=3,
+                                   precision=prec, q_bits=qb)
+        res[prec] = O.decode_f32(C, y, sig, p, seed=2)
+    assert abs(res[oracle_pkg.FIXACC][2].mean() - res[oracle_pkg.FP32][2].mean()) < 0.05
+    assert (res[oracle_pkg.FIXACC][1] == res[oracle_pkg.FP32][1]).mean() > 0.3
+
+
+def _dense_syndrome_weight(H, x):
+    return int(((H.astype(np.int64) @ (x < 0).astype(np.int64)) % 2).sum())
+
+
+def _corr_fixed(x, yv):
+    """sum_k rint(x_k y_k 2^32) in exact integers (numpy's rint: ties to even)."""
+    return int(np.rint(np.ldexp(x * np.asarray(yv, np.float64), 32)).astype(np.int64).sum())
+
+
+def pin_objective_trace(O):
+    """Objective trace f(x(t)) = C(t) 2^-32 + m - 2 U(t) (Sec. III-B objective):
+    - t = 0: x(0) = sign(y~), so U(0) is the syndrome weight of sign(y~) (dense H) and
+      C(0) = sum rint(|y~_k| 2^32), for FP32, FP64 and the Eq. 8 held samples;
+    - at t = iters of a passing frame, U = 0 and C is the correlation of the output word;
+    - entries after iters are not written;
+    - eta = 0, lambda = 1: the whole trace equals textbook M-GDBF's f(x(t)) evaluated densely."""
+    C = _pin_code()
+    H = C.dense()
+    y, _, sig = wl.frames(C, 24, 2.5, seed=26)
+    yc = np.clip(y, -2.5, 2.5)
+    T = 40
+    cases = [("f32", oracle_pkg.FP32, 0, yc), ("fix", oracle_pkg.FIX, 6, _eq8_value(yc, 6, 2.5)),
+             ("acc", oracle_pkg.FIXACC, 8, _eq8_value(yc, 8, 2.5))]
+    for name, prec, qb, held in cases:
+        p = oracle_pkg.make_params(w=0.75, theta=-0.9, eta=0.9, lam=0.97, y_max=2.5, t_max=T, variant=1,
+                                   precision=prec, q_bits=qb)
+        for arith in ("f32", "f64"):
+            if arith == "f64" and prec != oracle_pkg.FP32:
+                continue                      # the FP64 decoder holds unquantized samples
+            dec = O.decode_f64_trace if arith == "f64" else O.decode_f32_trace
+            bits, it, ps, tu, tc = dec(C, y, sig, p, 20, seed=3)
+            out = 1 - 2 * wl.unpack_bits(bits, C.n).astype(np.int64)
+            for f in range(20):
+                x0 = np.where(held[f] >= 0, 1, -1)
+                assert tu[f, 0] == _dense_syndrome_weight(H, x0), (name, f)
+                assert tc[f, 0] == _corr_fixed(np.ones(C.n), np.abs(held[f])), (name, f)
+                assert (tu[f, it[f] + 1:] == -1).all() and (tc[f, it[f] + 1:] == 0).all()
+                assert (tu[f, :it[f] + 1] >= 0).all()
+                if ps[f]:
+                    assert tu[f, it[f]] == 0 and tc[f, it[f]] == _corr_fixed(out[f], held[f]), (name, f)
+                else:
+                    assert tu[f, it[f]] > 0 and tc[f, it[f]] == _corr_fixed(out[f], held[f]), (name, f)
+            assert (ps == 1).any() and (ps == 0).any() and (it > 2).any()
+    # eta = 0: dense M-GDBF objective trajectory
+    p = oracle_pkg.make_params(w=0.75, theta=-0.9, eta=0.0, lam=1.0, y_max=2.5, t_max=T, variant=0)
+    bits, it, ps, tu, tc = O.decode_f64_trace(C, y, sig, p, 24, seed=3)
+    Hi = H.astype(np.int64)
+    w, th = float(np.float32(0.75)), float(np.float32(-0.9))
+    for f in range(24):
+        x = np.where(yc[f] >= 0, 1, -1)
+        for t in range(it[f] + 1):
+            U = _dense_syndrome_weight(H, x)
+            assert tu[f, t] == U, (f, t)
+            assert abs(tc[f, t] * 2.0 ** -32 - float(x @ yc[f].astype(np.float64))) <= C.n * 2.0 ** -33
+            s = 1 - 2 * ((Hi @ (x < 0).astype(np.int64)) % 2)
+            E = x * yc[f].astype(np.float64) + w * (Hi.T @ s)
+            x = np.where(E < th, -x, x)
+
+
 ALL_PINS = [
     pin_philox_kat, pin_icdf_vs_library, pin_icdf_symmetry_and_range, pin_gauss_f64_vs_library,
     pin_gauss4_wiring, pin_gauss_statistics,
@@ -680,4 +880,6 @@ ALL_PINS = [
     pin_f32_matches_injected_noise, pin_frame_independence, pin_f32_f64_statistics,
     pin_round_half, pin_metric_f16, pin_metric_f32_f64, pin_fix_quantizer, pin_trace_fixed_point, pin_table2_fixed_point, pin_fp16_reduces_to_fp32,
     pin_fix_reduces_to_fp32, pin_precision_statistics,
+    pin_uniform_deviate, pin_uniform4_wiring, pin_uniform_noise_in_decoder, pin_fixacc_scale_and_steps,
+    pin_trace_fixacc, pin_fixacc_is_exact_on_its_grid, pin_fixacc_statistics, pin_objective_trace,
 ]

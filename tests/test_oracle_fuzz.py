@@ -1,8 +1,9 @@
 """Randomized cross-check of the reference decoder against a dense restatement of the method.
 
 For random small codes, samples and parameters (every variant: multi-bit with or without
-threshold adaptation and output smoothing, and the single-bit Step 3a) and every arithmetic
-(FP64, FP32, binary16, Q-bit fixed point of Eq. 8), the reference decoder must give exactly the
+threshold adaptation and output smoothing, and the single-bit Step 3a, with Gaussian or uniform
+perturbations) and every arithmetic (FP64, FP32, binary16, Q-bit fixed point of Eq. 8, and Q-bit
+held samples with the fine fixed-point accumulator), the reference decoder must give exactly the
 decisions, iteration counts and pass flags of a plain numpy decoder over the dense parity-check
 matrix (Sec. III-B Steps 1-4, Step 2 of Sec. III-C, Sec. III-D in the theta lambda^u form of
 Sec. V-A, Eq. 7 of Sec. III-E).  The numpy decoder takes from the reference decoder only what is
@@ -47,6 +48,7 @@ def dense_decode(O, H, y, w, theta, lam, eta, sigma, T, W, y_max, variant, seed,
     """One frame in the order of the paper's steps (flooding schedule)."""
     m, n = H.shape
     adapt, smooth, single = bool(variant & 1), bool(variant & 2), bool(variant & 4)
+    uniform = bool(variant & 8)
     v = y.astype(np.float32)
     if y_max > 0:
         v = np.clip(v, np.float32(-y_max), np.float32(y_max))
@@ -59,10 +61,13 @@ def dense_decode(O, H, y, w, theta, lam, eta, sigma, T, W, y_max, variant, seed,
     if prec == "f64":
         thr = np.array([float(np.float32(theta)) * math.pow(float(np.float32(lam)), k) for k in range(T + 1)])
         scale = float(np.float32(eta)) * float(np.float32(sigma))
+        if uniform:
+            scale *= math.sqrt(3.0)
         wd = float(np.float32(w))
     else:
         thr = O.threshold_table_f32(theta, lam, T)
-        scale = np.float32(float(np.float32(eta)) * float(np.float32(sigma)))
+        scale = float(np.float32(eta)) * float(np.float32(sigma))
+        scale = np.float32(scale * math.sqrt(3.0) if uniform else scale)
         wd = np.float32(w)
         if prec == "f16":
             thr, wd = f16(thr), f16(wd)
@@ -72,6 +77,13 @@ def dense_decode(O, H, y, w, theta, lam, eta, sigma, T, W, y_max, variant, seed,
             x = np.where(yq > 0, 1, -1).astype(np.int64)
             thr = fix_value(thr, R, kmax)
             wq = int(fix_value(wd, R, kmax))
+        if prec == "acc":
+            R, kmax = O.fix_scale(q_bits, y_max), 2 ** (q_bits - 1) - 1
+            Rd = np.float32(O.fixacc_scale(q_bits, y_max))
+            yq = fix_value(v, R, kmax)
+            x = np.where(yq > 0, 1, -1).astype(np.int64)
+            thr = np.rint(np.asarray(thr, np.float32) * Rd).astype(np.int64)
+            wq = int(np.rint(np.float32(wd) * Rd))
     t_smooth = max(0, T - W) if smooth else T + 1
     for t in range(T + 1):
         s = np.prod(np.where(H == 1, x[None, :], 1), axis=1)
@@ -82,17 +94,22 @@ def dense_decode(O, H, y, w, theta, lam, eta, sigma, T, W, y_max, variant, seed,
         if t == T:
             break
         S = H.T.astype(np.int64) @ s
+        if uniform:
+            zu = np.concatenate([O.uniform4_f32(seed, frame, t, g) for g in range((n + 3) // 4)])[:n]
         if prec == "f64":
-            z = np.concatenate([O.gauss4_f64(seed, frame, t, g) for g in range((n + 3) // 4)])[:n]
+            z = zu.astype(np.float64) if uniform else \
+                np.concatenate([O.gauss4_f64(seed, frame, t, g) for g in range((n + 3) // 4)])[:n]
             E = (x * ys + wd * S) + scale * z
         else:
-            z = np.concatenate([O.gauss4_f32(seed, frame, t, g) for g in range((n + 3) // 4)])[:n]
+            z = zu if uniform else np.concatenate([O.gauss4_f32(seed, frame, t, g) for g in range((n + 3) // 4)])[:n]
             q = (scale * z).astype(np.float32)
             xy = np.where(x > 0, v, -v).astype(np.float32)
             if prec == "f32":
                 E = (xy + wd * S.astype(np.float32)) + q
             elif prec == "f16":
                 E = f16(f16(xy + f16(wd * S.astype(np.float32))) + f16(q))
+            elif prec == "acc":
+                E = x * yq * 256 + wq * S + np.rint(q * Rd).astype(np.int64)
             else:
                 E = x * yq + wq * S + fix_value(q, R, kmax)
         if single:
@@ -113,14 +130,14 @@ def dense_decode(O, H, y, w, theta, lam, eta, sigma, T, W, y_max, variant, seed,
        code_seed=st.integers(1, 3), frames=st.integers(1, 4), data_seed=st.integers(0, 10 ** 6),
        w=st.floats(0.05, 1.5), theta=st.floats(-1.5, 0.0), eta=st.sampled_from([0.0, 0.3, 0.7, 1.0]),
        lam=st.sampled_from([1.0, 0.99, 0.9, 0.8]), T=st.integers(0, 30), W=st.integers(0, 40),
-       y_max=st.sampled_from([0.0, 0.8, 2.5]), variant=st.sampled_from([0, 1, 2, 3, 4, 6]),
+       y_max=st.sampled_from([0.0, 0.8, 2.5]), variant=st.sampled_from([0, 1, 2, 3, 4, 6, 8, 11, 12]),
        sigma=st.floats(0.3, 1.2), seed=st.integers(0, 2 ** 40), frame_offset=st.integers(0, 2 ** 33),
-       prec=st.sampled_from(["f64", "f32", "f16", "fix"]), q_bits=st.integers(2, 8))
+       prec=st.sampled_from(["f64", "f32", "f16", "fix", "acc"]), q_bits=st.integers(2, 8))
 def test_reference_decoder_equals_dense_restatement(n, dv, code_seed, frames, data_seed, w, theta, eta, lam,
                                                      T, W, y_max, variant, sigma, seed, frame_offset, prec,
                                                      q_bits):
     O = oracle.load()
-    if prec == "fix" and y_max == 0.0:
+    if prec in ("fix", "acc") and y_max == 0.0:
         y_max = 2.0                           # the fixed point needs a saturation level
     code = code_for(n, dv, code_seed)
     H = code.dense().astype(np.int64)
@@ -128,9 +145,10 @@ def test_reference_decoder_equals_dense_restatement(n, dv, code_seed, frames, da
     y = (rng.choice([-1.0, 1.0], size=(frames, n)) + sigma * rng.standard_normal((frames, n))).astype(np.float32)
     if variant & 4:
         lam = 1.0                             # Step 3a has no adaptation
-    precision = {"f64": oracle.FP32, "f32": oracle.FP32, "f16": oracle.FP16, "fix": oracle.FIX}[prec]
+    precision = {"f64": oracle.FP32, "f32": oracle.FP32, "f16": oracle.FP16, "fix": oracle.FIX,
+                 "acc": oracle.FIXACC}[prec]
     p = oracle.make_params(w=w, theta=theta, eta=eta, lam=lam, y_max=y_max, t_max=T, smooth_window=W,
-                           variant=variant, precision=precision, q_bits=q_bits if prec == "fix" else 0)
+                           variant=variant, precision=precision, q_bits=q_bits if prec in ("fix", "acc") else 0)
     decode = O.decode_f64 if prec == "f64" else O.decode_f32
     bits, iters, ps = decode(code, y, sigma, p, seed=seed, frame_offset=frame_offset)
     got = wl.unpack_bits(bits, n)

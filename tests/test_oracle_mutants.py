@@ -80,6 +80,28 @@ MUTANTS = [
      "if (single && (best_k < 0 || E <= best32)) { best_k = k; best32 = E; }\n                }\n            }"),
     ("single-bit flips every symbol", "            if (single) continue;\n", ""),
     ("fix metric sign", "const int32_t Eq = x[k] * yfix[k] + X->fix_W * S", "const int32_t Eq = x[k] * yfix[k] - X->fix_W * S"),
+    ("uniform centre", "(int32_t)(2u * (r >> 8) + 1u) - (1 << 24)", "(int32_t)(2u * (r >> 8) + 1u) - (1 << 23)"),
+    ("uniform bits", "const int32_t odd = (int32_t)(2u * (r >> 8) + 1u)", "const int32_t odd = (int32_t)(2u * (r >> 9) + 1u)"),
+    ("uniform scale", "((double)P->eta * (double)sigma) * sqrt(3.0)", "((double)P->eta * (double)sigma) * sqrt(2.0)"),
+    ("uniform bit ignored", "if (uniform) oracle_uniform4_f32(X->seed, frame_id, (uint32_t)t, (uint32_t)(k >> 2), z32);",
+     "if (0) oracle_uniform4_f32(X->seed, frame_id, (uint32_t)t, (uint32_t)(k >> 2), z32);"),
+    ("uniform output order", "for (int i = 0; i < 4; ++i) v[i] = oracle_uniform_f32(r[i]);",
+     "for (int i = 0; i < 4; ++i) v[i] = oracle_uniform_f32(r[3 - i]);"),
+    ("fixacc step count", "ldexp(1.0, q_bits + ORC_ACC_BITS)", "ldexp(1.0, q_bits + ORC_ACC_BITS + 1)"),
+    ("fixacc held scale", "x[k] * yfix[k] * (1 << ORC_ACC_BITS)", "x[k] * yfix[k] * (1 << (ORC_ACC_BITS - 1))"),
+    ("fixacc truncates", "return (int32_t)lrintf(a);", "return (int32_t)a;"),
+    ("fixacc tie flips", "flip = Ea < X->thr_fix[u[k]];", "flip = Ea <= X->thr_fix[u[k]];"),
+    ("fixacc weight from levels", "X.acc_W = oracle_fixacc_steps(P->w, X.acc_R);",
+     "X.acc_W = X.fix_W * (1 << ORC_ACC_BITS);"),
+    ("fixacc threshold from levels", ": X.precision == ORC_FIXACC ? oracle_fixacc_steps(thr32[u], X.acc_R) : 0;",
+     ": X.precision == ORC_FIXACC ? fix_value(thr32[u], X.fix_R, X.fix_kmax) * (1 << ORC_ACC_BITS) : 0;"),
+    ("fixacc drops the perturbation", "X->acc_W * S +\n                                       oracle_fixacc_steps(q, X->acc_R);",
+     "X->acc_W * S;"),
+    ("trace counts satisfied checks", "tr_u[t] = unsat;", "tr_u[t] = m - unsat;"),
+    ("trace skips t = 0", "if (tr_u) {\n            tr_u[t]", "if (tr_u && t > 0) {\n            tr_u[t]"),
+    ("trace uses raw samples", "? (double)yfix[k] * X->y_unit", "? ys64[k]"),
+    ("trace unit", "llrint(ldexp((double)x[k] * yv, 32))", "llrint(ldexp((double)x[k] * yv, 31))"),
+    ("trace level value", "X.y_unit = ldexp((double)P->y_max, -P->q_bits);", "X.y_unit = ldexp((double)P->y_max, 1 - P->q_bits);"),
 ]
 
 RUNNER = r"""
