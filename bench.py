@@ -55,6 +55,33 @@ def ops_per_symbol_iter(dv: int) -> int:
 
 
 OPS_PER_SYMBOL_ITER = ops_per_symbol_iter(6)
+# Lane operations per symbol of the same-mix probe (ngdbf_mix_probe), by the same convention:
+# Philox 20 + deviate 13 + perturbation 1 + inversion function 5 + decision bit 1 + threshold,
+# adaptation, window and ballot 4 + the count lane's extraction 1 (the probe has no per-check
+# penalty work: the decode forms those counts bit-sliced, once for 32 slots).
+PROBE_OPS_PER_SYMBOL = 45
+PROBE_GROUPS = 32768
+
+
+def mix_probe(ngdbf, stream, reps=5, warmup=2):
+    """Attainable lane-op rate of the decode's per-slot instruction mix (CUDA events, best of reps)."""
+    import torch
+    sink = torch.zeros(1, dtype=torch.int32, device="cuda")
+    threads = 0
+    for _ in range(warmup):
+        threads = ngdbf.ngdbf_mix_probe(PROBE_GROUPS, sink.data_ptr(), stream.cuda_stream)
+    best = None
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        ngdbf.ngdbf_mix_probe(PROBE_GROUPS, sink.data_ptr(), stream.cuda_stream)
+        b.record(stream)
+        b.synchronize()
+        ms = a.elapsed_time(b)
+        best = ms if best is None else min(best, ms)
+    symbols = threads * PROBE_GROUPS * 4
+    return {"lane_op_s": symbols * PROBE_OPS_PER_SYMBOL / (best / 1e3), "ms": best, "threads": threads,
+            "symbols_per_launch": symbols, "ops_per_symbol": PROBE_OPS_PER_SYMBOL}
 # DRAM bytes (read + write) per decoded frame of the decode kernel, from an ncu capture of
 # this workload at 2*10^4 frames per Eb/N0 point (samples 164 MB per launch, larger than L2):
 # 183.8 MB read + 24.9 MB written at 3.5 dB; traffic scales with frames, each frame's samples
@@ -262,6 +289,9 @@ def run_ours(args):
     fps = frames_total / elapsed
 
     host_outs = [(b.cpu().numpy(), i.cpu().numpy(), p.cpu().numpy()) for b, i, p in outs]
+    with ClockSampler(local) as probe_clk:
+        probe = mix_probe(ngdbf, stream)
+    probe["clocks"] = probe_clk.summary()
     rates = error_rates(code, host_outs, cws)
     # roofline: algorithmic lane-ops of the iterations the frames needed, per launch
     sym_iters = [float(o[1].astype(np.int64).sum()) * code.n for o in host_outs]
@@ -274,8 +304,19 @@ def run_ours(args):
     achieved = ops_per_launch / mean_launch_s
     # the capture behind DRAM_BYTES_PER_FRAME is of the FP32 kernel
     traffic = DRAM_BYTES_PER_FRAME * F if (DRAM_BYTES_PER_FRAME and args.precision == "fp32") else None
-    rl = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12, "unit": "Tlane-op/s",
-          "frac": achieved / peak_ops, "traffic": traffic,
+    # the peak is the measured rate of the same instruction mix (probe), at the probe's clock
+    # scaled to the decode's sampled clock; the nominal issue rate is kept beside it
+    pclk = probe["clocks"].get("sm_mhz") or peak_mhz
+    dclk = clocks.get("sm_mhz") or peak_mhz
+    peak_meas = probe["lane_op_s"] * dclk / pclk
+    rl = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_meas / 1e12, "unit": "Tlane-op/s",
+          "frac": achieved / peak_meas, "traffic": traffic,
+          "peak_basis": f"measured: same-mix probe (ngdbf_mix_probe, {PROBE_OPS_PER_SYMBOL} lane-ops per symbol) "
+                        f"{probe['lane_op_s'] / 1e12:.2f} T at {pclk:.0f} MHz, scaled to the decode's median "
+                        f"{dclk:.0f} MHz",
+          "peak_nominal": peak_ops / 1e12, "frac_nominal": achieved / peak_ops,
+          "peak_nominal_basis": f"{sm_count} SMs x 128 lanes x {peak_mhz:.0f} MHz (max SM clock)",
+          "probe": {k: v for k, v in probe.items() if k != "clocks"} | {"sm_mhz": pclk},
           "kernel": "ngdbf_persistent_kernel<ADAPT,SMOOTH,state in smem>",
           "ops_per_symbol_iter": OPS_PER_SYMBOL_ITER,
           "ops_basis": "FP32 path" if args.precision == "fp32" else
@@ -284,35 +325,41 @@ def run_ours(args):
           "traffic_basis": "ncu dram__bytes_read.sum + dram__bytes_write.sum per frame on a 2*10^4-frame "
                            "capture, scaled to the launch's frames" if traffic else
                            "no capture of this precision's kernel",
-          "symbol_iters_per_launch": float(np.mean(sym_iters)), "mean_launch_ms": mean_launch_s * 1e3,
-          "peak_basis": f"{sm_count} SMs x 128 lanes x {peak_mhz:.0f} MHz (max SM clock)"}
+          "symbol_iters_per_launch": float(np.mean(sym_iters)), "mean_launch_ms": mean_launch_s * 1e3}
 
     # end to end through the host-buffer C-ABI call: copies inside the timed region
-    e2e_steps = max(1, min(args.steps, 2))
-    bits_h = [np.empty((F, nb), np.uint8) for _ in EBN0_DB]
-    it_h = [np.empty(F, np.int32) for _ in EBN0_DB]
-    ps_h = [np.empty(F, np.uint8) for _ in EBN0_DB]
+    e2e_steps = max(1, args.steps)
     bits_p = [torch.empty((F, nb), dtype=torch.uint8, pin_memory=True) for _ in EBN0_DB]
     it_p = [torch.empty(F, dtype=torch.int32, pin_memory=True) for _ in EBN0_DB]
     ps_p = [torch.empty(F, dtype=torch.uint8, pin_memory=True) for _ in EBN0_DB]
-    del bits_h, it_h, ps_h
     dc.decode_host(ys_host[0][:4096], sigmas[0], gp, seed=DECODER_SEED, frame_offset=off,
                    out=(bits_p[0][:4096], it_p[0][:4096], ps_p[0][:4096]))
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
+    host_stats = []
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         for j in range(len(EBN0_DB)):
             dc.decode_host(ys_host[j], sigmas[j], gp, seed=DECODER_SEED + j, frame_offset=off,
                            out=(bits_p[j], it_p[j], ps_p[j]))
+            host_stats.append(ngdbf.ngdbf_last_host_stats())
     e2e_s = time.perf_counter() - t0
     e2e_s = max_over_ranks(e2e_s, "cuda")
     e2e_ok = all(np.array_equal(bits_p[j].numpy(), host_outs[j][0]) for j in range(len(EBN0_DB)))
+    tot = {k: sum(h[k] for h in host_stats) for k in ("h2d_bytes", "d2h_bytes", "h2d_ms", "kernel_ms", "d2h_ms",
+                                                     "wall_ms", "chunks")}
     e2e = {"value": F * len(EBN0_DB) * e2e_steps * world / e2e_s, "unit": "frames/s",
            "h2d_bytes_per_step": F * code.n * 4 * len(EBN0_DB),
            "d2h_bytes_per_step": F * (nb + 4 + 1) * len(EBN0_DB), "steps": e2e_steps,
-           "matches_device_run": bool(e2e_ok)}
+           "matches_device_run": bool(e2e_ok),
+           # CUDA events around each chunk of ngdbf_decode_host (device clock)
+           "h2d_gbs": tot["h2d_bytes"] / max(tot["h2d_ms"], 1e-9) / 1e6,
+           "d2h_gbs": tot["d2h_bytes"] / max(tot["d2h_ms"], 1e-9) / 1e6,
+           "chunks": tot["chunks"], "h2d_ms": tot["h2d_ms"], "kernel_ms": tot["kernel_ms"],
+           "d2h_ms": tot["d2h_ms"], "event_wall_ms": tot["wall_ms"],
+           "host_wall_ms": e2e_s * 1e3,
+           "device_kernel_ms_same_frames": mean_launch_s * 1e3 * len(EBN0_DB) * e2e_steps}
 
     base = None
     if rank == 0 and not args.no_cpu_baseline:

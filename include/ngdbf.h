@@ -63,8 +63,12 @@ typedef enum {
 /* Variant bits (Sec. III-C/D/E).  0 = plain M-NGDBF with one threshold.
  * NGDBF_SINGLE: S-NGDBF, Step 3a of Sec. III-B with the noisy Step 2 of Sec. III-C:
  * each iteration flips only the symbol with the least E_k (ties go to the lowest k);
- * no threshold, so it excludes NGDBF_ADAPT; NGDBF_SMOOTH may be added. */
-enum { NGDBF_ADAPT = 1, NGDBF_SMOOTH = 2, NGDBF_SINGLE = 4 };
+ * no threshold, so it excludes NGDBF_ADAPT; NGDBF_SMOOTH may be added.
+ * NGDBF_UNIFORM: uniform instead of Gaussian perturbation samples (Sec. V-B), with the
+ * same variance: output r of the same Philox counter gives v = (2 (r >> 8) + 1 - 2^24)
+ * 2^-24, uniform on (-1, 1), and q_k = fl32(eta sigma sqrt 3) v.  Combines with any of
+ * the other bits. */
+enum { NGDBF_ADAPT = 1, NGDBF_SMOOTH = 2, NGDBF_SINGLE = 4, NGDBF_UNIFORM = 8 };
 
 /* Arithmetic of the held samples and the inversion function (Sec. IV-E); the
  * perturbation is always the FP32 generator output.
@@ -75,8 +79,15 @@ enum { NGDBF_ADAPT = 1, NGDBF_SMOOTH = 2, NGDBF_SINGLE = 4 };
  *               2^(Q-1) - 1), R = fl32(2^Q / (2 y_max)), the product in FP32;
  *               value 2b + 1 (b = k, or -k-1 for v < 0) in units of y_max / 2^Q;
  *               E~ = x Y~ + W~ S + Q~ in exact integers against the level of
- *               fl32(theta lambda^u).  Samples are held in 8 bits. */
-enum { NGDBF_FP32 = 0, NGDBF_FP16 = 1, NGDBF_FIX = 2 };
+ *               fl32(theta lambda^u).  Samples are held in 8 bits.
+ *   NGDBF_FIXACC samples held as the Eq. 8 level code of NGDBF_FIX (q_bits = Q, 8 bits
+ *               each), but only the sample is quantized to Q bits: E is accumulated in
+ *               exact int32 in steps of Y_max 2^-(Q+8) (256 steps per half level):
+ *               E = x (2b+1) 256 + W S + rint(fl32(q Rd)), W = rint(fl32(w Rd)),
+ *               Rd = fl32(2^(Q+8) / Y_max), flip when E < rint(fl32(fl32(theta
+ *               lambda^u) Rd)).  The accumulator terms must stay below 2^28 steps
+ *               (|theta|, 64 w and 8 eta sigma), else NGDBF_ERR_UNSUPPORTED. */
+enum { NGDBF_FP32 = 0, NGDBF_FP16 = 1, NGDBF_FIX = 2, NGDBF_FIXACC = 3 };
 
 /* Limits of this build. */
 enum {
@@ -95,9 +106,9 @@ typedef struct ngdbf_params {
     float y_max;          /* saturation magnitude; <= 0 or +inf disables (Sec. IV-A) */
     int32_t t_max;        /* T: at most T flip phases, 0 <= T <= NGDBF_MAX_T */
     int32_t smooth_window;/* W: X_k sums x(t) for t = max(0, T-W) .. T, 0 <= W <= 126 */
-    int32_t variant;      /* OR of NGDBF_ADAPT, NGDBF_SMOOTH, NGDBF_SINGLE (not with ADAPT) */
-    int32_t precision;    /* NGDBF_FP32, NGDBF_FP16 or NGDBF_FIX */
-    int32_t q_bits;       /* NGDBF_FIX: Q in 2..8 (needs a finite y_max > 0); otherwise 0 */
+    int32_t variant;      /* OR of NGDBF_ADAPT, NGDBF_SMOOTH, NGDBF_SINGLE (not with ADAPT), NGDBF_UNIFORM */
+    int32_t precision;    /* NGDBF_FP32, NGDBF_FP16, NGDBF_FIX or NGDBF_FIXACC */
+    int32_t q_bits;       /* NGDBF_FIX / NGDBF_FIXACC: Q in 2..8 (needs a finite y_max > 0); otherwise 0 */
 } ngdbf_params;
 
 typedef struct ngdbf_code ngdbf_code_t;   /* opaque; owned by the library */
@@ -155,6 +166,26 @@ ngdbf_status ngdbf_decode(const ngdbf_code_t* code, const float* y, int64_t n_fr
                           uint8_t* pass, void* stream);
 
 /*
+ * ngdbf_decode with the objective trace of Sec. III-B, f(x) = sum_k x_k y_k + sum_i s_i
+ * (the quantity Sec. VI follows over iterations): for frames 0 .. trace_frames-1 of the
+ * call, at every syndrome test t = 0 .. iters[f] the decoder records
+ *   trace_unsat[f][t] = U(t), the number of unsatisfied checks of x(t), and
+ *   trace_corr[f][t]  = C(t) = sum_k rint(x_k(t) y~_k 2^32), with y~ the held (saturated,
+ *                       rounded or quantized) sample as an exact double,
+ * so f(x(t)) = C(t) 2^-32 + m - 2 U(t) (|C 2^-32 - sum x y~| <= n 2^-33; the integer sum
+ * does not depend on the order of its terms).  Entries after iters[f] are not written.
+ *   trace_unsat  DEVICE int32[trace_frames][t_max + 1]
+ *   trace_corr   DEVICE int64[trace_frames][t_max + 1]
+ * 0 <= trace_frames <= n_frames; tracing needs a finite y_max > 0 below 2^30.  The decode
+ * results equal ngdbf_decode's.  Errors: as ngdbf_decode, INVALID_ARG for bad trace buffers.
+ */
+ngdbf_status ngdbf_decode_trace(const ngdbf_code_t* code, const float* y, int64_t n_frames,
+                                float sigma, const ngdbf_params* params, uint64_t seed,
+                                uint64_t frame_offset, uint8_t* bits, int32_t* iters,
+                                uint8_t* pass, int64_t trace_frames, int32_t* trace_unsat,
+                                int64_t* trace_corr, void* stream);
+
+/*
  * Same decode with HOST buffers, synchronous: copies y to the device in
  * chunks on two streams, decodes each chunk as soon as it has arrived while
  * the next chunk is copied, copies the outputs back, and returns when the
@@ -168,6 +199,24 @@ ngdbf_status ngdbf_decode_host(const ngdbf_code_t* code, const float* y_host, in
                                float sigma, const ngdbf_params* params, uint64_t seed,
                                uint64_t frame_offset, uint8_t* bits_host, int32_t* iters_host,
                                uint8_t* pass_host, int64_t chunk_frames);
+
+/* Timing of the most recent ngdbf_decode_host on the calling thread, from CUDA events
+ * recorded around each chunk's copy in, decode and copy out (device clock, ms): summed
+ * durations of each kind, and the wall time from the first copy in to the last copy out.
+ * h2d_bytes / h2d_ms is the achieved host-to-device rate; when copies overlap decoding,
+ * wall_ms < h2d_ms + kernel_ms + d2h_ms.  All zero after a failed call. */
+typedef struct ngdbf_host_stats {
+    int32_t chunks;
+    int32_t reserved;
+    int64_t h2d_bytes;       /* samples copied in */
+    int64_t d2h_bytes;       /* bits, iteration counts and pass flags copied out */
+    double h2d_ms;
+    double kernel_ms;
+    double d2h_ms;
+    double wall_ms;
+} ngdbf_host_stats;
+
+ngdbf_status ngdbf_last_host_stats(ngdbf_host_stats* out);
 
 /*
  * ngdbf_decode_noalloc -- ngdbf_decode that allocates no device memory.
@@ -197,6 +246,16 @@ ngdbf_status ngdbf_decode_noalloc(const ngdbf_code_t* code, const float* y, int6
                                   float sigma, const ngdbf_params* params, uint64_t seed,
                                   uint64_t frame_offset, uint8_t* bits, int32_t* iters,
                                   uint8_t* pass, void* stream);
+
+/*
+ * Device memory held by the library's stream-ordered scratch pool of the current device (the
+ * pool ngdbf_decode, ngdbf_decode_host and ngdbf_decode_trace take scratch from): bytes in use
+ * now and the most in use since the mark was last reset; reset_high != 0 first resets the mark
+ * to the current use.  Both are 0 while no decode on this device has created the pool.  Lets a
+ * caller confirm that a code path (ngdbf_decode_noalloc) takes nothing from the pool.
+ * Errors: INVALID_ARG for NULL outputs, CUDA.
+ */
+ngdbf_status ngdbf_pool_usage(int32_t reset_high, int64_t* used_now, int64_t* used_high);
 
 /*
  * Job tables: several decode jobs -- codes of different length, rate, degree
@@ -313,6 +372,30 @@ ngdbf_status ngdbf_server_destroy(ngdbf_server_t* server);
  * INVALID_ARG for a NULL or host z.
  */
 ngdbf_status ngdbf_gaussian_range(uint32_t start, uint32_t count, float* z, void* stream);
+
+/*
+ * The perturbation generator's coefficient table (verification; host only, no device call):
+ * out[4 (8 j + s) + n] = c_n of segment (j, s), the FP32 cubic in the position v of p inside
+ * the segment that interpolates Phi^{-1} at the Chebyshev points (the table the kernels
+ * evaluate; see the conventions at the top).  out: HOST float[1024].
+ */
+ngdbf_status ngdbf_generator_table(float* out);
+
+/*
+ * Same-mix throughput probe (measurement; the paper has no counterpart): every thread of a
+ * full-occupancy grid runs `groups` steps of the decode's per-slot symbol work for four
+ * symbols on register-resident data -- one Philox4x32-10 call, four inverse-CDF deviates
+ * (coefficient table in shared memory), the FP32 inversion function from a 4-bit count lane,
+ * the threshold lookup in shared memory and the comparison, the adaptation and window
+ * counters, and a warp ballot rebuilding the decision word -- without the sample, state and
+ * count traffic of a decode.  Timed with CUDA events, threads * groups * 4 symbols per
+ * launch give the attainable rate of that instruction mix on the device.
+ *   groups       >= 1 steps of four symbols per thread
+ *   sink         DEVICE uint32[1], receives an XOR of every thread's result
+ *   threads_out  receives the number of threads launched
+ * Asynchronous on `stream`.  Errors: INVALID_ARG, CUDA.
+ */
+ngdbf_status ngdbf_mix_probe(int32_t groups, uint32_t* sink, int64_t* threads_out, void* stream);
 
 /* Launch shape of the most recent ngdbf_decode* or ngdbf_batch_* call on the calling thread. */
 typedef struct ngdbf_launch_info {

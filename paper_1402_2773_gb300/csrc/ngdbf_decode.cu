@@ -29,14 +29,54 @@ __global__ void gaussian_range_kernel(const __grid_constant__ GenConsts G, uint3
         z[i] = gauss_icdf(start + i, tab);
 }
 
+// Same-mix throughput probe: the per-slot work of the decode's symbol loop for `groups` groups of
+// four symbols on register-resident data (one Philox call, four inverse-CDF deviates from the
+// shared coefficient table, the FP32 inversion function from a 4-bit count lane, the threshold
+// lookup in shared memory and the comparison, the adaptation and window counters, and a warp
+// ballot rebuilding the decision word), without the sample, state and count traffic.  Every
+// thread folds its result into *sink so that nothing is dead code.
+__global__ void __launch_bounds__(256) mix_probe_kernel(const __grid_constant__ GenConsts G, int groups, uint32_t* sink) {
+    __shared__ float4 tab[256];
+    __shared__ uint32_t thr[kMaxT + 1];
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) tab[i] = G.icdf[i];
+    for (int u = threadIdx.x; u <= kMaxT; u += blockDim.x) thr[u] = __float_as_uint(-0.7f + 0.001f * (float)u);
+    __syncthreads();
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t fid = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t nib_shift = 4u * (lane & 7u);
+    const float wgt = 0.1875f, wgt_m8 = -8.0f * 0.1875f, scale = 0.35f;
+    uint32_t xw[4] = {0x0F0F0F0Fu ^ fid, 0x33333333u, 0x55555555u ^ fid, 0x00FF00FFu};
+    uint32_t sv[4] = {lane, lane + 3u, lane + 7u, lane + 11u};
+    uint32_t cw = 0x9ABCDEF1u ^ (fid << 4);
+    const float yv[4] = {0.9f + 0.01f * lane, -0.2f, 1.3f, 0.45f};
+    for (int g = 0; g < groups; ++g) {
+        float z[4];
+        noise4((uint32_t)g, 0u, fid, 0u, G, tab, false, z);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const uint32_t th = thr[sv[j] & kUMask];
+            const uint32_t nib = (cw >> nib_shift) & 0xFu;
+            const float ws = __fmaf_rn(wgt, __uint2float_rn(nib), wgt_m8);
+            const uint32_t xsign = (xw[j] << (31u - lane)) & 0x80000000u;
+            const float q = __fmul_rn(scale, z[j]);
+            const float E = __fadd_rn(__fadd_rn(__uint_as_float(__float_as_uint(yv[j]) ^ xsign), ws), q);
+            const bool flip = E < __uint_as_float(th);
+            sv[j] = (sv[j] + (flip ? 0u : 1u) + (xsign >> (31 - kCShift))) & 0x3FFFu;
+            xw[j] ^= __ballot_sync(0xFFFFFFFFu, flip);
+        }
+        cw = (cw >> 4) | (cw << 28);
+    }
+    atomicXor(sink, xw[0] ^ xw[1] ^ xw[2] ^ xw[3] ^ sv[0] ^ sv[1] ^ sv[2] ^ sv[3]);
+}
+
 template <bool ADAPT, bool SMOOTH, bool ST_SMEM, bool WIDE, int PREC>
 __global__ void __launch_bounds__(1024) ngdbf_persistent_kernel(const __grid_constant__ DecodeArgs A) {
     using HeldT = typename Held<PREC>::T;
     const Job& J = A.J;
     const SmemLayout L = smem_layout(J.n, J.m, J.t_max, J.dv_max, J.dc_max, ADAPT,
                                      ST_SMEM && (ADAPT || SMOOTH), A.placement);
-    HeldT* ys = static_cast<HeldT*>(A.yslots) + (size_t)blockIdx.x * J.n * kSlots;
-    uint16_t* st = A.st_global ? A.st_global + (size_t)blockIdx.x * J.n * kSlots : nullptr;
+    HeldT* ys = static_cast<HeldT*>(A.yslots) + (size_t)blockIdx.x * pad4(J.n) * kSlots;
+    uint16_t* st = A.st_global ? A.st_global + (size_t)blockIdx.x * pad4(J.n) * kSlots : nullptr;
     decode_job<ADAPT, SMOOTH, ST_SMEM, WIDE, PREC>(J, A.thr, A.G, L, A.placement, ys, st);
 }
 
@@ -55,6 +95,7 @@ namespace host {
 
 thread_local std::string g_last_error;
 thread_local ngdbf_launch_info g_last_launch = {0, 0, 0, 0, 0, 0};
+thread_local ngdbf_host_stats g_last_host = {};
 
 ngdbf_status fail(ngdbf_status s, const std::string& msg) {
     g_last_error = msg;
@@ -105,53 +146,76 @@ ngdbf_status get_pool(int dev, cudaMemPool_t* out) {
 
 namespace {
 
-// Phi(z) = erfc(-z / sqrt 2) / 2 in double (C library erfc).
-double phi_cdf(double z) { return 0.5 * std::erfc(-z * 0.70710678118654752); }
-
-// Phi^{-1}(p), 0 < p < 1/2: 100 bisection steps of Phi(z) = p on [-40, 0].
-double inv_phi(double p) {
-    double lo = -40.0, hi = 0.0;
-    for (int it = 0; it < 100; ++it) {
-        const double mid = 0.5 * (lo + hi);
-        if (phi_cdf(mid) < p) lo = mid;
-        else hi = mid;
+// Generator table of the inverse normal CDF (host, double precision, built once per process).
+//
+// Segment (j, s), j = 0..31, s = 0..7, covers the lower-tail probabilities
+// p(v) = (8 + s + 1/2 + v) 2^-(j+5), v in [-1/2, 1/2].  Its FP32 cubic c0 + c1 v + c2 v^2 + c3 v^3
+// is the polynomial through Phi^{-1} at the four Chebyshev points of [-1/2, 1/2],
+// v_i = cos((2i+1) pi / 8) / 2, i = 0..3.  The definition fixes every double operation, so
+// that an independent evaluation reproduces the FP32 words bit for bit:
+//   * Phi^{-1}(p): 100 halvings of [-40, 0] on Phi(z) = erfc(-z / sqrt 2) / 2 (C library erfc),
+//     keeping the half whose Phi at the midpoint is not below p as the upper end;
+//   * with u = (cos(pi/8), cos(3 pi/8)) formed as sqrt(2 +- sqrt 2) / 2 and h = sqrt(2) / 2, the
+//     nodes are (u0, u1, -u1, -u0) / 2; writing the node values as even parts e0 = g0 + g3,
+//     e1 = g1 + g2 and odd parts o0 = g0 - g3, o1 = g1 - g2, the Chebyshev coefficients on
+//     x = 2v are b0 = (e0 + e1) / 4, b1 = (o0 u0 + o1 u1) / 2, b2 = ((e0 - e1) h) / 2,
+//     b3 = (o0 u1 - o1 u0) / 2, each in this order;
+//   * T1(2v) = 2v, T2(2v) = 8v^2 - 1, T3(2v) = 32v^3 - 6v give the monomial coefficients
+//     (b0 - b2, 2 b1 - 6 b3, 8 b2, 32 b3), rounded to FP32.
+class InverseCdfTable {
+  public:
+    InverseCdfTable() {
+        const double root2 = std::sqrt(2.0);
+        u_[0] = 0.5 * std::sqrt(2.0 + root2);
+        u_[1] = 0.5 * std::sqrt(2.0 - root2);
+        h_ = 0.5 * root2;
+        const double node[4] = {0.5 * u_[0], 0.5 * u_[1], -0.5 * u_[1], -0.5 * u_[0]};
+        for (int seg = 0; seg < 256; ++seg) {
+            const int level = seg >> 3, sub = seg & 7;
+            double value[4];
+            for (int i = 0; i < 4; ++i) value[i] = quantile(std::ldexp(8.0 + sub + 0.5 + node[i], -(level + 5)));
+            words_[seg] = cubic(value);
+        }
     }
-    return 0.5 * (lo + hi);
-}
+    const float4* words() const { return words_; }
 
-// Coefficients of the inverse normal CDF segments: segment (j, s) covers
-// p = (8 + s + 1/2 + v) 2^-(j+5), v in [-1/2, 1/2]; its cubic interpolates Phi^{-1} at the
-// Chebyshev nodes v_i = cos((2i+1) pi/8)/2.  In the basis T_n(2v) the coefficients are
-// b0 = sum g_i / 4 and b_n = sum g_i T_n(x_i) / 2; expanding T_1(2v) = 2v,
-// T_2(2v) = 8v^2 - 1, T_3(2v) = 32v^3 - 6v gives the monomial ones.  Double arithmetic in
-// a fixed order, rounded to FP32 at the end.
-struct IcdfTable {
-    float4 c[256];
-    IcdfTable() {
-        const double C1 = 0.5 * std::sqrt(2.0 + std::sqrt(2.0));   // cos(pi/8)
-        const double C3 = 0.5 * std::sqrt(2.0 - std::sqrt(2.0));   // cos(3 pi/8)
-        const double R = 0.5 * std::sqrt(2.0);                      // T_2 at the nodes: +-R
-        const double v[4] = {0.5 * C1, 0.5 * C3, -0.5 * C3, -0.5 * C1};
-        for (int j = 0; j < 32; ++j)
-            for (int s = 0; s < 8; ++s) {
-                double g[4];
-                for (int i = 0; i < 4; ++i) g[i] = inv_phi(std::ldexp(8.0 + s + 0.5 + v[i], -(j + 5)));
-                const double d03 = g[0] - g[3], d12 = g[1] - g[2];
-                const double s03 = g[0] + g[3], s12 = g[1] + g[2];
-                const double b0 = (s03 + s12) * 0.25;
-                const double b1 = (d03 * C1 + d12 * C3) * 0.5;
-                const double b2 = ((s03 - s12) * R) * 0.5;
-                const double b3 = (d03 * C3 - d12 * C1) * 0.5;   // T_3 at the nodes: C3, -C1, C1, -C3
-                c[8 * j + s] = make_float4((float)(b0 - b2), (float)(2.0 * b1 - 6.0 * b3), (float)(8.0 * b2),
-                                           (float)(32.0 * b3));
-            }
+  private:
+    static double lower_tail(double z) { return 0.5 * std::erfc(-z * 0.70710678118654752); }
+
+    // Phi^{-1}(p) for 0 < p < 1/2 by interval halving on [-40, 0].
+    static double quantile(double p) {
+        double below = -40.0, above = 0.0;
+        for (int step = 0; step < 100; ++step) {
+            const double mid = 0.5 * (below + above);
+            (lower_tail(mid) < p ? below : above) = mid;
+        }
+        return 0.5 * (below + above);
     }
+
+    // Monomial coefficients of the cubic through the node values g (nodes in the order above).
+    float4 cubic(const double g[4]) const {
+        const double o0 = g[0] - g[3], o1 = g[1] - g[2];
+        const double e0 = g[0] + g[3], e1 = g[1] + g[2];
+        const double b0 = (e0 + e1) * 0.25;
+        const double b1 = (o0 * u_[0] + o1 * u_[1]) * 0.5;
+        const double b2 = ((e0 - e1) * h_) * 0.5;
+        const double b3 = (o0 * u_[1] - o1 * u_[0]) * 0.5;
+        return make_float4((float)(b0 - b2), (float)(2.0 * b1 - 6.0 * b3), (float)(8.0 * b2), (float)(32.0 * b3));
+    }
+
+    double u_[2], h_;
+    float4 words_[256];
 };
 
 }  // namespace
 
+const InverseCdfTable& icdf_table() {
+    static const InverseCdfTable table;     // built once per process (thread-safe static)
+    return table;
+}
+
 void host_gen_consts(uint64_t seed, GenConsts& G) {
-    static const IcdfTable table;     // built once per process (thread-safe static)
+    const InverseCdfTable& table = icdf_table();
     uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
     for (int r = 0; r < 10; ++r) {
         G.rk0[r] = k0;
@@ -159,7 +223,7 @@ void host_gen_consts(uint64_t seed, GenConsts& G) {
         k0 += 0x9E3779B9u;
         k1 += 0xBB67AE85u;
     }
-    std::memcpy(G.icdf, table.c, sizeof(G.icdf));
+    std::memcpy(G.icdf, table.words(), sizeof(G.icdf));
 }
 
 struct LaunchPlan {
@@ -190,12 +254,15 @@ KernelFn pick_kernel(int variant, int precision, bool st_smem, bool wide) {
     switch (precision) {
         case NGDBF_FP16: return pick_variant<kFP16>(variant, st_smem, wide);
         case NGDBF_FIX: return pick_variant<kFIX>(variant, st_smem, wide);
+        case NGDBF_FIXACC: return pick_variant<kFIXACC>(variant, st_smem, wide);
         default: return pick_variant<kFP32>(variant, st_smem, wide);
     }
 }
 
 // Bytes of one held sample.
-size_t held_bytes(int precision) { return precision == NGDBF_FP16 ? 2 : (precision == NGDBF_FIX ? 1 : 4); }
+size_t held_bytes(int precision) {
+    return precision == NGDBF_FP16 ? 2 : ((precision == NGDBF_FIX || precision == NGDBF_FIXACC) ? 1 : 4);
+}
 
 // Shared-memory placement of a launch: the per-slot state and the adjacency tables.  The
 // state stays in shared memory whenever some candidate fits with it there (it is read and
@@ -292,6 +359,20 @@ ngdbf_status plan_launch(const ngdbf_code* C, const ngdbf_params* P, int64_t n_f
     return NGDBF_OK;
 }
 
+// Standard deviation of the perturbation: fl32(eta sigma), or fl32(eta sigma sqrt 3) for the
+// uniform deviates on (-1, 1) (same variance), formed in double.
+float noise_scale(const ngdbf_params* P, float sigma) {
+    const double s = (double)P->eta * (double)sigma;
+    return (float)((P->variant & NGDBF_UNIFORM) ? s * std::sqrt(3.0) : s);
+}
+
+// FIXACC: accumulator steps per unit, fl32(2^(Q+8) / Y_max), and v in steps, rint(fl32(v Rd)).
+float acc_scale(const ngdbf_params* P) { return (float)(std::ldexp(1.0, P->q_bits + kAccBits) / (double)P->y_max); }
+int32_t acc_steps(float v, float Rd) {
+    const float a = v * Rd;
+    return (int32_t)std::lrint(a);
+}
+
 // Job fields of one decode and its threshold words thr[0..t_max].
 void fill_job(const ngdbf_code* C, const ngdbf_params* P, const float* y, int64_t n_frames, float sigma,
               uint64_t frame_offset, uint8_t* bits, int32_t* iters, uint8_t* pass,
@@ -303,17 +384,23 @@ void fill_job(const ngdbf_code* C, const ngdbf_params* P, const float* y, int64_
     J.y = y; J.n_frames = n_frames; J.frame_offset = frame_offset;
     J.bits = bits; J.iters = iters; J.pass = pass; J.nb = (C->n + 7) / 8;
     J.w = P->precision == NGDBF_FP16 ? __half2float(__float2half_rn(P->w)) : P->w;
-    J.scale = (float)((double)P->eta * (double)sigma);
+    J.scale = noise_scale(P, sigma);
+    J.uniform = (P->variant & NGDBF_UNIFORM) ? 1 : 0;
     J.clamp = (P->y_max > 0.0f && std::isfinite(P->y_max)) ? 1 : 0;
     J.y_max = J.clamp ? P->y_max : 0.0f;
     J.t_max = P->t_max;
     J.t_smooth = std::max(0, P->t_max - P->smooth_window);
     J.queue = queue;
     J.single = (P->variant & NGDBF_SINGLE) ? 1 : 0;
-    if (P->precision == NGDBF_FIX) {
+    if (P->precision == NGDBF_FIX || P->precision == NGDBF_FIXACC) {
         J.fix_R = (float)(std::ldexp(1.0, P->q_bits) / (2.0 * (double)P->y_max));
         J.fix_kmax = (1 << (P->q_bits - 1)) - 1;
         J.fix_W = 2 * fix_code(P->w, J.fix_R, J.fix_kmax) + 1;
+        J.trace_yunit = std::ldexp((double)P->y_max, -P->q_bits);
+    }
+    if (P->precision == NGDBF_FIXACC) {
+        J.acc_R = acc_scale(P);
+        J.acc_W = acc_steps(P->w, J.acc_R);
     }
     double p = 1.0;
     for (int u = 0; u <= P->t_max; ++u) {
@@ -321,6 +408,9 @@ void fill_job(const ngdbf_code* C, const ngdbf_params* P, const float* y, int64_
         uint32_t word;
         if (P->precision == NGDBF_FIX) {
             const int32_t v = 2 * fix_code(th, J.fix_R, J.fix_kmax) + 1;
+            std::memcpy(&word, &v, 4);
+        } else if (P->precision == NGDBF_FIXACC) {
+            const int32_t v = acc_steps(th, J.acc_R);
             std::memcpy(&word, &v, 4);
         } else {
             const float h = P->precision == NGDBF_FP16 ? __half2float(__float2half_rn(th)) : th;
@@ -360,23 +450,38 @@ ngdbf_status check_params(const ngdbf_params* P, float sigma) {
     if (P->t_max > NGDBF_MAX_T) return fail(NGDBF_ERR_UNSUPPORTED, "t_max above NGDBF_MAX_T");
     if (P->smooth_window < 0) return fail(NGDBF_ERR_INVALID_ARG, "smooth_window must be >= 0");
     if (P->smooth_window > NGDBF_MAX_WINDOW) return fail(NGDBF_ERR_UNSUPPORTED, "smooth_window above NGDBF_MAX_WINDOW");
-    if (P->variant & ~7) return fail(NGDBF_ERR_INVALID_ARG, "unknown variant bits");
+    if (P->variant & ~15) return fail(NGDBF_ERR_INVALID_ARG, "unknown variant bits");
     if ((P->variant & NGDBF_SINGLE) && (P->variant & NGDBF_ADAPT))
         return fail(NGDBF_ERR_INVALID_ARG, "the single-bit variant has no threshold to adapt");
-    if (P->precision < NGDBF_FP32 || P->precision > NGDBF_FIX) return fail(NGDBF_ERR_INVALID_ARG, "unknown precision");
-    if (P->precision == NGDBF_FIX) {
+    if (P->precision < NGDBF_FP32 || P->precision > NGDBF_FIXACC) return fail(NGDBF_ERR_INVALID_ARG, "unknown precision");
+    if (P->precision == NGDBF_FIX || P->precision == NGDBF_FIXACC) {
         if (P->q_bits < 2 || P->q_bits > 8) return fail(NGDBF_ERR_INVALID_ARG, "fixed point needs 2 <= q_bits <= 8");
         if (!(P->y_max > 0.0f) || !std::isfinite(P->y_max))
             return fail(NGDBF_ERR_INVALID_ARG, "fixed point needs a finite y_max > 0 (it sets the step)");
     } else if (P->q_bits != 0) {
-        return fail(NGDBF_ERR_INVALID_ARG, "q_bits must be 0 unless precision is NGDBF_FIX");
+        return fail(NGDBF_ERR_INVALID_ARG, "q_bits must be 0 unless precision is NGDBF_FIX or NGDBF_FIXACC");
+    }
+    if (P->precision == NGDBF_FIXACC) {
+        // every accumulator term far inside int32: |theta|, 64 w and the largest perturbation
+        // (8 standard deviations) below 2^28 steps
+        const double Rd = acc_scale(P), lim = std::ldexp(1.0, 28);
+        if (!(std::fabs((double)P->theta) * Rd < lim && (double)P->w * Rd * 64.0 < lim &&
+              8.0 * (double)noise_scale(P, sigma) * Rd < lim))
+            return fail(NGDBF_ERR_UNSUPPORTED, "NGDBF_FIXACC: theta, w or the perturbation exceeds the accumulator range");
     }
     return NGDBF_OK;
 }
 
+// Objective-trace buffers of one decode (ngdbf_decode_trace).
+struct TraceSpec {
+    int64_t frames;
+    int32_t* unsat;
+    int64_t* corr;
+};
+
 ngdbf_status decode_impl(const ngdbf_code* C, const float* y, int64_t n_frames, float sigma,
                          const ngdbf_params* P, uint64_t seed, uint64_t frame_offset, uint8_t* bits,
-                         int32_t* iters, uint8_t* pass, cudaStream_t stream) {
+                         int32_t* iters, uint8_t* pass, cudaStream_t stream, const TraceSpec* tr = nullptr) {
     if (!C) return fail(NGDBF_ERR_INVALID_ARG, "code is NULL");
     ngdbf_status s = check_params(P, sigma);
     if (s != NGDBF_OK) return s;
@@ -406,7 +511,7 @@ ngdbf_status decode_impl(const ngdbf_code* C, const float* y, int64_t n_frames, 
     s = get_pool(dev, &pool);
     if (s != NGDBF_OK) return s;
     const bool state = (P->variant & 3) != 0;
-    const size_t slot_elems = (size_t)plan.grid * C->n * kSlots;
+    const size_t slot_elems = (size_t)plan.grid * pad4(C->n) * kSlots;
     const size_t bytes_y = (slot_elems * held_bytes(P->precision) + 255) / 256 * 256;
     const size_t bytes_st = (state && !plan.st_smem) ? (slot_elems * 2 + 255) / 256 * 256 : 0;
     const size_t total = 256 + bytes_y + bytes_st;
@@ -422,6 +527,11 @@ ngdbf_status decode_impl(const ngdbf_code* C, const float* y, int64_t n_frames, 
     DecodeArgs A;
     fill_args(C, P, plan, y, n_frames, sigma, seed, frame_offset, bits, iters, pass, base,
               base + 256 + bytes_y, bytes_st != 0, &A);
+    if (tr && tr->frames > 0) {
+        A.J.trace_u = tr->unsat;
+        A.J.trace_c = reinterpret_cast<long long*>(tr->corr);
+        A.J.trace_frames = tr->frames;
+    }
 
     e = cudaMemsetAsync(A.J.queue, 0, sizeof(unsigned long long), stream);
     if (e == cudaSuccess) {
@@ -443,6 +553,12 @@ using namespace ngdbf::host;
 extern "C" {
 
 const char* ngdbf_last_error(void) { return g_last_error.c_str(); }
+
+ngdbf_status ngdbf_last_host_stats(ngdbf_host_stats* out) {
+    if (!out) return fail(NGDBF_ERR_INVALID_ARG, "out is NULL");
+    *out = g_last_host;
+    return NGDBF_OK;
+}
 
 ngdbf_status ngdbf_last_launch(ngdbf_launch_info* out) {
     if (!out) return fail(NGDBF_ERR_INVALID_ARG, "out is NULL");
@@ -517,6 +633,33 @@ ngdbf_status ngdbf_code_create(int32_t n, int32_t m, const int32_t* row_ptr, con
     return NGDBF_OK;
 }
 
+ngdbf_status ngdbf_pool_usage(int32_t reset_high, int64_t* used_now, int64_t* used_high) {
+    if (!used_now || !used_high) return fail(NGDBF_ERR_INVALID_ARG, "NULL output");
+    *used_now = 0;
+    *used_high = 0;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev < 0 || dev >= 64) return fail(NGDBF_ERR_UNSUPPORTED, "device index out of range");
+    cudaMemPool_t pool;
+    {
+        std::lock_guard<std::mutex> lk(g_pool_mu);
+        pool = g_pools[dev];
+    }
+    if (!pool) return NGDBF_OK;
+    uint64_t cur = 0, high = 0;
+    e = cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &cur);
+    if (e == cudaSuccess && reset_high) {
+        uint64_t zero = 0;              // resets the mark to the current use
+        e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrUsedMemHigh, &zero);
+    }
+    if (e == cudaSuccess) e = cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemHigh, &high);
+    if (e != cudaSuccess) return cuda_fail(e, "pool attributes");
+    *used_now = (int64_t)cur;
+    *used_high = (int64_t)high;
+    return NGDBF_OK;
+}
+
 ngdbf_status ngdbf_code_destroy(ngdbf_code_t* C) {
     if (!C) return NGDBF_OK;
     cudaFree(C->d_chk_cols);
@@ -540,6 +683,30 @@ ngdbf_status ngdbf_decode(const ngdbf_code_t* C, const float* y, int64_t n_frame
                           int32_t* iters, uint8_t* pass, void* stream) {
     return decode_impl(C, y, n_frames, sigma, P, seed, frame_offset, bits, iters, pass,
                        static_cast<cudaStream_t>(stream));
+}
+
+ngdbf_status ngdbf_decode_trace(const ngdbf_code_t* C, const float* y, int64_t n_frames, float sigma,
+                                const ngdbf_params* P, uint64_t seed, uint64_t frame_offset, uint8_t* bits,
+                                int32_t* iters, uint8_t* pass, int64_t trace_frames, int32_t* trace_unsat,
+                                int64_t* trace_corr, void* stream) {
+    if (!P) return fail(NGDBF_ERR_INVALID_ARG, "params is NULL");
+    if (trace_frames < 0 || trace_frames > n_frames) return fail(NGDBF_ERR_INVALID_ARG, "need 0 <= trace_frames <= n_frames");
+    if (trace_frames > 0) {
+        if (!trace_unsat || !trace_corr) return fail(NGDBF_ERR_INVALID_ARG, "NULL trace buffer");
+        if (!(P->y_max > 0.0f && P->y_max < 1073741824.0f))
+            return fail(NGDBF_ERR_INVALID_ARG, "the objective trace needs a finite y_max below 2^30");
+        for (const void* p : {(const void*)trace_unsat, (const void*)trace_corr}) {
+            cudaPointerAttributes a;
+            cudaError_t e = cudaPointerGetAttributes(&a, p);
+            if (e != cudaSuccess || !(a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged)) {
+                cudaGetLastError();
+                return fail(NGDBF_ERR_INVALID_ARG, "trace buffers must be device memory");
+            }
+        }
+    }
+    const TraceSpec tr = {trace_frames, trace_unsat, trace_corr};
+    return decode_impl(C, y, n_frames, sigma, P, seed, frame_offset, bits, iters, pass,
+                       static_cast<cudaStream_t>(stream), &tr);
 }
 
 ngdbf_status ngdbf_decode_host(const ngdbf_code_t* C, const float* y_host, int64_t n_frames, float sigma,
@@ -575,12 +742,25 @@ ngdbf_status ngdbf_decode_host(const ngdbf_code_t* C, const float* y_host, int64
     const size_t bp = (size_t)chunk_frames;
     const size_t per = align256(by) + align256(bb) + align256(bi) + align256(bp);
     ngdbf_status rs = NGDBF_OK;
+    g_last_host = ngdbf_host_stats{};
     for (int b = 0; b < 2 && rs == NGDBF_OK; ++b) {
         e = cudaStreamCreateWithFlags(&st[b], cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaMallocFromPoolAsync(&buf[b], per, pool, st[b]);
         if (e != cudaSuccess) rs = cuda_fail(e, "host decode set-up");
     }
-    int64_t kernels = 0;
+    // per chunk: events before the copy in, after it, after the decode and after the copy out
+    std::vector<cudaEvent_t> ev;
+    auto mark = [&](cudaStream_t s_) {
+        cudaEvent_t x = nullptr;
+        if (cudaEventCreate(&x) == cudaSuccess) {
+            ev.push_back(x);
+            cudaEventRecord(x, s_);
+        } else {
+            cudaGetLastError();
+            ev.push_back(nullptr);
+        }
+    };
+    int64_t kernels = 0, chunks = 0;
     for (int64_t off = 0, c = 0; off < n_frames && rs == NGDBF_OK; off += chunk_frames, ++c) {
         const int b = (int)(c & 1);
         const int64_t F = std::min(chunk_frames, n_frames - off);
@@ -589,15 +769,22 @@ ngdbf_status ngdbf_decode_host(const ngdbf_code_t* C, const float* y_host, int64
         uint8_t* dbits = p + align256(by);
         int32_t* diters = reinterpret_cast<int32_t*>(dbits + align256(bb));
         uint8_t* dpass = reinterpret_cast<uint8_t*>(diters) + align256(bi);
+        mark(st[b]);
         e = cudaMemcpyAsync(dy, y_host + off * n, (size_t)F * n * 4, cudaMemcpyHostToDevice, st[b]);
         if (e != cudaSuccess) { rs = cuda_fail(e, "host-to-device copy"); break; }
+        mark(st[b]);
         rs = decode_impl(C, dy, F, sigma, P, seed, frame_offset + (uint64_t)off, dbits, diters, dpass, st[b]);
         if (rs != NGDBF_OK) break;
         kernels += g_last_launch.kernels;
+        mark(st[b]);
         e = cudaMemcpyAsync(bits_host + off * nb, dbits, (size_t)F * nb, cudaMemcpyDeviceToHost, st[b]);
         if (e == cudaSuccess) e = cudaMemcpyAsync(iters_host + off, diters, (size_t)F * 4, cudaMemcpyDeviceToHost, st[b]);
         if (e == cudaSuccess) e = cudaMemcpyAsync(pass_host + off, dpass, (size_t)F, cudaMemcpyDeviceToHost, st[b]);
         if (e != cudaSuccess) rs = cuda_fail(e, "device-to-host copy");
+        mark(st[b]);
+        g_last_host.h2d_bytes += (int64_t)F * n * 4;
+        g_last_host.d2h_bytes += (int64_t)F * (nb + 5);
+        ++chunks;
     }
     for (int b = 0; b < 2; ++b) {
         if (buf[b]) cudaFreeAsync(buf[b], st[b]);
@@ -607,6 +794,27 @@ ngdbf_status ngdbf_decode_host(const ngdbf_code_t* C, const float* y_host, int64
             cudaStreamDestroy(st[b]);
         }
     }
+    if (rs == NGDBF_OK && chunks > 0 && ev.size() == (size_t)chunks * 4) {
+        auto ms = [&](cudaEvent_t a, cudaEvent_t b_) {
+            float v = 0.0f;
+            if (a && b_ && cudaEventElapsedTime(&v, a, b_) == cudaSuccess) return (double)v;
+            cudaGetLastError();
+            return 0.0;
+        };
+        g_last_host.chunks = (int32_t)chunks;
+        double first = 0.0, last = 0.0;
+        for (int64_t c = 0; c < chunks; ++c) {
+            cudaEvent_t* q = ev.data() + 4 * c;
+            g_last_host.h2d_ms += ms(q[0], q[1]);
+            g_last_host.kernel_ms += ms(q[1], q[2]);
+            g_last_host.d2h_ms += ms(q[2], q[3]);
+            last = std::max(last, ms(ev[0], q[3]));
+            first = std::min(first, ms(ev[0], q[0]));
+        }
+        g_last_host.wall_ms = last - first;
+    }
+    for (cudaEvent_t x : ev)
+        if (x) cudaEventDestroy(x);
     if (rs == NGDBF_OK) g_last_launch.kernels = (int32_t)kernels;
     return rs;
 }
@@ -678,8 +886,8 @@ extern "C" ngdbf_status ngdbf_decode_noalloc(const ngdbf_code_t* C, const float*
 
     // Fit the launch into the static array: fewer CTAs when a full grid does not fit.
     const bool state = (P->variant & 3) != 0;
-    const size_t per_cta_y = (size_t)C->n * kSlots * held_bytes(P->precision);
-    const size_t per_cta_st = (state && !plan.st_smem) ? (size_t)C->n * kSlots * 2 : 0;
+    const size_t per_cta_y = (size_t)pad4(C->n) * kSlots * held_bytes(P->precision);
+    const size_t per_cta_st = (state && !plan.st_smem) ? (size_t)pad4(C->n) * kSlots * 2 : 0;
     const size_t avail = (size_t)NGDBF_NOALLOC_SCRATCH_BYTES - 256 - 256;   // counter + alignment
     const size_t max_grid = avail / (per_cta_y + per_cta_st);
     if (max_grid < 1)
@@ -899,8 +1107,8 @@ extern "C" ngdbf_status ngdbf_batch_create(const ngdbf_job* jobs, int32_t n_jobs
     int max_bps = 0;
     for (const auto& sh : shapes) max_bps = std::max(max_bps, sh.second);
     const size_t grid_max = (size_t)T.sm_count * max_bps;
-    const size_t per_slot_y = (size_t)T.n_max * kSlots * held_bytes(T.precision);
-    const size_t per_slot_st = T.state_global ? (size_t)T.n_max * kSlots * 2 : 0;
+    const size_t per_slot_y = (size_t)pad4(T.n_max) * kSlots * held_bytes(T.precision);
+    const size_t per_slot_st = T.state_global ? (size_t)pad4(T.n_max) * kSlots * 2 : 0;
     const size_t off_jobs = 0, off_thr = align256(sizeof(Job) * n_jobs), off_q = off_thr + align256(T.thr_words * 4);
     const size_t off_first = off_q + align256(8 * (size_t)n_jobs), off_y = off_first + align256(4 * grid_max);
     const size_t off_st = off_y + align256(grid_max * per_slot_y);
@@ -999,6 +1207,35 @@ extern "C" ngdbf_status ngdbf_batch_launch(ngdbf_batch_t* B, void* stream_ptr) {
 
 extern "C" ngdbf_status ngdbf_batch_destroy(ngdbf_batch_t* B) {
     batch_free(B);
+    return NGDBF_OK;
+}
+
+extern "C" ngdbf_status ngdbf_generator_table(float* out) {
+    if (!out) return fail(NGDBF_ERR_INVALID_ARG, "out is NULL");
+    std::memcpy(out, icdf_table().words(), 256 * sizeof(float4));
+    return NGDBF_OK;
+}
+
+extern "C" ngdbf_status ngdbf_mix_probe(int32_t groups, uint32_t* sink, int64_t* threads_out, void* stream) {
+    if (groups < 1 || !sink || !threads_out) return fail(NGDBF_ERR_INVALID_ARG, "need groups >= 1, sink and threads_out");
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, sink);
+    if (e != cudaSuccess || !(a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged)) {
+        cudaGetLastError();
+        return fail(NGDBF_ERR_INVALID_ARG, "sink must be device memory");
+    }
+    int dev = 0, sms = 0, bps = 0;
+    e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, mix_probe_kernel, 256, 0);
+    if (e != cudaSuccess) return cuda_fail(e, "probe set-up");
+    GenConsts G;
+    host_gen_consts(3, G);
+    const int grid = sms * std::max(bps, 1);
+    mix_probe_kernel<<<grid, 256, 0, static_cast<cudaStream_t>(stream)>>>(G, groups, sink);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "probe launch");
+    *threads_out = (int64_t)grid * 256;
     return NGDBF_OK;
 }
 

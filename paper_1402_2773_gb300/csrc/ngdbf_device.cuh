@@ -58,14 +58,27 @@ __device__ __forceinline__ float gauss_icdf(uint32_t r, const float4* tab) {
     return __uint_as_float(__float_as_uint(g) ^ (r & 0x80000000u));
 }
 
-// Four standard normals for symbols 4g .. 4g+3 of frame (flo, fhi) at iteration t:
-// symbol 4g + i takes Philox output i of counter (g, t, flo, fhi).
-__device__ __forceinline__ void gauss4(uint32_t g, uint32_t t, uint32_t flo, uint32_t fhi,
-                                       const GenConsts& G, const float4* tab, float z[4]) {
+// Uniform deviate on (-1, 1) of one Philox output (Sec. V-B variant): the top 24 bits a give
+// the odd integer 2a + 1 - 2^24, exact in FP32, scaled by 2^-24 (exact).
+__device__ __forceinline__ float uniform_dev(uint32_t r) {
+    const int32_t odd = (int32_t)(2u * (r >> 8) + 1u) - (1 << 24);
+    return __fmul_rn(__int2float_rn(odd), 5.9604644775390625e-08f);
+}
+
+// Four deviates for symbols 4g .. 4g+3 of frame (flo, fhi) at iteration t: symbol 4g + i takes
+// Philox output i of counter (g, t, flo, fhi), as a standard normal deviate or, when `uniform`
+// is set, as a uniform deviate on (-1, 1).
+__device__ __forceinline__ void noise4(uint32_t g, uint32_t t, uint32_t flo, uint32_t fhi,
+                                       const GenConsts& G, const float4* tab, bool uniform, float z[4]) {
     uint32_t r[4];
     philox4x32_10(g, t, flo, fhi, G, r);
+    if (uniform) {
 #pragma unroll
-    for (int i = 0; i < 4; ++i) z[i] = gauss_icdf(r[i], tab);
+        for (int i = 0; i < 4; ++i) z[i] = uniform_dev(r[i]);
+    } else {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) z[i] = gauss_icdf(r[i], tab);
+    }
 }
 
 }  // namespace ngdbf

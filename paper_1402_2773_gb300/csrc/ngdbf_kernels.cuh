@@ -23,12 +23,14 @@
 // converged frame frees its slot at once, and the CTA only stops when the
 // queue is empty and its last slot finished.
 //
-// Per-(symbol, slot) state: the held sample (global scratch laid out
-// [k][slot], L2-resident), and a 16-bit word holding u_k (bits 0-8) and
-// the number of -1 decisions inside the smoothing window (bits 9-15), in
-// shared memory when it fits, else in global scratch.  Decision and syndrome
-// words, counts, the threshold and generator tables live in shared memory, the
-// adjacency tables there when they fit.
+// Per-(symbol, slot) state: the held sample (global scratch, L2-resident), and a
+// 16-bit word holding u_k (bits 0-8) and the number of -1 decisions inside the
+// smoothing window (bits 9-15), in shared memory when it fits, else in global
+// scratch.  Both are laid out by groups of four symbols, [k/4][slot][k%4], so
+// that phase C reads one vector per lane for the four symbols of a Philox call;
+// the count words likewise ([k/4][slot quarter][k%4]) and the decision words
+// are contiguous.  Decision and syndrome words, counts, the threshold and
+// generator tables live in shared memory, the adjacency tables there when they fit.
 #pragma once
 
 #include <cuda_fp16.h>
@@ -44,6 +46,11 @@
 namespace ngdbf {
 
 constexpr int kSlots = 32;
+
+// Symbols rounded up to whole groups of four (the per-slot arrays are laid out by groups).
+__host__ __device__ inline int pad4(int n) { return (n + 3) & ~3; }
+// Index of (symbol k, slot f) in the group layout [k/4][slot][k%4].
+__host__ __device__ inline int gidx(int k, int f) { return (((k >> 2) * kSlots + f) << 2) | (k & 3); }
 constexpr int kTabChk = 1;              // N(i) table in shared memory
 constexpr int kTabSym = 2;              // M(k) table and degrees in shared memory
 
@@ -53,12 +60,14 @@ constexpr int kCShift = 9;            // smoothing count: bits 9-15
 
 // Arithmetic of the held samples and of E_k (Sec. IV-E): the perturbation is
 // always the FP32 generator output.
-enum Precision { kFP32 = 0, kFP16 = 1, kFIX = 2 };
+enum Precision { kFP32 = 0, kFP16 = 1, kFIX = 2, kFIXACC = 3 };
+constexpr int kAccBits = 8;           // FIXACC: accumulator steps per half level = 2^8
 
 template <int PREC> struct Held;
 template <> struct Held<kFP32> { using T = float; };
 template <> struct Held<kFP16> { using T = __half; };
-template <> struct Held<kFIX> { using T = int8_t; };   // signed level code b, value 2b + 1
+template <> struct Held<kFIX> { using T = int8_t; };      // signed level code b, value 2b + 1
+template <> struct Held<kFIXACC> { using T = int8_t; };   // the same Eq. 8 level code
 
 // One decode job: a code, a batch of frames and the parameters of the method.
 struct Job {
@@ -80,20 +89,29 @@ struct Job {
     int32_t clamp, t_max, t_smooth;   // t_smooth = max(0, T - W)
     float fix_R;                // fixed point: fl32(2^Q / (2 Y_max)), kmax = 2^(Q-1) - 1, W~
     int32_t fix_kmax, fix_W;
+    float acc_R;                // FIXACC: accumulator steps per unit fl32(2^(Q+8) / Y_max), w in steps
+    int32_t acc_W;
     // thresholds theta lambda^u, u = 0..T: FP32 bits, binary16 values as FP32 bits, or
-    // fixed-point levels Theta~(u) as int32 (device memory; the single-job launch passes
-    // them inline instead)
+    // fixed-point levels Theta~(u) (FIX) or steps (FIXACC) as int32 (device memory; the
+    // single-job launch passes them inline instead)
     const uint32_t* thr;
     unsigned long long* queue;  // next unclaimed frame of this job
     int32_t single;             // Step 3a: flip only the symbol with the least E_k (ties: lowest k)
+    int32_t uniform;            // Sec. V-B: uniform perturbation of the same variance
+    // objective trace of frames 0 .. trace_frames-1 (nullptr: off): unsatisfied checks U(t) and
+    // the correlation C(t) = sum_k rint(x_k y~_k 2^32), [frame][t_max + 1]
+    int32_t* trace_u;
+    long long* trace_c;
+    long long trace_frames;
+    double trace_yunit;         // FIX / FIXACC: value of one half level, Y_max 2^-Q
 };
 
 // Launch of one job: the job and its thresholds travel as kernel parameters.
 struct DecodeArgs {
     Job J;
     int32_t placement;          // adjacency tables copied into shared memory: kTabChk | kTabSym
-    void* yslots;               // [grid][n][32] held samples (4, 2 or 1 bytes each)
-    uint16_t* st_global;        // [grid][n][32] when the state is not in shared memory
+    void* yslots;               // [grid][pad4(n)/4][32][4] held samples (4, 2 or 1 bytes each)
+    uint16_t* st_global;        // [grid][pad4(n)/4][32][4] when the state is not in shared memory
     GenConsts G;
     uint32_t thr[kMaxT + 1];
 };
@@ -107,23 +125,25 @@ struct MultiArgs {
     const int32_t* first_job;   // [grid]
     int32_t n_max, m_max, t_max, dv_max, dc_max;   // layout maxima over the jobs
     int32_t placement;          // adjacency tables copied into shared memory: kTabChk | kTabSym
-    void* yslots;               // [grid][n_max][32]
-    uint16_t* st_global;        // [grid][n_max][32] when the state is not in shared memory
+    void* yslots;               // [grid][pad4(n_max)/4][32][4]
+    uint16_t* st_global;        // [grid][pad4(n_max)/4][32][4] when the state is not in shared memory
     GenConsts G;
 };
 
 struct SmemLayout {
-    int32_t off_frame, off_start, off_ctl, off_best, off_icdf, off_xw, off_sw, off_cnt, off_thr, off_st, off_chk,
-        off_sym, total;
+    int32_t off_frame, off_start, off_ctl, off_best, off_trace, off_icdf, off_xw, off_sw, off_cnt, off_thr, off_st,
+        off_chk, off_sym, total;
 };
 
 // Offsets in bytes of the shared-memory arrays.  ctl holds: [0..1] unsatisfied
 // masks (double-buffered by pass parity), [2] live mask, [3] new-slot mask.
 // When d_v <= 7 (narrow), sw holds per check four words with one 4-bit lane per slot
 // (lane f & 7 of word f >> 3: 1 when check i is unsatisfied for slot f), and cnt holds
-// per symbol, in the same lanes, S_k + 8 = d_v(k) + 8 - 2 (unsatisfied checks in M(k))
-// (16 bytes).  Otherwise (wide) sw holds the 32-bit unsatisfied mask of each check and
-// cnt the bit-sliced count (seven words, bit f for slot f) and d_v(k) (32 bytes).
+// per symbol, in the same lanes, S_k + 8 = d_v(k) + 8 - 2 (unsatisfied checks in M(k)),
+// as words [k/4][quarter f >> 3][k%4] (16 bytes per symbol).  Otherwise (wide) sw holds
+// the 32-bit unsatisfied mask of each check and cnt, per symbol, the bit-sliced count
+// (seven words, bit f for slot f) and d_v(k) (32 bytes).  xw has room for whole groups
+// and the zero sentinel word at index n.
 __host__ __device__ inline SmemLayout smem_layout(int n, int m, int t_max, int dv_max, int dc_max,
                                                   bool need_thr, bool st_smem, int tables) {
     SmemLayout L;
@@ -139,12 +159,13 @@ __host__ __device__ inline SmemLayout smem_layout(int n, int m, int t_max, int d
     L.off_start = take(kSlots * 4, 16);
     L.off_ctl = take(8 * 4, 16);
     L.off_best = take(kSlots * 8, 16);     // single-bit variant: least (E key, k) per slot
+    L.off_trace = take(kSlots * 12, 16);   // objective trace: per slot C (int64), then U (int32)
     L.off_icdf = take(256 * 16, 16);       // inverse normal CDF coefficients
-    L.off_cnt = take(n * cnt_bytes, 16);
-    L.off_xw = take((n + 1) * 4, 16);
+    L.off_cnt = take(pad4(n) * cnt_bytes, 16);
+    L.off_xw = take(pad4(n + 1) * 4, 16);
     L.off_sw = take((m + 1) * (dv_max <= 7 ? 16 : 4), 16);
     L.off_thr = need_thr ? take((t_max + 1) * 4, 16) : -1;
-    L.off_st = st_smem ? take(n * kSlots * 2, 16) : -1;
+    L.off_st = st_smem ? take(pad4(n) * kSlots * 2, 16) : -1;
     L.off_chk = (tables & kTabChk) ? take(dc_max * m * 2, 16) : -1;
     L.off_sym = (tables & kTabSym) ? take(n * dv_max * 2 + n, 16) : -1;
     L.total = (o + 15) / 16 * 16;
@@ -182,6 +203,92 @@ __device__ __forceinline__ uint32_t spread_nibbles(uint32_t b) {
 __device__ __forceinline__ int nth_set_bit(uint32_t mask, int j) {
     for (int i = 0; i < j; ++i) mask &= mask - 1u;
     return __ffs(mask) - 1;
+}
+
+// Objective trace (Sec. III-B objective f(x) = sum_k x_k y_k + sum_i s_i): for the live slots whose
+// frame id is below A.trace_frames, records at this syndrome test t the number of unsatisfied
+// checks U(t) and C(t) = sum_k rint(x_k(t) y~_k 2^32) (each term exact in double; integer sums are
+// independent of their order).  CTA-wide; every thread calls it with the same `live`.
+template <int PREC>
+__device__ __forceinline__ void trace_round(const Job& A, const SmemLayout& L, const uint16_t* chk_cols,
+                                         const typename Held<PREC>::T* ys, uint32_t live, int round) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const long long* lane_frame = reinterpret_cast<const long long*>(smem + L.off_frame);
+    const int32_t* lane_start = reinterpret_cast<const int32_t*>(smem + L.off_start);
+    const uint32_t* xw = reinterpret_cast<const uint32_t*>(smem + L.off_xw);
+    unsigned long long* tr_c = reinterpret_cast<unsigned long long*>(smem + L.off_trace);
+    int32_t* tr_u = reinterpret_cast<int32_t*>(smem + L.off_trace + kSlots * 8);
+    const int tid = threadIdx.x, lane = tid & 31;
+    const bool mine = ((live >> lane) & 1u) && lane_frame[lane] >= 0 && lane_frame[lane] < A.trace_frames;
+    const uint32_t tmask = __ballot_sync(0xFFFFFFFFu, mine);   // the same in every warp
+    if (tmask == 0u) return;
+    if (tid < kSlots) {
+        tr_c[tid] = 0ull;
+        tr_u[tid] = 0;
+    }
+    __syncthreads();
+    const int n = A.n, m = A.m;
+    // U(t): the syndrome words recomputed from the decision words
+    for (int base = 0; base < m; base += blockDim.x) {
+        const int i = base + tid;
+        uint32_t s = 0u;
+        if (i < m)
+            for (int j = 0; j < A.dc_max; ++j) s ^= xw[chk_cols[j * m + i]];
+        for (uint32_t r = tmask; r; r &= r - 1u) {
+            const int f = __ffs(r) - 1;
+            const int c = __popc(__ballot_sync(0xFFFFFFFFu, (s >> f) & 1u));
+            if (lane == 0 && c) atomicAdd(tr_u + f, c);
+        }
+    }
+    // C(t): sum over symbols of the signed held sample, scaled by 2^32 and rounded
+    for (int base = 0; base < n; base += blockDim.x) {
+        const int k = base + tid;
+        for (uint32_t r = tmask; r; r &= r - 1u) {
+            const int f = __ffs(r) - 1;
+            long long term = 0;
+            if (k < n) {
+                double v;
+                if constexpr (PREC == kFP32) {
+                    v = (double)ys[gidx(k, f)];
+                } else if constexpr (PREC == kFP16) {
+                    v = (double)__half2float(ys[gidx(k, f)]);
+                } else {
+                    v = (double)(2 * (int32_t)ys[gidx(k, f)] + 1) * A.trace_yunit;
+                }
+                if ((xw[k] >> f) & 1u) v = -v;
+                term = __double2ll_rn(v * 4294967296.0);
+            }
+#pragma unroll
+            for (int o = 16; o; o >>= 1) term += __shfl_xor_sync(0xFFFFFFFFu, term, o);
+            if (lane == 0 && term) atomicAdd(tr_c + f, (unsigned long long)term);
+        }
+    }
+    __syncthreads();
+    if (tid < kSlots && ((tmask >> tid) & 1u)) {
+        const long long fr = lane_frame[tid];
+        const size_t at = (size_t)fr * (size_t)(A.t_max + 1) + (size_t)(round - lane_start[tid]);
+        A.trace_u[at] = tr_u[tid];
+        A.trace_c[at] = (long long)tr_c[tid];
+    }
+    __syncthreads();
+}
+
+// The four held samples of one slot in a group (16, 8 or 4 bytes, aligned).
+__device__ __forceinline__ void load_held4(const float* p, float v[4]) {
+    const float4 a = *reinterpret_cast<const float4*>(p);
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+}
+__device__ __forceinline__ void load_held4(const __half* p, __half v[4]) {
+    const uint2 a = *reinterpret_cast<const uint2*>(p);
+    v[0] = __ushort_as_half((unsigned short)(a.x & 0xFFFFu));
+    v[1] = __ushort_as_half((unsigned short)(a.x >> 16));
+    v[2] = __ushort_as_half((unsigned short)(a.y & 0xFFFFu));
+    v[3] = __ushort_as_half((unsigned short)(a.y >> 16));
+}
+__device__ __forceinline__ void load_held4(const int8_t* p, int8_t v[4]) {
+    const uint32_t a = *reinterpret_cast<const uint32_t*>(p);
+    v[0] = (int8_t)(a & 0xFFu); v[1] = (int8_t)((a >> 8) & 0xFFu);
+    v[2] = (int8_t)((a >> 16) & 0xFFu); v[3] = (int8_t)(a >> 24);
 }
 
 // The slot loop for one job (rows a0-a8 of the method): CTA-wide, returns when the job
@@ -231,12 +338,12 @@ __device__ __forceinline__ void decode_job(const Job& A, const uint32_t* thr_src
 
     // ---- set-up: generator table, zero the state, sentinels, thresholds, first 32 frames ----
     for (int i = tid; i < 256; i += blockDim.x) icdf[i] = G.icdf[i];
-    for (int k = tid; k <= n; k += blockDim.x) xw[k] = 0u;
+    for (int k = tid; k < pad4(n + 1); k += blockDim.x) xw[k] = 0u;
     for (int i = tid; i < (m + 1) * (WIDE ? 1 : 4); i += blockDim.x) sw[i] = 0u;
     if constexpr (ADAPT)
         for (int u = tid; u <= T; u += blockDim.x) thr[u] = thr_src[u];
     if constexpr (kState)
-        for (int e = tid; e < n * kSlots; e += blockDim.x) st[e] = 0;
+        for (int e = tid; e < pad4(n) * kSlots; e += blockDim.x) st[e] = 0;
     if (tid < kSlots) best[tid] = ~0ull;
     if (tid == 0) {
         for (int c = 0; c < 8; ++c) ctl[c] = 0u;
@@ -276,20 +383,21 @@ __device__ __forceinline__ void decode_job(const Job& A, const uint32_t* thr_src
                         if (v < -A.y_max) v = -A.y_max;
                     }
                     bool negative;
+                    const int at = gidx(k, f);
                     if constexpr (PREC == kFP32) {
-                        ys[k * kSlots + f] = v;
+                        ys[at] = v;
                         negative = !(v >= 0.0f);
                     } else if constexpr (PREC == kFP16) {
                         const __half h = __float2half_rn(v);
-                        ys[k * kSlots + f] = h;
+                        ys[at] = h;
                         negative = !(__half2float(h) >= 0.0f);        // sign(-0) = +1
                     } else {
                         const int32_t b = fix_code(v, A.fix_R, A.fix_kmax);
-                        ys[k * kSlots + f] = (int8_t)b;
+                        ys[at] = (int8_t)b;
                         negative = b < 0;
                     }
                     if (negative) word |= 1u << f;
-                    if constexpr (kState) st[k * kSlots + f] = 0;
+                    if constexpr (kState) st[at] = 0;
                 }
                 xw[k] = word;
             }
@@ -325,6 +433,8 @@ __device__ __forceinline__ void decode_job(const Job& A, const uint32_t* thr_src
         const uint32_t unsat = ctl[pass_id & 1];
         ++pass_id;
         uint32_t live = ctl[2];
+        if (A.trace_u != nullptr)
+            trace_round<PREC>(A, L, chk_cols, ys, live, round);
         const uint32_t conv = live & ~unsat;
         const int my_t = round - lane_start[lane];
         const uint32_t at_T = __ballot_sync(0xFFFFFFFFu, ((live >> lane) & 1u) && my_t >= T);
@@ -349,7 +459,7 @@ __device__ __forceinline__ void decode_job(const Job& A, const uint32_t* thr_src
                             if (!ok) {
                                 // X_k = terms - 2 * (#-1 decisions), x(T) included here
                                 const int terms = tf - A.t_smooth + 1;
-                                const int neg = (int)(st[k * kSlots + f] >> kCShift) + (int)bit;
+                                const int neg = (int)(st[gidx(k, f)] >> kCShift) + (int)bit;
                                 const int X = terms - 2 * neg;
                                 bit = X < 0 ? 1u : (X > 0 ? 0u : bit);
                             }
@@ -407,7 +517,11 @@ __device__ __forceinline__ void decode_job(const Job& A, const uint32_t* thr_src
                     c.x += s.x; c.y += s.y; c.z += s.z; c.w += s.w;
                 }
                 const uint32_t D = ((uint32_t)sym_deg[k] + 8u) * 0x11111111u;
-                cnt[k] = make_uint4(D - 2u * c.x, D - 2u * c.y, D - 2u * c.z, D - 2u * c.w);
+                uint32_t* cw = reinterpret_cast<uint32_t*>(cnt) + ((k >> 2) << 4) + (k & 3);
+                cw[0] = D - 2u * c.x;     // quarter q of the group at word 4 q + k % 4
+                cw[4] = D - 2u * c.y;
+                cw[8] = D - 2u * c.z;
+                cw[12] = D - 2u * c.w;
             } else {
                 uint32_t b[7] = {0, 0, 0, 0, 0, 0, 0};     // count <= 127: seven slices
                 for (int e = 0; e < dv_max; ++e) {
@@ -435,37 +549,47 @@ __device__ __forceinline__ void decode_job(const Job& A, const uint32_t* thr_src
             const bool window = SMOOTH && act && t >= A.t_smooth;
             const int groups = (n + 3) >> 2;
             const uint32_t th0 = thr_src[0];    // threshold of the non-adaptive variants
-            const float scale = A.scale, wgt = A.w, fix_R = A.fix_R;
-            const int32_t fix_kmax = A.fix_kmax, fix_W = A.fix_W;
+            const float scale = A.scale, wgt = A.w, fix_R = A.fix_R, acc_R = A.acc_R;
+            const int32_t fix_kmax = A.fix_kmax, fix_W = A.fix_W, acc_W = A.acc_W;
+            const bool uniform = A.uniform != 0;
             const bool single = !ADAPT && A.single;
             const uint32_t nib_shift = 4u * (lane & 7);
             const float wgt_m8 = -8.0f * wgt;       // exact
             unsigned long long my_best = ~0ull;      // single-bit variant: (E key << 32) | k
             // one group of four symbols; only the last group of a code with n % 4 != 0 is partial
+            // (its missing symbols read the zeroed padding and are skipped)
             auto group = [&](const int g, auto partial_tag) {
                 constexpr bool kPartial = decltype(partial_tag)::value;
                 const int k0 = 4 * g;
-                // issue the sample, state, count, decision-word and threshold loads before the
-                // generator's arithmetic, so that their latency overlaps it
+                const int at = (g * kSlots + lane) * 4;   // this lane's entries in the group layout
+                // issue the sample, state, count, decision-word and threshold loads (one vector
+                // each) before the generator's arithmetic, so that their latency overlaps it
                 HeldT yv[4];
+                load_held4(ys + at, yv);
                 [[maybe_unused]] uint32_t sv[4], cwv[4], thv[4];
-                uint32_t xwv[4];
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const bool in = !kPartial || k0 + j < n;
-                    yv[j] = in ? ys[(k0 + j) * kSlots + lane] : HeldT(0);
-                    if constexpr (kState) sv[j] = in ? (uint32_t)st[(k0 + j) * kSlots + lane] : 0u;
-                    if constexpr (!WIDE)
-                        cwv[j] = in ? reinterpret_cast<const uint32_t*>(cnt)[4 * (k0 + j) + (lane >> 3)] : 0u;
-                    xwv[j] = in ? xw[k0 + j] : 0u;
+                if constexpr (kState) {
+                    const uint2 s2 = *reinterpret_cast<const uint2*>(st + at);
+                    sv[0] = s2.x & 0xFFFFu; sv[1] = s2.x >> 16; sv[2] = s2.y & 0xFFFFu; sv[3] = s2.y >> 16;
                 }
+                if constexpr (!WIDE) {
+                    const uint4 c4 = reinterpret_cast<const uint4*>(cnt)[g * 4 + (lane >> 3)];
+                    cwv[0] = c4.x; cwv[1] = c4.y; cwv[2] = c4.z; cwv[3] = c4.w;
+                }
+                const uint4 x4 = reinterpret_cast<const uint4*>(xw)[g];
+                const uint32_t xwv[4] = {x4.x, x4.y, x4.z, x4.w};
                 if constexpr (ADAPT) {
                     // u_k <= t - 1 < T for a live slot (cleared on every refill)
 #pragma unroll
                     for (int j = 0; j < 4; ++j) thv[j] = thr[sv[j] & kUMask];
                 }
                 float z[4];
-                gauss4((uint32_t)g, (uint32_t)t, flo, fhi, G, icdf, z);
+                noise4((uint32_t)g, (uint32_t)t, flo, fhi, G, icdf, uniform, z);
+                uint32_t fmv[4] = {0u, 0u, 0u, 0u};          // flip masks of the four symbols
+                [[maybe_unused]] uint32_t nvv[4];             // new state words
+                if constexpr (kState) {
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) nvv[j] = sv[j];
+                }
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
                     const int k = k0 + j;
@@ -509,17 +633,26 @@ __device__ __forceinline__ void decode_job(const Job& A, const uint32_t* thr_src
                             return __float2half_rn(0.0f);
                         }
                     };
+                    // the held Eq. 8 level in accumulator steps (2^8 per half level), plus the
+                    // weight and the perturbation rounded to steps: exact int32
+                    [[maybe_unused]] auto metric_acc = [&]() -> int32_t {
+                        const int32_t Y = (2 * (int32_t)yv[j] + 1) * (1 << kAccBits);
+                        const int32_t Qs = __float2int_rn(__fmul_rn(q, acc_R));
+                        return (xneg ? -Y : Y) + acc_W * S + Qs;
+                    };
                     // below_threshold(u): E_k < theta_k in the held arithmetic
                     auto below = [&](uint32_t th_bits) -> bool {
                         if constexpr (PREC == kFP32) {
                             return metric32() < __uint_as_float(th_bits);
                         } else if constexpr (PREC == kFP16) {
                             return __half2float(metric16()) < __uint_as_float(th_bits);
-                        } else {
+                        } else if constexpr (PREC == kFIX) {
                             // Eq. 9 in units of Delta/2, exact integers
                             const int32_t Y = 2 * (int32_t)yv[j] + 1;
                             const int32_t Qv = 2 * fix_code(q, fix_R, fix_kmax) + 1;
                             return (xneg ? -Y : Y) + fix_W * S + Qv < (int32_t)th_bits;
+                        } else {
+                            return metric_acc() < (int32_t)th_bits;
                         }
                     };
                     if constexpr (!ADAPT) {
@@ -530,6 +663,8 @@ __device__ __forceinline__ void decode_job(const Job& A, const uint32_t* thr_src
                                 key = order_key(metric32());
                             } else if constexpr (PREC == kFP16) {
                                 key = order_key(__half2float(metric16()));
+                            } else if constexpr (PREC == kFIXACC) {
+                                key = (uint32_t)metric_acc() ^ 0x80000000u;
                             } else {
                                 const int32_t Y = 2 * (int32_t)yv[j] + 1;
                                 const int32_t Qv = 2 * fix_code(q, fix_R, fix_kmax) + 1;
@@ -538,7 +673,7 @@ __device__ __forceinline__ void decode_job(const Job& A, const uint32_t* thr_src
                             const unsigned long long cand = ((unsigned long long)key << 32) | (uint32_t)k;
                             my_best = cand < my_best ? cand : my_best;
                             if constexpr (SMOOTH) {
-                                if (window && xneg) st[k * kSlots + lane] = (uint16_t)(sv[j] + (1u << kCShift));
+                                if (window && xneg) nvv[j] = sv[j] + (1u << kCShift);
                             }
                             continue;
                         }
@@ -550,16 +685,22 @@ __device__ __forceinline__ void decode_job(const Job& A, const uint32_t* thr_src
                         const bool lower = below(th);       // evaluated for every lane, no branch
                         flip = act && lower;
                         // u_k += 1 when not flipped; the window counter counts x_k = -1
-                        const uint32_t nv = s0 + ((ADAPT && act && !flip) ? 1u : 0u) +
-                                            (window ? (xsign >> (31 - kCShift)) : 0u);
-                        if (ADAPT || nv != s0) st[k * kSlots + lane] = (uint16_t)nv;
+                        nvv[j] = s0 + ((ADAPT && act && !flip) ? 1u : 0u) + (window ? (xsign >> (31 - kCShift)) : 0u);
                     } else {
                         const bool lower = below(th0);
                         flip = act && lower;
                     }
-                    const uint32_t fm = __ballot_sync(0xFFFFFFFFu, flip);
-                    if (lane == 0) xw[k] = xword ^ fm;
+                    fmv[j] = __ballot_sync(0xFFFFFFFFu, flip);
                 }
+                if constexpr (kState) {
+                    const uint2 n2 = make_uint2(nvv[0] | (nvv[1] << 16), nvv[2] | (nvv[3] << 16));
+                    if (ADAPT || nvv[0] != sv[0] || nvv[1] != sv[1] || nvv[2] != sv[2] || nvv[3] != sv[3])
+                        *reinterpret_cast<uint2*>(st + at) = n2;
+                }
+                // Step 3b flips of the group (the single-bit variant flips after the sweep)
+                if (lane == 0 && !single)
+                    reinterpret_cast<uint4*>(xw)[g] = make_uint4(xwv[0] ^ fmv[0], xwv[1] ^ fmv[1], xwv[2] ^ fmv[2],
+                                                                 xwv[3] ^ fmv[3]);
             };
             const int full = n >> 2;
             for (int g = warp; g < full; g += nwarps) group(g, std::false_type{});

@@ -12,8 +12,8 @@ __global__ void __launch_bounds__(1024) ngdbf_multi_kernel(const __grid_constant
     __shared__ int32_t next_job;
     const SmemLayout L = smem_layout(A.n_max, A.m_max, A.t_max, A.dv_max, A.dc_max, ADAPT,
                                      ST_SMEM && (ADAPT || SMOOTH), A.placement);
-    HeldT* ys = static_cast<HeldT*>(A.yslots) + (size_t)blockIdx.x * A.n_max * kSlots;
-    uint16_t* st = A.st_global ? A.st_global + (size_t)blockIdx.x * A.n_max * kSlots : nullptr;
+    HeldT* ys = static_cast<HeldT*>(A.yslots) + (size_t)blockIdx.x * pad4(A.n_max) * kSlots;
+    uint16_t* st = A.st_global ? A.st_global + (size_t)blockIdx.x * pad4(A.n_max) * kSlots : nullptr;
     int j = A.first_job[blockIdx.x];
     while (j >= 0) {
         if (threadIdx.x == 0) job = A.jobs[j];
@@ -66,6 +66,7 @@ void* multi_kernel_fn(int variant, int precision, bool st_smem, bool wide) {
     switch (precision) {
         case NGDBF_FP16: return (void*)pick_variant<kFP16>(variant, st_smem, wide);
         case NGDBF_FIX: return (void*)pick_variant<kFIX>(variant, st_smem, wide);
+        case NGDBF_FIXACC: return (void*)pick_variant<kFIXACC>(variant, st_smem, wide);
         default: return (void*)pick_variant<kFP32>(variant, st_smem, wide);
     }
 }

@@ -116,8 +116,8 @@ ngdbf_status layout_launch(ngdbf_server* S, const std::vector<Request*>& reqs, L
     for (const ngdbf_job& q : jobs) groups += (q.n_frames + 31) / 32;
     L.block = L.plan.shapes[0].first;
     L.grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)L.plan.sm_count * L.plan.shapes[0].second, groups));
-    const size_t per_slot_y = (size_t)L.plan.n_max * 32 * held_bytes(L.plan.precision);
-    const size_t per_slot_st = L.plan.state_global ? (size_t)L.plan.n_max * 32 * 2 : 0;
+    const size_t per_slot_y = (size_t)pad4(L.plan.n_max) * kSlots * held_bytes(L.plan.precision);
+    const size_t per_slot_st = L.plan.state_global ? (size_t)pad4(L.plan.n_max) * kSlots * 2 : 0;
     L.off_jobs = align256(8 * (size_t)J);                 // queues first
     L.off_thr = L.off_jobs + align256(sizeof(Job) * J);
     L.off_first = L.off_thr + align256(L.plan.thr_words * 4);

@@ -24,9 +24,11 @@ NGDBF_ERR_TIMEOUT = 5
 NGDBF_ADAPT = 1
 NGDBF_SMOOTH = 2
 NGDBF_SINGLE = 4
+NGDBF_UNIFORM = 8
 NGDBF_FP32 = 0
 NGDBF_FP16 = 1
 NGDBF_FIX = 2
+NGDBF_FIXACC = 3
 NGDBF_MAX_T = 511
 NGDBF_MAX_WINDOW = 126
 NGDBF_NOALLOC_SCRATCH_BYTES = 40 << 20
@@ -64,6 +66,12 @@ class ngdbf_server_stats(ctypes.Structure):
                 ("peak_concurrent_launches", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
+class ngdbf_host_stats(ctypes.Structure):
+    _fields_ = [("chunks", ctypes.c_int32), ("reserved", ctypes.c_int32), ("h2d_bytes", ctypes.c_int64),
+                ("d2h_bytes", ctypes.c_int64), ("h2d_ms", ctypes.c_double), ("kernel_ms", ctypes.c_double),
+                ("d2h_ms", ctypes.c_double), ("wall_ms", ctypes.c_double)]
+
+
 class ngdbf_launch_info(ctypes.Structure):
     _fields_ = [("grid", ctypes.c_int32), ("block", ctypes.c_int32), ("smem_bytes", ctypes.c_int32),
                 ("state_in_smem", ctypes.c_int32), ("kernels", ctypes.c_int32),
@@ -99,6 +107,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
                                       ctypes.POINTER(ngdbf_params), ctypes.c_uint64, ctypes.c_uint64,
                                       vp, vp, vp, ctypes.c_int64]
     lib.ngdbf_decode_noalloc.argtypes = lib.ngdbf_decode.argtypes
+    lib.ngdbf_decode_trace.argtypes = [vp, vp, ctypes.c_int64, ctypes.c_float, ctypes.POINTER(ngdbf_params),
+                                       ctypes.c_uint64, ctypes.c_uint64, vp, vp, vp, ctypes.c_int64, vp, vp, vp]
     lib.ngdbf_batch_create.argtypes = [ctypes.POINTER(ngdbf_job), ctypes.c_int32, ctypes.c_uint64,
                                        ctypes.c_int32, vp, ctypes.POINTER(vp)]
     lib.ngdbf_batch_launch.argtypes = [vp, vp]
@@ -113,14 +123,19 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.ngdbf_server_get_stats.argtypes = [vp, ctypes.POINTER(ngdbf_server_stats)]
     lib.ngdbf_server_destroy.argtypes = [vp]
     lib.ngdbf_gaussian_range.argtypes = [ctypes.c_uint32, ctypes.c_uint32, vp, vp]
+    lib.ngdbf_generator_table.argtypes = [ctypes.POINTER(ctypes.c_float)]
+    lib.ngdbf_mix_probe.argtypes = [ctypes.c_int32, vp, ctypes.POINTER(ctypes.c_int64), vp]
+    lib.ngdbf_pool_usage.argtypes = [ctypes.c_int32, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
     lib.ngdbf_last_launch.argtypes = [ctypes.POINTER(ngdbf_launch_info)]
+    lib.ngdbf_last_host_stats.argtypes = [ctypes.POINTER(ngdbf_host_stats)]
     lib.ngdbf_last_error.argtypes = []
     lib.ngdbf_last_error.restype = ctypes.c_char_p
     for fn in ("ngdbf_code_create", "ngdbf_code_destroy", "ngdbf_code_info", "ngdbf_decode",
-               "ngdbf_decode_host", "ngdbf_decode_noalloc", "ngdbf_last_launch", "ngdbf_batch_create",
+               "ngdbf_decode_host", "ngdbf_decode_noalloc", "ngdbf_decode_trace", "ngdbf_last_launch", "ngdbf_batch_create",
                "ngdbf_batch_launch", "ngdbf_batch_destroy", "ngdbf_server_create", "ngdbf_server_submit",
                "ngdbf_server_poll", "ngdbf_server_wait", "ngdbf_server_get_stats", "ngdbf_server_destroy",
-               "ngdbf_gaussian_range"):
+               "ngdbf_gaussian_range", "ngdbf_pool_usage", "ngdbf_last_host_stats", "ngdbf_mix_probe",
+               "ngdbf_generator_table"):
         getattr(lib, fn).restype = ctypes.c_int
     if path is None:
         _lib = lib
@@ -172,6 +187,14 @@ def ngdbf_decode(code: int, y_ptr: int, n_frames: int, sigma: float, params: ngd
     lib = load()
     _check(lib, lib.ngdbf_decode(code, y_ptr, n_frames, sigma, ctypes.byref(params), seed, frame_offset,
                                  bits_ptr, iters_ptr, pass_ptr, stream))
+
+
+def ngdbf_decode_trace(code: int, y_ptr: int, n_frames: int, sigma: float, params: ngdbf_params, seed: int,
+                       frame_offset: int, bits_ptr: int, iters_ptr: int, pass_ptr: int, trace_frames: int,
+                       unsat_ptr: int, corr_ptr: int, stream: int = 0) -> None:
+    lib = load()
+    _check(lib, lib.ngdbf_decode_trace(code, y_ptr, n_frames, sigma, ctypes.byref(params), seed, frame_offset,
+                                       bits_ptr, iters_ptr, pass_ptr, trace_frames, unsat_ptr, corr_ptr, stream))
 
 
 def ngdbf_decode_noalloc(code: int, y_ptr: int, n_frames: int, sigma: float, params: ngdbf_params,
@@ -259,6 +282,38 @@ def ngdbf_gaussian_range(start: int, count: int, z_ptr: int, stream: int = 0) ->
     _check(lib, lib.ngdbf_gaussian_range(start & 0xFFFFFFFF, count, z_ptr, stream))
 
 
+def ngdbf_generator_table() -> np.ndarray:
+    """[32, 8, 4] FP32 coefficients of the generator's inverse-CDF segments (host call)."""
+    lib = load()
+    out = np.empty((32, 8, 4), dtype=np.float32)
+    _check(lib, lib.ngdbf_generator_table(out.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+    return out
+
+
+def ngdbf_mix_probe(groups: int, sink_ptr: int, stream: int = 0) -> int:
+    """Launches the same-mix throughput probe; returns the number of threads launched."""
+    lib = load()
+    th = ctypes.c_int64()
+    _check(lib, lib.ngdbf_mix_probe(groups, sink_ptr, ctypes.byref(th), stream))
+    return th.value
+
+
+def ngdbf_pool_usage(reset_high: bool = False) -> tuple[int, int]:
+    """(bytes in use now, most bytes in use since the last reset) of the library's scratch pool."""
+    lib = load()
+    now, high = ctypes.c_int64(), ctypes.c_int64()
+    _check(lib, lib.ngdbf_pool_usage(1 if reset_high else 0, ctypes.byref(now), ctypes.byref(high)))
+    return now.value, high.value
+
+
+def ngdbf_last_host_stats() -> dict:
+    """Event timing of the calling thread's most recent ngdbf_decode_host (ms, bytes)."""
+    lib = load()
+    st = ngdbf_host_stats()
+    _check(lib, lib.ngdbf_last_host_stats(ctypes.byref(st)))
+    return {f: getattr(st, f) for f, _ in st._fields_ if f != "reserved"}
+
+
 def ngdbf_last_launch() -> dict:
     lib = load()
     info = ngdbf_launch_info()
@@ -307,6 +362,24 @@ class DeviceCode:
         ngdbf_decode(self.handle, y.data_ptr(), F, float(sigma), params, int(seed), int(frame_offset),
                      bits.data_ptr(), iters.data_ptr(), pas.data_ptr(), s.cuda_stream)
         return bits, iters, pas
+
+    def decode_trace(self, y, sigma: float, params: ngdbf_params, trace_frames: int, seed: int = 1,
+                     frame_offset: int = 0, stream=None):
+        """decode() plus the objective trace of the first trace_frames frames: returns (bits, iters,
+        pass, U int32 [K, T+1], C int64 [K, T+1]) as CUDA tensors; U is -1 and C 0 after iters[f]."""
+        import torch
+        assert y.is_cuda and y.dtype == torch.float32 and y.is_contiguous() and y.shape[-1] == self.n
+        F, K, T = y.shape[0], int(trace_frames), params.t_max
+        bits = torch.empty((F, (self.n + 7) // 8), dtype=torch.uint8, device=y.device)
+        iters = torch.empty(F, dtype=torch.int32, device=y.device)
+        pas = torch.empty(F, dtype=torch.uint8, device=y.device)
+        tu = torch.full((max(K, 1), T + 1), -1, dtype=torch.int32, device=y.device)
+        tc = torch.zeros((max(K, 1), T + 1), dtype=torch.int64, device=y.device)
+        s = stream if stream is not None else torch.cuda.current_stream(y.device)
+        ngdbf_decode_trace(self.handle, y.data_ptr(), F, float(sigma), params, int(seed), int(frame_offset),
+                           bits.data_ptr(), iters.data_ptr(), pas.data_ptr(), K, tu.data_ptr(), tc.data_ptr(),
+                           s.cuda_stream)
+        return bits, iters, pas, tu[:K], tc[:K]
 
     def decode_host(self, y: np.ndarray, sigma: float, params: ngdbf_params, seed: int = 1,
                     frame_offset: int = 0, out=None, chunk_frames: int = 0):

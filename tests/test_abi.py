@@ -98,8 +98,9 @@ def test_struct_layouts_match_the_c_compiler(tmp_path):
 #include "ngdbf.h"
 #define F(T, f) printf("%s.%s %zu\\n", #T, #f, offsetof(T, f));
 int main(void) {
-    printf("ngdbf_params %zu\\nngdbf_job %zu\\nngdbf_launch_info %zu\\n", sizeof(ngdbf_params),
-           sizeof(ngdbf_job), sizeof(ngdbf_launch_info));
+    printf("ngdbf_params %zu\\nngdbf_job %zu\\nngdbf_launch_info %zu\\nngdbf_host_stats %zu\\n",
+           sizeof(ngdbf_params), sizeof(ngdbf_job), sizeof(ngdbf_launch_info), sizeof(ngdbf_host_stats));
+    F(ngdbf_host_stats, h2d_bytes) F(ngdbf_host_stats, h2d_ms) F(ngdbf_host_stats, wall_ms)
     F(ngdbf_job, code) F(ngdbf_job, y) F(ngdbf_job, n_frames) F(ngdbf_job, sigma) F(ngdbf_job, params)
     F(ngdbf_job, frame_offset) F(ngdbf_job, bits) F(ngdbf_job, iters) F(ngdbf_job, pass)
     F(ngdbf_params, q_bits) F(ngdbf_launch_info, sm_count) F(ngdbf_launch_info, tables_in_smem)
@@ -112,9 +113,38 @@ int main(void) {
     assert int(got["ngdbf_params"]) == ctypes.sizeof(ngdbf.ngdbf_params)
     assert int(got["ngdbf_job"]) == ctypes.sizeof(ngdbf.ngdbf_job)
     assert int(got["ngdbf_launch_info"]) == ctypes.sizeof(ngdbf.ngdbf_launch_info)
+    assert int(got["ngdbf_host_stats"]) == ctypes.sizeof(ngdbf.ngdbf_host_stats)
+    for f in ("h2d_bytes", "h2d_ms", "wall_ms"):
+        assert int(got[f"ngdbf_host_stats.{f}"]) == getattr(ngdbf.ngdbf_host_stats, f).offset, f
     for f in ("code", "y", "n_frames", "sigma", "params", "frame_offset", "bits", "iters"):
         assert int(got[f"ngdbf_job.{f}"]) == getattr(ngdbf.ngdbf_job, f).offset, f
     assert int(got["ngdbf_job.pass"]) == ngdbf.ngdbf_job.pass_.offset
     assert int(got["ngdbf_params.q_bits"]) == ngdbf.ngdbf_params.q_bits.offset
     assert int(got["ngdbf_launch_info.sm_count"]) == ngdbf.ngdbf_launch_info.sm_count.offset
     assert int(got["ngdbf_launch_info.tables_in_smem"]) == ngdbf.ngdbf_launch_info.tables_in_smem.offset
+
+
+def test_generator_table_equals_the_reference_and_an_independent_derivation():
+    """The library's inverse-CDF table (host code of libngdbf.so, no GPU needed) equals the reference
+    decoder's word for word, and an independent derivation -- scipy's ndtri at the Chebyshev
+    points, cubic by a float64 Vandermonde solve -- agrees within one FP32 ulp on every coefficient
+    (c3 carries the cancellation of a third difference: its FP32 word may differ by an ulp between
+    double-precision routes, which is why the table is defined by one fixed double computation)."""
+    import numpy as np
+    from scipy.special import ndtri
+
+    import oracle
+    lib_tab = ngdbf.ngdbf_generator_table()
+    ref_tab = oracle.load().icdf_table()
+    assert lib_tab.tobytes() == ref_tab.tobytes()
+    nodes = 0.5 * np.cos((2 * np.arange(4) + 1) * np.pi / 8)
+    V = np.vander(nodes, 4, increasing=True)
+    worst = 0.0
+    for j in range(32):
+        for s in range(8):
+            g = ndtri(np.ldexp(8.0 + s + 0.5 + nodes, -(j + 5)))
+            c = np.linalg.solve(V, g)
+            w = lib_tab[j, s]
+            ulp = np.spacing(np.abs(w)).astype(np.float64)
+            worst = max(worst, float(np.max(np.abs(c - w.astype(np.float64)) / ulp)))
+    assert worst <= 1.0, f"{worst:.2f} ulp"

@@ -301,7 +301,7 @@ def test_invalid_arguments_report_status():
         dc.decode(y, -1.0, ngdbf.make_params())
     assert e.value.status == ngdbf.NGDBF_ERR_INVALID_ARG
     for bad in (dict(precision=ngdbf.NGDBF_FIX, q_bits=9), dict(precision=ngdbf.NGDBF_FIX, q_bits=8, y_max=0.0),
-                dict(precision=ngdbf.NGDBF_FP16, q_bits=4), dict(precision=7), dict(variant=5), dict(variant=8)):
+                dict(precision=ngdbf.NGDBF_FP16, q_bits=4), dict(precision=7), dict(variant=5), dict(variant=16)):
         with pytest.raises(ngdbf.NgdbfError) as e:
             dc.decode(y, 0.5, ngdbf.make_params(**bad))
         assert e.value.status == ngdbf.NGDBF_ERR_INVALID_ARG

@@ -8,7 +8,11 @@ instead of pool memory.  This test calls it twice in a row through the C ABI
 and checks each result bit-for-bit against ngdbf_decode, the tolerance every
 parity test here uses.  The second call uses a longer code whose per-slot
 state lives in the static array too, so the array is reused with another
-layout and a launch that is cut down to fit it.
+layout and a launch that is cut down to fit it.  It also checks the property
+the entry point exists for: across a call, neither the library's scratch pool
+(its high-water mark, reset before the call) nor the device's free memory
+nor torch's allocator moves, while the same check sees ngdbf_decode's pool
+allocation.
 """
 import numpy as np
 import pytest
@@ -57,6 +61,29 @@ def test_noalloc_matches_the_allocating_entry_point_on_two_calls():
         try:
             got = _run(ngdbf.ngdbf_decode_noalloc, dc.handle, y, sigma, params, 9, 100 * call, code.n)
             ref = _run(ngdbf.ngdbf_decode, dc.handle, y, sigma, params, 9, 100 * call, code.n)
+        finally:
+            dc.close()
+        # a repeated no-alloc call takes nothing from the pool, the device or torch's allocator
+        bits, iters, pas = (torch.empty((F, (code.n + 7) // 8), dtype=torch.uint8, device="cuda"),
+                            torch.empty(F, dtype=torch.int32, device="cuda"),
+                            torch.empty(F, dtype=torch.uint8, device="cuda"))
+        dc = ngdbf.DeviceCode.from_code(code)
+        try:
+            stream = torch.cuda.current_stream().cuda_stream
+            args = (dc.handle, y.data_ptr(), F, float(sigma), params, 9, 100 * call, bits.data_ptr(),
+                    iters.data_ptr(), pas.data_ptr(), stream)
+            torch.cuda.synchronize()
+            now0, _ = ngdbf.ngdbf_pool_usage(reset_high=True)
+            free0, torch0 = torch.cuda.mem_get_info()[0], torch.cuda.memory_allocated()
+            ngdbf.ngdbf_decode_noalloc(*args)
+            torch.cuda.synchronize()
+            now1, high1 = ngdbf.ngdbf_pool_usage()
+            assert (now1, high1) == (now0, now0), "ngdbf_decode_noalloc took scratch from the pool"
+            assert torch.cuda.mem_get_info()[0] == free0 and torch.cuda.memory_allocated() == torch0
+            ngdbf.ngdbf_pool_usage(reset_high=True)
+            ngdbf.ngdbf_decode(*args)                       # control: the pool path is visible
+            torch.cuda.synchronize()
+            assert ngdbf.ngdbf_pool_usage()[1] > now0
         finally:
             dc.close()
         for a, b, name in zip(got[:3], ref[:3], ("bits", "iters", "pass")):
