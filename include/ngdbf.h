@@ -283,7 +283,10 @@ typedef struct ngdbf_job {
 typedef struct ngdbf_batch ngdbf_batch_t;   /* opaque; owns device scratch and the job table */
 
 enum {
-    NGDBF_BATCH_TUNE = 1,   /* time the candidate block sizes on this table, keep the fastest */
+    NGDBF_BATCH_TUNE = 1,   /* time the candidate launch shapes on this table -- block size x
+                               thread-block cluster size (1, 2, 4, 8: codes of 2048 symbols or more
+                               split over the CTAs of a cluster) x adjacency tables in shared
+                               memory -- and keep the fastest */
     NGDBF_BATCH_GRAPH = 2   /* capture the launch (queue reset + kernel) in a CUDA graph */
 };
 
@@ -406,9 +409,22 @@ typedef struct ngdbf_launch_info {
     int32_t kernels;         /* kernels launched by the call */
     int32_t sm_count;        /* SMs of the device */
     int32_t tables_in_smem;  /* adjacency tables copied to shared memory: 1 N(i), 2 M(k), 3 both */
+    int32_t cluster;         /* CTAs per thread-block cluster (1: none); codes of 2048 symbols or
+                                more are split over a cluster, smaller ones decoded CTA by CTA */
 } ngdbf_launch_info;
 
 ngdbf_status ngdbf_last_launch(ngdbf_launch_info* out);
+
+/* The candidate launch shapes of a batch, the ones NGDBF_BATCH_TUNE times (block size x
+ * cluster size x adjacency tables in shared memory; candidate 0 is the default).  *count
+ * (may be NULL) receives their number; info (may be NULL) receives candidate k (k < 0: the
+ * shape in use): grid = the most CTAs resident at once, block, shared memory, placements
+ * and cluster size. */
+ngdbf_status ngdbf_batch_shape(const ngdbf_batch_t* batch, int32_t k, int32_t* count, ngdbf_launch_info* info);
+
+/* Makes candidate k the shape of later launches (recaptures the graph of NGDBF_BATCH_GRAPH).
+ * Results do not depend on the shape. */
+ngdbf_status ngdbf_batch_use_shape(ngdbf_batch_t* batch, int32_t k);
 
 /* Message for the last error on the calling thread ("" if none). */
 const char* ngdbf_last_error(void);

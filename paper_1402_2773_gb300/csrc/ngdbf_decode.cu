@@ -104,6 +104,7 @@ ngdbf_status fail(ngdbf_status s, const std::string& msg) {
 
 void set_last_launch(int grid, int block, int smem, int state_in_smem, int tables_in_smem, int kernels,
                      int sm_count) {
+    g_last_launch.cluster = 1;
     g_last_launch.grid = grid;
     g_last_launch.block = block;
     g_last_launch.smem_bytes = smem;
@@ -278,11 +279,11 @@ struct PlacementChoice {
 
 template <class FnOf>
 ngdbf_status choose_placement(int dev, int n, int m, int t_max, int dv_max, int dc_max, bool adapt, bool state,
-                              int limit, FnOf fn_of, PlacementChoice* out) {
+                              int limit, FnOf fn_of, PlacementChoice* out, int n_local = -1) {
     using Key = std::vector<int64_t>;
     static std::mutex mu;
     static std::map<Key, PlacementChoice> cache;
-    const Key key = {dev, n, m, t_max, dv_max, dc_max, adapt, state, limit,
+    const Key key = {dev, n, m, t_max, dv_max, dc_max, adapt, state, limit, n_local,
                      (int64_t)(intptr_t)fn_of(true), (int64_t)(intptr_t)fn_of(false)};
     {
         std::lock_guard<std::mutex> g(mu);
@@ -301,7 +302,7 @@ ngdbf_status choose_placement(int dev, int n, int m, int t_max, int dv_max, int 
         if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
         if (best.bps > 0) break;                       // state fits in shared memory
         for (const int tb : {kTabChk | kTabSym, kTabChk, 0}) {
-            const SmemLayout L = smem_layout(n, m, t_max, dv_max, dc_max, adapt, st, tb);
+            const SmemLayout L = smem_layout(n, m, t_max, dv_max, dc_max, adapt, st, tb, n_local);
             if (L.total > limit) continue;
             for (const int block : {1024, 512, 256}) {
                 int bps = 0;
@@ -919,12 +920,16 @@ extern "C" ngdbf_status ngdbf_decode_noalloc(const ngdbf_code_t* C, const float*
 struct ngdbf_batch {
     int device = 0, n_jobs = 0, sm_count = 0;
     void* fn = nullptr;                 // job-table kernel
-    int grid = 0, block = 0, smem = 0, state_in_smem = 0, tables_in_smem = 0;
+    int grid = 0, block = 0, smem = 0, state_in_smem = 0, tables_in_smem = 0, cluster = 1;
     MultiArgs args;
     unsigned char* d_mem = nullptr;     // jobs | thresholds | queues | first_job | samples | state
+    unsigned char* d_st = nullptr;      // per-slot state when it is not in shared memory
     unsigned long long* d_queues = nullptr;
     int32_t* d_first = nullptr;
     std::vector<int64_t> frames, weight;
+    std::vector<int> n_of_job;
+    std::vector<TableShape> shapes;
+    int shape = 0;                      // index of the shape in use
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
 };
@@ -936,13 +941,18 @@ namespace host {
 // (frames x n x (T + 1)), at least one CTA per job with frames, at most one CTA
 // per 32 of its frames; CTAs left over go to the jobs with the most work per CTA.
 std::vector<int32_t> assign_ctas(const std::vector<int64_t>& frames, const std::vector<int64_t>& weight, int grid) {
+    std::vector<int64_t> cap(frames.size());
+    for (size_t j = 0; j < frames.size(); ++j) cap[j] = (frames[j] + kSlots - 1) / kSlots;
+    return assign_ctas_capped(frames, weight, cap, grid);
+}
+
+// The same with explicit caps (the most CTAs, or clusters, a job can keep busy).
+std::vector<int32_t> assign_ctas_capped(const std::vector<int64_t>& frames, const std::vector<int64_t>& weight,
+                                        const std::vector<int64_t>& cap, int grid) {
     const int J = (int)frames.size();
-    std::vector<int64_t> cap(J), cnt(J, 0);
+    std::vector<int64_t> cnt(J, 0);
     double total = 0;
-    for (int j = 0; j < J; ++j) {
-        cap[j] = (frames[j] + kSlots - 1) / kSlots;
-        total += (double)weight[j];
-    }
+    for (int j = 0; j < J; ++j) total += (double)weight[j];
     int used = 0;
     for (int j = 0; j < J; ++j) {
         if (frames[j] == 0) continue;
@@ -1036,6 +1046,91 @@ ngdbf_status plan_table(const ngdbf_job* jobs, int32_t n_jobs, int dev, TablePla
     return NGDBF_OK;
 }
 
+// Codes of at least this many symbols are split over the CTAs of a cluster.
+constexpr int kSplitMinN = 2048;
+
+ngdbf_status table_shapes(const TablePlan& T, const ngdbf_job* jobs, int32_t n_jobs, int dev,
+                          std::vector<TableShape>* out) {
+    out->clear();
+    for (const auto& sh : T.shapes) {
+        TableShape c;
+        c.fn = T.fn; c.block = sh.first; c.cluster = 1; c.grid_max = T.sm_count * sh.second; c.smem = T.smem;
+        c.placement = T.placement; c.n_local = T.n_max; c.split_min_n = INT32_MAX;
+        c.st_smem = T.st_smem; c.state_global = T.state_global;
+        out->push_back(c);
+    }
+    int smem_optin = 0;
+    cudaError_t e = cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
+    const bool state = (T.variant & 3) != 0, adapt = (T.variant & NGDBF_ADAPT) != 0;
+    const int variant = T.variant, precision = T.precision;
+    const bool wide = T.wide;
+    {
+        // no cluster, the other placements of the adjacency tables that fit with the plan's state
+        cudaFuncAttributes fa;
+        e = cudaFuncGetAttributes(&fa, T.fn);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaFuncGetAttributes");
+        const int limit = smem_optin - (int)fa.sharedSizeBytes;
+        for (const int tb : {kTabChk | kTabSym, kTabChk, 0}) {
+            if (tb == T.placement) continue;
+            const SmemLayout L = smem_layout(T.n_max, T.m_max, T.t_max, T.dv_max, T.dc_max, adapt, T.st_smem, tb);
+            if (L.total > limit) continue;
+            for (const int block : {1024, 512}) {
+                int bps = 0;
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, (const void*)T.fn, block, L.total);
+                if (e != cudaSuccess) return cuda_fail(e, "occupancy");
+                if (bps <= 0) continue;
+                TableShape c;
+                c.fn = T.fn; c.block = block; c.cluster = 1; c.grid_max = T.sm_count * bps; c.smem = L.total;
+                c.placement = tb; c.n_local = T.n_max; c.split_min_n = INT32_MAX;
+                c.st_smem = T.st_smem; c.state_global = T.state_global;
+                out->push_back(c);
+            }
+        }
+    }
+    for (const int C : {2, 4, 8}) {
+        // symbols per CTA: the share of a split code, or a whole code decoded per CTA
+        int n_local = 0, n_split = 0;
+        for (int j = 0; j < n_jobs; ++j) {
+            const int n = jobs[j].code->n;
+            if (n >= kSplitMinN) {
+                n_local = std::max(n_local, split_local_max(n, C));
+                ++n_split;
+            } else {
+                n_local = std::max(n_local, n);
+            }
+        }
+        if (n_split == 0) break;            // nothing to split
+        cudaFuncAttributes fa;
+        e = cudaFuncGetAttributes(&fa, multi_cluster_kernel_fn(variant, precision, state, wide));
+        if (e != cudaSuccess) return cuda_fail(e, "cudaFuncGetAttributes");
+        const int limit = smem_optin - (int)fa.sharedSizeBytes;
+        for (const bool st : {true, false}) {
+            if (st && !state) continue;
+            void* fn = multi_cluster_kernel_fn(variant, precision, st, wide);
+            e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, limit);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+            bool any = false;
+            for (const int tb : {kTabChk | kTabSym, kTabChk, 0}) {
+                const SmemLayout L = smem_layout(T.n_max, T.m_max, T.t_max, T.dv_max, T.dc_max, adapt, st, tb, n_local);
+                if (L.total > limit) continue;
+                for (const int block : {1024, 512}) {
+                    const int clusters = max_active_clusters(fn, C, block, L.total);
+                    if (clusters <= 0) continue;
+                    TableShape c;
+                    c.fn = fn; c.block = block; c.cluster = C; c.grid_max = clusters * C; c.smem = L.total;
+                    c.placement = tb; c.n_local = n_local; c.split_min_n = kSplitMinN;
+                    c.st_smem = st; c.state_global = state && !st;
+                    out->push_back(c);
+                    any = true;
+                }
+            }
+            if (any) break;                  // the state fits shared memory: keep it there
+        }
+    }
+    return NGDBF_OK;
+}
+
 }  // namespace host
 }  // namespace ngdbf
 
@@ -1047,14 +1142,52 @@ cudaError_t batch_enqueue(ngdbf_batch* B, cudaStream_t stream) {
     return launch_multi(B->fn, B->args, B->grid, B->block, B->smem, stream);
 }
 
-ngdbf_status batch_set_shape(ngdbf_batch* B, int block, int bps) {
-    B->block = block;
-    int64_t groups = 0;
-    for (int j = 0; j < B->n_jobs; ++j) groups += (B->frames[j] + kSlots - 1) / kSlots;
-    B->grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)B->sm_count * bps, groups));
-    std::vector<int32_t> first = assign_ctas(B->frames, B->weight, B->grid);
+// Puts candidate `k` in use: kernel, launch shape, shared-memory plan and the first job of
+// every CTA (of every cluster: a split job keeps one cluster busy per 32 frames, a job decoded
+// CTA by CTA one cluster per 32 C frames).
+ngdbf_status batch_set_shape(ngdbf_batch* B, int k) {
+    const TableShape& sh = B->shapes[k];
+    const int C = sh.cluster;
+    B->shape = k;
+    B->fn = sh.fn;
+    B->block = sh.block;
+    B->smem = sh.smem;
+    B->cluster = C;
+    B->state_in_smem = sh.st_smem ? 1 : 0;
+    B->tables_in_smem = sh.placement;
+    B->args.placement = sh.placement;
+    B->args.cluster = C;
+    B->args.split_min_n = sh.split_min_n;
+    B->args.n_local = sh.n_local;
+    B->args.st_global = sh.state_global ? reinterpret_cast<uint16_t*>(B->d_st) : nullptr;
+    std::vector<int64_t> cap(B->n_jobs);
+    int64_t clusters = 0;
+    for (int j = 0; j < B->n_jobs; ++j) {
+        const int64_t per = (int64_t)kSlots * (B->n_of_job[j] >= sh.split_min_n ? 1 : C);
+        cap[j] = (B->frames[j] + per - 1) / per;
+        clusters += cap[j];
+    }
+    const int64_t n_cl = std::max<int64_t>(1, std::min<int64_t>(sh.grid_max / C, clusters));
+    B->grid = (int)(n_cl * C);
+    std::vector<int32_t> first = assign_ctas_capped(B->frames, B->weight, cap, (int)n_cl);
     cudaError_t e = cudaMemcpy(B->d_first, first.data(), first.size() * 4, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_fail(e, "job table: first jobs");
+    return NGDBF_OK;
+}
+
+// Captures queue reset + kernel in a CUDA graph that ngdbf_batch_launch replays.
+ngdbf_status batch_capture(ngdbf_batch* B) {
+    cudaStream_t cs;
+    cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        cudaError_t le = batch_enqueue(B, cs);
+        e = cudaStreamEndCapture(cs, &B->graph);
+        if (le != cudaSuccess) e = le;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&B->exec, B->graph, 0);
+    cudaStreamDestroy(cs);
+    if (e != cudaSuccess) return cuda_fail(e, "graph capture of the job table");
     return NGDBF_OK;
 }
 
@@ -1099,20 +1232,19 @@ extern "C" ngdbf_status ngdbf_batch_create(const ngdbf_job* jobs, int32_t n_jobs
     B->device = dev;
     B->n_jobs = n_jobs;
     B->sm_count = T.sm_count;
-    B->fn = T.fn;
-    B->smem = T.smem;
-    B->state_in_smem = T.st_smem ? 1 : 0;
-    B->tables_in_smem = T.placement;
-    std::vector<std::pair<int, int>> shapes = T.shapes;
-    int max_bps = 0;
-    for (const auto& sh : shapes) max_bps = std::max(max_bps, sh.second);
-    const size_t grid_max = (size_t)T.sm_count * max_bps;
-    const size_t per_slot_y = (size_t)pad4(T.n_max) * kSlots * held_bytes(T.precision);
-    const size_t per_slot_st = T.state_global ? (size_t)pad4(T.n_max) * kSlots * 2 : 0;
+    ngdbf_status ss = table_shapes(T, jobs, n_jobs, dev, &B->shapes);
+    if (ss != NGDBF_OK) { batch_free(B); return ss; }
+    // scratch for the largest candidate: per CTA the samples (and state) of its symbols
+    size_t grid_max = 0, bytes_y = 0, bytes_st = 0;
+    for (const TableShape& sh : B->shapes) {
+        grid_max = std::max(grid_max, (size_t)sh.grid_max);
+        bytes_y = std::max(bytes_y, (size_t)sh.grid_max * pad4(sh.n_local) * kSlots * held_bytes(T.precision));
+        if (sh.state_global) bytes_st = std::max(bytes_st, (size_t)sh.grid_max * pad4(sh.n_local) * kSlots * 2);
+    }
     const size_t off_jobs = 0, off_thr = align256(sizeof(Job) * n_jobs), off_q = off_thr + align256(T.thr_words * 4);
     const size_t off_first = off_q + align256(8 * (size_t)n_jobs), off_y = off_first + align256(4 * grid_max);
-    const size_t off_st = off_y + align256(grid_max * per_slot_y);
-    const size_t total = off_st + align256(grid_max * per_slot_st);
+    const size_t off_st = off_y + align256(bytes_y);
+    const size_t total = off_st + align256(bytes_st);
     e = cudaMalloc(&B->d_mem, total);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -1121,12 +1253,14 @@ extern "C" ngdbf_status ngdbf_batch_create(const ngdbf_job* jobs, int32_t n_jobs
     }
     B->d_queues = reinterpret_cast<unsigned long long*>(B->d_mem + off_q);
     B->d_first = reinterpret_cast<int32_t*>(B->d_mem + off_first);
+    B->d_st = bytes_st ? B->d_mem + off_st : nullptr;
     // job table and thresholds
     std::vector<Job> hjobs(n_jobs);
     std::vector<uint32_t> hthr(T.thr_words);
     size_t tpos = 0;
     B->frames.resize(n_jobs);
     B->weight.resize(n_jobs);
+    B->n_of_job.resize(n_jobs);
     for (int j = 0; j < n_jobs; ++j) {
         const ngdbf_job& q = jobs[j];
         fill_job(q.code, &q.params, q.y, q.n_frames, q.sigma, q.frame_offset, q.bits, q.iters, q.pass,
@@ -1135,6 +1269,7 @@ extern "C" ngdbf_status ngdbf_batch_create(const ngdbf_job* jobs, int32_t n_jobs
         tpos += (size_t)q.params.t_max + 1;
         B->frames[j] = q.n_frames;
         B->weight[j] = q.n_frames * (int64_t)q.code->n * (q.params.t_max + 1);
+        B->n_of_job[j] = q.code->n;
     }
     e = cudaMemcpy(B->d_mem + off_jobs, hjobs.data(), sizeof(Job) * n_jobs, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(B->d_mem + off_thr, hthr.data(), hthr.size() * 4, cudaMemcpyHostToDevice);
@@ -1145,20 +1280,19 @@ extern "C" ngdbf_status ngdbf_batch_create(const ngdbf_job* jobs, int32_t n_jobs
     A.n_jobs = n_jobs;
     A.first_job = B->d_first;
     A.n_max = T.n_max; A.m_max = T.m_max; A.t_max = T.t_max; A.dv_max = T.dv_max; A.dc_max = T.dc_max;
-    A.placement = T.placement;
     A.yslots = B->d_mem + off_y;
-    A.st_global = per_slot_st ? reinterpret_cast<uint16_t*>(B->d_mem + off_st) : nullptr;
     host_gen_consts(seed, A.G);
-    // launch shape: the largest block by default, or the fastest candidate on this table
-    ngdbf_status s = batch_set_shape(B, shapes[0].first, shapes[0].second);
-    if (s == NGDBF_OK && (flags & NGDBF_BATCH_TUNE) && shapes.size() > 1) {
+    // launch shape: the default, or the fastest candidate on this table (block size x cluster
+    // size x placement of the adjacency tables)
+    ngdbf_status s = batch_set_shape(B, 0);
+    if (s == NGDBF_OK && (flags & NGDBF_BATCH_TUNE) && B->shapes.size() > 1) {
         cudaEvent_t t0, t1;
         cudaEventCreate(&t0);
         cudaEventCreate(&t1);
         float best = 1e30f;
-        std::pair<int, int> best_shape = shapes[0];
-        for (const auto& sh : shapes) {
-            s = batch_set_shape(B, sh.first, sh.second);
+        int best_shape = 0;
+        for (int k = 0; k < (int)B->shapes.size(); ++k) {
+            s = batch_set_shape(B, k);
             if (s != NGDBF_OK) break;
             e = batch_enqueue(B, stream);                    // warm-up
             if (e == cudaSuccess) e = cudaEventRecord(t0, stream);
@@ -1168,28 +1302,49 @@ extern "C" ngdbf_status ngdbf_batch_create(const ngdbf_job* jobs, int32_t n_jobs
             if (e != cudaSuccess) { s = cuda_fail(e, "tuning launch"); break; }
             float ms = 0;
             cudaEventElapsedTime(&ms, t0, t1);
-            if (ms < best) { best = ms; best_shape = sh; }
+            if (ms < best) { best = ms; best_shape = k; }
         }
         cudaEventDestroy(t0);
         cudaEventDestroy(t1);
-        if (s == NGDBF_OK) s = batch_set_shape(B, best_shape.first, best_shape.second);
+        if (s == NGDBF_OK) s = batch_set_shape(B, best_shape);
     }
     if (s != NGDBF_OK) { batch_free(B); return s; }
     if (flags & NGDBF_BATCH_GRAPH) {
-        cudaStream_t cs;
-        e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
-        if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
-        if (e == cudaSuccess) {
-            cudaError_t le = batch_enqueue(B, cs);
-            e = cudaStreamEndCapture(cs, &B->graph);
-            if (le != cudaSuccess) e = le;
-        }
-        if (e == cudaSuccess) e = cudaGraphInstantiate(&B->exec, B->graph, 0);
-        cudaStreamDestroy(cs);
-        if (e != cudaSuccess) { batch_free(B); return cuda_fail(e, "graph capture of the job table"); }
+        s = batch_capture(B);
+        if (s != NGDBF_OK) { batch_free(B); return s; }
     }
     *out = B;
     return NGDBF_OK;
+}
+
+extern "C" ngdbf_status ngdbf_batch_shape(const ngdbf_batch_t* B, int32_t k, int32_t* count, ngdbf_launch_info* info) {
+    if (!B) return fail(NGDBF_ERR_INVALID_ARG, "batch is NULL");
+    if (count) *count = (int32_t)B->shapes.size();
+    if (!info) return NGDBF_OK;
+    if (k < 0) k = B->shape;
+    if (k >= (int32_t)B->shapes.size()) return fail(NGDBF_ERR_INVALID_ARG, "no such shape");
+    const TableShape& sh = B->shapes[k];
+    std::memset(info, 0, sizeof(*info));
+    info->grid = sh.grid_max;
+    info->block = sh.block;
+    info->smem_bytes = sh.smem;
+    info->state_in_smem = sh.st_smem ? 1 : 0;
+    info->kernels = 1;
+    info->sm_count = B->sm_count;
+    info->tables_in_smem = sh.placement;
+    info->cluster = sh.cluster;
+    return NGDBF_OK;
+}
+
+extern "C" ngdbf_status ngdbf_batch_use_shape(ngdbf_batch_t* B, int32_t k) {
+    if (!B) return fail(NGDBF_ERR_INVALID_ARG, "batch is NULL");
+    if (k < 0 || k >= (int32_t)B->shapes.size()) return fail(NGDBF_ERR_INVALID_ARG, "no such shape");
+    const bool graph = B->exec != nullptr;
+    if (B->exec) { cudaGraphExecDestroy(B->exec); B->exec = nullptr; }
+    if (B->graph) { cudaGraphDestroy(B->graph); B->graph = nullptr; }
+    ngdbf_status s = batch_set_shape(B, k);
+    if (s == NGDBF_OK && graph) s = batch_capture(B);
+    return s;
 }
 
 extern "C" ngdbf_status ngdbf_batch_launch(ngdbf_batch_t* B, void* stream_ptr) {
@@ -1202,6 +1357,7 @@ extern "C" ngdbf_status ngdbf_batch_launch(ngdbf_batch_t* B, void* stream_ptr) {
     e = B->exec ? cudaGraphLaunch(B->exec, stream) : batch_enqueue(B, stream);
     if (e != cudaSuccess) return cuda_fail(e, "job table launch");
     set_last_launch(B->grid, B->block, B->smem, B->state_in_smem, B->tables_in_smem, 1, B->sm_count);
+    g_last_launch.cluster = B->cluster;
     return NGDBF_OK;
 }
 

@@ -56,8 +56,23 @@ struct TablePlan {
     std::vector<std::pair<int, int>> shapes;
 };
 ngdbf_status plan_table(const ngdbf_job* jobs, int32_t n_jobs, int dev, TablePlan* out);
+
+// One candidate launch shape of a job table: kernel, block size, cluster size (jobs of at
+// least split_min_n symbols split over a cluster), shared-memory plan (state placement,
+// adjacency tables in shared memory, symbols held per CTA) and the largest resident grid.
+struct TableShape {
+    void* fn = nullptr;
+    int block = 0, cluster = 1, grid_max = 0, smem = 0, placement = 0, n_local = 0, split_min_n = 0;
+    bool st_smem = false, state_global = false;
+};
+// The candidates of a planned table over block size x cluster size x table placement; the
+// first is the default (no cluster, the plan's own placement, the largest block).
+ngdbf_status table_shapes(const TablePlan& T, const ngdbf_job* jobs, int32_t n_jobs, int dev,
+                          std::vector<TableShape>* out);
 // First job of every CTA, in proportion to the estimated work of each job.
 std::vector<int32_t> assign_ctas(const std::vector<int64_t>& frames, const std::vector<int64_t>& weight, int grid);
+std::vector<int32_t> assign_ctas_capped(const std::vector<int64_t>& frames, const std::vector<int64_t>& weight,
+                                        const std::vector<int64_t>& cap, int grid);
 
 }  // namespace host
 }  // namespace ngdbf

@@ -33,6 +33,7 @@
 // generator tables live in shared memory, the adjacency tables there when they fit.
 #pragma once
 
+#include <cooperative_groups.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
@@ -125,10 +126,32 @@ struct MultiArgs {
     const int32_t* first_job;   // [grid]
     int32_t n_max, m_max, t_max, dv_max, dc_max;   // layout maxima over the jobs
     int32_t placement;          // adjacency tables copied into shared memory: kTabChk | kTabSym
-    void* yslots;               // [grid][pad4(n_max)/4][32][4]
-    uint16_t* st_global;        // [grid][pad4(n_max)/4][32][4] when the state is not in shared memory
+    // cluster launches: jobs with n >= split_min_n are split over the `cluster` CTAs of a
+    // cluster (n_local symbols per CTA at most); the per-CTA arrays hold n_local symbols
+    int32_t cluster, split_min_n, n_local;
+    void* yslots;               // [grid][pad4(n_local)/4][32][4]
+    uint16_t* st_global;        // [grid][pad4(n_local)/4][32][4] when the state is not in shared memory
     GenConsts G;
 };
+
+// Symbols one CTA decodes when the `size` CTAs of a cluster share one 32-slot group: [k_lo, k_hi),
+// k_lo a multiple of 32 (size 1: the whole code).  Rank r of C takes chunks of 32 symbols
+// [r nc / C, (r + 1) nc / C) of the nc = ceil(n / 32) chunks.
+struct Split {
+    int rank, size, k_lo, k_hi;
+};
+__host__ __device__ inline Split split_range(int rank, int size, int n) {
+    const int nc = (n + 31) / 32;
+    Split S;
+    S.rank = rank;
+    S.size = size;
+    S.k_lo = 32 * (rank * nc / size);
+    S.k_hi = 32 * ((rank + 1) * nc / size);
+    if (S.k_hi > n) S.k_hi = n;
+    return S;
+}
+// Largest number of symbols a CTA holds when a code of n symbols is split over `size` CTAs.
+__host__ __device__ inline int split_local_max(int n, int size) { return 32 * (((n + 31) / 32 + size - 1) / size); }
 
 struct SmemLayout {
     int32_t off_frame, off_start, off_ctl, off_best, off_trace, off_icdf, off_xw, off_sw, off_cnt, off_thr, off_st,
@@ -145,7 +168,8 @@ struct SmemLayout {
 // (seven words, bit f for slot f) and d_v(k) (32 bytes).  xw has room for whole groups
 // and the zero sentinel word at index n.
 __host__ __device__ inline SmemLayout smem_layout(int n, int m, int t_max, int dv_max, int dc_max,
-                                                  bool need_thr, bool st_smem, int tables) {
+                                                  bool need_thr, bool st_smem, int tables, int n_local = -1) {
+    if (n_local < 0) n_local = n;   // symbols whose counts, state and M(k) rows this CTA holds
     SmemLayout L;
     int o = 0;
     auto take = [&](int bytes, int align) {
@@ -158,16 +182,16 @@ __host__ __device__ inline SmemLayout smem_layout(int n, int m, int t_max, int d
     L.off_frame = take(kSlots * 8, 16);
     L.off_start = take(kSlots * 4, 16);
     L.off_ctl = take(8 * 4, 16);
-    L.off_best = take(kSlots * 8, 16);     // single-bit variant: least (E key, k) per slot
+    L.off_best = take(2 * kSlots * 8, 16); // single-bit variant: least (E key, k) per slot, two rounds
     L.off_trace = take(kSlots * 12, 16);   // objective trace: per slot C (int64), then U (int32)
     L.off_icdf = take(256 * 16, 16);       // inverse normal CDF coefficients
-    L.off_cnt = take(pad4(n) * cnt_bytes, 16);
+    L.off_cnt = take(pad4(n_local) * cnt_bytes, 16);
     L.off_xw = take(pad4(n + 1) * 4, 16);
     L.off_sw = take((m + 1) * (dv_max <= 7 ? 16 : 4), 16);
     L.off_thr = need_thr ? take((t_max + 1) * 4, 16) : -1;
-    L.off_st = st_smem ? take(pad4(n) * kSlots * 2, 16) : -1;
+    L.off_st = st_smem ? take(pad4(n_local) * kSlots * 2, 16) : -1;
     L.off_chk = (tables & kTabChk) ? take(dc_max * m * 2, 16) : -1;
-    L.off_sym = (tables & kTabSym) ? take(n * dv_max * 2 + n, 16) : -1;
+    L.off_sym = (tables & kTabSym) ? take(n_local * dv_max * 2 + n_local, 16) : -1;
     L.total = (o + 15) / 16 * 16;
     return L;
 }
@@ -295,14 +319,39 @@ __device__ __forceinline__ void load_held4(const int8_t* p, int8_t v[4]) {
 // has no unclaimed frame left and every slot of this CTA is idle.  `A` is the job (kernel
 // parameters or a shared-memory copy), `thr_src` its thresholds, `L` the shared-memory
 // layout of the launch, `ys`/`st_cta` this CTA's slot scratch.
-template <bool ADAPT, bool SMOOTH, bool ST_SMEM, bool WIDE, int PREC>
+//
+// Cluster split (CL, S.size > 1): the S.size CTAs of a thread-block cluster decode the same
+// 32 slots, each the symbols [S.k_lo, S.k_hi) (samples, state, counts and M(k) rows of those
+// only), with a full copy of the decision words in every CTA: each computes all syndromes (so
+// the stop vote is the same everywhere), writes the decision words it changes into every
+// copy through distributed shared memory, and rank 0 claims frames for the cluster and
+// writes the slot table into every CTA.  Cluster barriers separate the phases; every CTA
+// takes the same branches (they depend only on the vote and the slot table), so all of them
+// reach every barrier.
+template <bool ADAPT, bool SMOOTH, bool ST_SMEM, bool WIDE, int PREC, bool CL = false>
 __device__ __forceinline__ void decode_job(const Job& A, const uint32_t* thr_src, const GenConsts& G,
                                            const SmemLayout& L, int tables,
-                                           typename Held<PREC>::T* ys, uint16_t* st_cta) {
+                                           typename Held<PREC>::T* ys, uint16_t* st_cta,
+                                           Split S = Split{0, 1, 0, 0}) {
     constexpr bool kState = ADAPT || SMOOTH;
     using HeldT = typename Held<PREC>::T;
     extern __shared__ __align__(16) unsigned char smem[];
     const int n = A.n, m = A.m, T = A.t_max, dv_max = A.dv_max, dc_max = A.dc_max;
+    const bool split = CL && S.size > 1;
+    const int k_lo = split ? S.k_lo : 0, k_hi = split ? S.k_hi : n;   // this CTA's symbols
+    const int nl = k_hi - k_lo;
+    // barrier over the CTAs that share the slots (the cluster when split, else this CTA)
+    auto group_sync = [&]() {
+        if constexpr (CL) {
+            if (split) {
+                cooperative_groups::this_cluster().sync();
+                return;
+            }
+        }
+        __syncthreads();
+    };
+    // the same shared-memory word in another CTA of the cluster
+    auto peer = [&](auto* p, int r) { return cooperative_groups::this_cluster().map_shared_rank(p, r); };
     long long* lane_frame = reinterpret_cast<long long*>(smem + L.off_frame);
     int32_t* lane_start = reinterpret_cast<int32_t*>(smem + L.off_start);
     uint32_t* ctl = reinterpret_cast<uint32_t*>(smem + L.off_ctl);
@@ -327,13 +376,15 @@ __device__ __forceinline__ void decode_job(const Job& A, const uint32_t* thr_src
         for (int i = tid; i < dc_max * m; i += blockDim.x) c[i] = A.chk_cols[i];
         chk_cols = c;
     }
+    int sym_base = 0;           // first symbol of the M(k) rows sym_chks points to
     if (tables & kTabSym) {
         uint16_t* s = reinterpret_cast<uint16_t*>(smem + L.off_sym);
-        uint8_t* d = reinterpret_cast<uint8_t*>(s + n * dv_max);
-        for (int i = tid; i < n * dv_max; i += blockDim.x) s[i] = A.sym_chks[i];
-        for (int i = tid; i < n; i += blockDim.x) d[i] = A.sym_deg[i];
+        uint8_t* d = reinterpret_cast<uint8_t*>(s + nl * dv_max);
+        for (int i = tid; i < nl * dv_max; i += blockDim.x) s[i] = A.sym_chks[k_lo * dv_max + i];
+        for (int i = tid; i < nl; i += blockDim.x) d[i] = A.sym_deg[k_lo + i];
         sym_chks = s;
         sym_deg = d;
+        sym_base = k_lo;
     }
 
     // ---- set-up: generator table, zero the state, sentinels, thresholds, first 32 frames ----
@@ -343,10 +394,12 @@ __device__ __forceinline__ void decode_job(const Job& A, const uint32_t* thr_src
     if constexpr (ADAPT)
         for (int u = tid; u <= T; u += blockDim.x) thr[u] = thr_src[u];
     if constexpr (kState)
-        for (int e = tid; e < pad4(n) * kSlots; e += blockDim.x) st[e] = 0;
-    if (tid < kSlots) best[tid] = ~0ull;
-    if (tid == 0) {
+        for (int e = tid; e < pad4(nl) * kSlots; e += blockDim.x) st[e] = 0;
+    if (tid < 2 * kSlots) best[tid] = ~0ull;
+    if (tid == 0)
         for (int c = 0; c < 8; ++c) ctl[c] = 0u;
+    if (split) group_sync();        // every copy cleared before rank 0 writes the slot table
+    if (tid == 0 && (!split || S.rank == 0)) {
         const unsigned long long base = atomicAdd(A.queue, (unsigned long long)kSlots);
         uint32_t live = 0;
         for (int f = 0; f < kSlots; ++f) {
@@ -361,8 +414,22 @@ __device__ __forceinline__ void decode_job(const Job& A, const uint32_t* thr_src
         }
         ctl[2] = live;
         ctl[3] = live;
+        if constexpr (CL) {
+            for (int r = 0; split && r < S.size; ++r) {
+                if (r == S.rank) continue;
+                long long* pf = peer(lane_frame, r);
+                int32_t* ps = peer(lane_start, r);
+                uint32_t* pc = peer(ctl, r);
+                for (int f = 0; f < kSlots; ++f) {
+                    pf[f] = lane_frame[f];
+                    ps[f] = 0;
+                }
+                pc[2] = live;
+                pc[3] = live;
+            }
+        }
     }
-    __syncthreads();
+    group_sync();
 
     int round = 0;   // flip phases executed by this CTA; slot f is at t = round - lane_start[f]
     int pass_id = 0;
@@ -371,7 +438,7 @@ __device__ __forceinline__ void decode_job(const Job& A, const uint32_t* thr_src
         if (refill) {
             // ---- load new frames: saturated samples into the slot columns, x(0) = sign(y) ----
             const uint32_t fresh = ctl[3];
-            for (int k = tid; k < n; k += blockDim.x) {
+            for (int k = k_lo + tid; k < k_hi; k += blockDim.x) {
                 uint32_t word = xw[k] & ~fresh;
                 uint32_t rest = fresh;
                 while (rest) {
@@ -383,7 +450,7 @@ __device__ __forceinline__ void decode_job(const Job& A, const uint32_t* thr_src
                         if (v < -A.y_max) v = -A.y_max;
                     }
                     bool negative;
-                    const int at = gidx(k, f);
+                    const int at = gidx(k - k_lo, f);
                     if constexpr (PREC == kFP32) {
                         ys[at] = v;
                         negative = !(v >= 0.0f);
@@ -400,8 +467,12 @@ __device__ __forceinline__ void decode_job(const Job& A, const uint32_t* thr_src
                     if constexpr (kState) st[at] = 0;
                 }
                 xw[k] = word;
+                if constexpr (CL) {
+                    for (int r = 0; split && r < S.size; ++r)
+                        if (r != S.rank) peer(xw, r)[k] = word;
+                }
             }
-            __syncthreads();
+            group_sync();
             refill = false;
         }
 
@@ -443,9 +514,10 @@ __device__ __forceinline__ void decode_job(const Job& A, const uint32_t* thr_src
         if (fin) {
             // ---- B. outputs of finished slots ----
             const int nfin = __popc(fin);
-            const int work = nfin * A.nb;
+            const int b_lo = k_lo >> 3, nbl = ((k_hi + 7) >> 3) - b_lo;   // this CTA's output bytes
+            const int work = nfin * nbl;
             for (int idx = tid; idx < work; idx += blockDim.x) {
-                const int j = idx / A.nb, b = idx - j * A.nb;
+                const int j = idx / nbl, b = b_lo + (idx - j * nbl);
                 const int f = nth_set_bit(fin, j);
                 const bool ok = (conv >> f) & 1u;
                 const int tf = round - lane_start[f];
@@ -459,7 +531,7 @@ __device__ __forceinline__ void decode_job(const Job& A, const uint32_t* thr_src
                             if (!ok) {
                                 // X_k = terms - 2 * (#-1 decisions), x(T) included here
                                 const int terms = tf - A.t_smooth + 1;
-                                const int neg = (int)(st[gidx(k, f)] >> kCShift) + (int)bit;
+                                const int neg = (int)(st[gidx(k - k_lo, f)] >> kCShift) + (int)bit;
                                 const int X = terms - 2 * neg;
                                 bit = X < 0 ? 1u : (X > 0 ? 0u : bit);
                             }
@@ -469,16 +541,16 @@ __device__ __forceinline__ void decode_job(const Job& A, const uint32_t* thr_src
                 }
                 A.bits[(size_t)lane_frame[f] * A.nb + b] = (uint8_t)byte;
             }
-            if (tid < nfin) {
+            if (tid < nfin && (!split || S.rank == 0)) {
                 const int f = nth_set_bit(fin, tid);
                 const bool ok = (conv >> f) & 1u;
                 const long long fr = lane_frame[f];
                 A.iters[fr] = ok ? round - lane_start[f] : T;
                 A.pass[fr] = ok ? 1 : 0;
             }
-            __syncthreads();
+            group_sync();           // every CTA is done with the finished slots' table entries
             // ---- claim new frames for the finished slots ----
-            if (tid == 0) {
+            if (tid == 0 && (!split || S.rank == 0)) {
                 uint32_t fresh = 0;
                 const unsigned long long base = atomicAdd(A.queue, (unsigned long long)nfin);
                 for (int j = 0; j < nfin; ++j) {
@@ -494,8 +566,23 @@ __device__ __forceinline__ void decode_job(const Job& A, const uint32_t* thr_src
                 }
                 ctl[2] = (live & ~fin) | fresh;
                 ctl[3] = fresh;
+                if constexpr (CL) {
+                    for (int r = 0; split && r < S.size; ++r) {
+                        if (r == S.rank) continue;
+                        long long* pf = peer(lane_frame, r);
+                        int32_t* ps = peer(lane_start, r);
+                        uint32_t* pc = peer(ctl, r);
+                        for (int j = 0; j < nfin; ++j) {
+                            const int f = nth_set_bit(fin, j);
+                            pf[f] = lane_frame[f];
+                            ps[f] = lane_start[f];
+                        }
+                        pc[2] = ctl[2];
+                        pc[3] = ctl[3];
+                    }
+                }
             }
-            __syncthreads();
+            group_sync();
             live = ctl[2];
             if (ctl[3]) {
                 refill = true;      // new frames need their t = 0 syndrome test first
@@ -505,8 +592,9 @@ __device__ __forceinline__ void decode_job(const Job& A, const uint32_t* thr_src
         if (live == 0) break;
 
         // ---- A'. per symbol and slot, the count of unsatisfied checks in M(k) ----
-        for (int k = tid; k < n; k += blockDim.x) {
-            const uint16_t* row = sym_chks + k * dv_max;
+        for (int k = k_lo + tid; k < k_hi; k += blockDim.x) {
+            const int kk = k - k_lo;                      // local index of the symbol
+            const uint16_t* row = sym_chks + (k - sym_base) * dv_max;
             if constexpr (!WIDE) {
                 // d_v <= 7: one 4-bit lane per slot, counts added lane-wise without carries;
                 // stored as S_k + 8 = d_v + 8 - 2 count in [1, 15]
@@ -516,8 +604,8 @@ __device__ __forceinline__ void decode_job(const Job& A, const uint32_t* thr_src
                     const uint4 s = sw4[row[e]];
                     c.x += s.x; c.y += s.y; c.z += s.z; c.w += s.w;
                 }
-                const uint32_t D = ((uint32_t)sym_deg[k] + 8u) * 0x11111111u;
-                uint32_t* cw = reinterpret_cast<uint32_t*>(cnt) + ((k >> 2) << 4) + (k & 3);
+                const uint32_t D = ((uint32_t)sym_deg[k - sym_base] + 8u) * 0x11111111u;
+                uint32_t* cw = reinterpret_cast<uint32_t*>(cnt) + ((kk >> 2) << 4) + (kk & 3);
                 cw[0] = D - 2u * c.x;     // quarter q of the group at word 4 q + k % 4
                 cw[4] = D - 2u * c.y;
                 cw[8] = D - 2u * c.z;
@@ -533,8 +621,8 @@ __device__ __forceinline__ void decode_job(const Job& A, const uint32_t* thr_src
                         carry = c;
                     }
                 }
-                cnt[2 * k] = make_uint4(b[0], b[1], b[2], b[3]);
-                cnt[2 * k + 1] = make_uint4(b[4], b[5], b[6], (uint32_t)sym_deg[k]);
+                cnt[2 * kk] = make_uint4(b[0], b[1], b[2], b[3]);
+                cnt[2 * kk + 1] = make_uint4(b[4], b[5], b[6], (uint32_t)sym_deg[k - sym_base]);
             }
         }
         __syncthreads();
@@ -547,7 +635,7 @@ __device__ __forceinline__ void decode_job(const Job& A, const uint32_t* thr_src
             const uint32_t flo = (uint32_t)fid, fhi = (uint32_t)(fid >> 32);
             const int t = act ? round - lane_start[lane] : 0;
             const bool window = SMOOTH && act && t >= A.t_smooth;
-            const int groups = (n + 3) >> 2;
+            const int g_lo = k_lo >> 2;              // first group of this CTA's symbols
             const uint32_t th0 = thr_src[0];    // threshold of the non-adaptive variants
             const float scale = A.scale, wgt = A.w, fix_R = A.fix_R, acc_R = A.acc_R;
             const int32_t fix_kmax = A.fix_kmax, fix_W = A.fix_W, acc_W = A.acc_W;
@@ -558,10 +646,11 @@ __device__ __forceinline__ void decode_job(const Job& A, const uint32_t* thr_src
             unsigned long long my_best = ~0ull;      // single-bit variant: (E key << 32) | k
             // one group of four symbols; only the last group of a code with n % 4 != 0 is partial
             // (its missing symbols read the zeroed padding and are skipped)
-            auto group = [&](const int g, auto partial_tag) {
+            auto group = [&](const int gl, auto partial_tag) {
                 constexpr bool kPartial = decltype(partial_tag)::value;
+                const int g = g_lo + gl;                  // group index in the code (Philox counter)
                 const int k0 = 4 * g;
-                const int at = (g * kSlots + lane) * 4;   // this lane's entries in the group layout
+                const int at = (gl * kSlots + lane) * 4;  // this lane's entries in the group layout
                 // issue the sample, state, count, decision-word and threshold loads (one vector
                 // each) before the generator's arithmetic, so that their latency overlaps it
                 HeldT yv[4];
@@ -572,7 +661,7 @@ __device__ __forceinline__ void decode_job(const Job& A, const uint32_t* thr_src
                     sv[0] = s2.x & 0xFFFFu; sv[1] = s2.x >> 16; sv[2] = s2.y & 0xFFFFu; sv[3] = s2.y >> 16;
                 }
                 if constexpr (!WIDE) {
-                    const uint4 c4 = reinterpret_cast<const uint4*>(cnt)[g * 4 + (lane >> 3)];
+                    const uint4 c4 = reinterpret_cast<const uint4*>(cnt)[gl * 4 + (lane >> 3)];
                     cwv[0] = c4.x; cwv[1] = c4.y; cwv[2] = c4.z; cwv[3] = c4.w;
                 }
                 const uint4 x4 = reinterpret_cast<const uint4*>(xw)[g];
@@ -603,7 +692,7 @@ __device__ __forceinline__ void decode_job(const Job& A, const uint32_t* thr_src
                         S = (int)nib - 8;
                         ws = __fmaf_rn(wgt, __uint2float_rn(nib), wgt_m8);
                     } else {
-                        const uint4 c = cnt[2 * k], d = cnt[2 * k + 1];
+                        const uint4 c = cnt[2 * (k - k_lo)], d = cnt[2 * (k - k_lo) + 1];
                         const int unsat_cnt = (int)(((c.x >> lane) & 1u) | (((c.y >> lane) & 1u) << 1) |
                                                     (((c.z >> lane) & 1u) << 2) | (((c.w >> lane) & 1u) << 3) |
                                                     (((d.x >> lane) & 1u) << 4) | (((d.y >> lane) & 1u) << 5) |
@@ -698,28 +787,48 @@ __device__ __forceinline__ void decode_job(const Job& A, const uint32_t* thr_src
                         *reinterpret_cast<uint2*>(st + at) = n2;
                 }
                 // Step 3b flips of the group (the single-bit variant flips after the sweep)
-                if (lane == 0 && !single)
-                    reinterpret_cast<uint4*>(xw)[g] = make_uint4(xwv[0] ^ fmv[0], xwv[1] ^ fmv[1], xwv[2] ^ fmv[2],
-                                                                 xwv[3] ^ fmv[3]);
+                if (lane == 0 && !single) {
+                    const uint4 nw = make_uint4(xwv[0] ^ fmv[0], xwv[1] ^ fmv[1], xwv[2] ^ fmv[2], xwv[3] ^ fmv[3]);
+                    reinterpret_cast<uint4*>(xw)[g] = nw;
+                    if constexpr (CL) {
+                        for (int r = 0; split && r < S.size; ++r)
+                            if (r != S.rank) reinterpret_cast<uint4*>(peer(xw, r))[g] = nw;
+                    }
+                }
             };
-            const int full = n >> 2;
-            for (int g = warp; g < full; g += nwarps) group(g, std::false_type{});
-            if (full < groups && warp == full % nwarps) group(full, std::true_type{});
+            const int full = nl >> 2, groups_l = (nl + 3) >> 2;   // only the code's last group can be partial
+            for (int gl = warp; gl < full; gl += nwarps) group(gl, std::false_type{});
+            if (full < groups_l && warp == full % nwarps) group(full, std::true_type{});
             if constexpr (!ADAPT) {
-                if (single && act) atomicMin(best + lane, my_best);
+                // the least (E key, k) of each slot over this CTA's symbols; when split, in the
+                // buffer of this round's parity (the CTAs of the cluster read each other's)
+                unsigned long long* bcur = best + (split ? (round & 1) * kSlots : 0);
+                if (single && act) atomicMin(bcur + lane, my_best);
             }
         }
         if constexpr (!ADAPT) {
             if (!ADAPT && A.single) {
-                __syncthreads();
-                // each live slot flips its least-E_k symbol (the lowest k among equal values)
+                group_sync();
+                // each live slot flips its least-E_k symbol (the lowest k among equal values), in
+                // every copy of the decision words
+                unsigned long long* bcur = best + (split ? (round & 1) * kSlots : 0);
                 if (tid < kSlots) {
-                    if ((live >> tid) & 1u) atomicXor(xw + (uint32_t)best[tid], 1u << tid);
-                    best[tid] = ~0ull;
+                    unsigned long long b = bcur[tid];
+                    if constexpr (CL) {
+                        for (int r = 0; split && r < S.size; ++r) {
+                            if (r == S.rank) continue;
+                            const unsigned long long o = *peer(bcur + tid, r);
+                            b = o < b ? o : b;
+                        }
+                    }
+                    if ((live >> tid) & 1u) atomicXor(xw + (uint32_t)b, 1u << tid);
+                    // clear the buffer of the next round (when split, the other CTAs finished
+                    // reading it before the previous round's closing barrier)
+                    best[(split ? ((round + 1) & 1) * kSlots : 0) + tid] = ~0ull;
                 }
             }
         }
-        __syncthreads();
+        group_sync();
         ++round;
     }
 }

@@ -72,8 +72,23 @@ void* multi_kernel_fn(int variant, int precision, bool st_smem, bool wide) {
 }
 
 cudaError_t launch_multi(void* fn, const MultiArgs& args, int grid, int block, int smem, cudaStream_t stream) {
-    reinterpret_cast<MultiFn>(fn)<<<grid, block, smem, stream>>>(args);
-    return cudaGetLastError();
+    if (args.cluster <= 1) {
+        reinterpret_cast<MultiFn>(fn)<<<grid, block, smem, stream>>>(args);
+        return cudaGetLastError();
+    }
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)args.cluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)block);
+    cfg.dynamicSmemBytes = (size_t)smem;
+    cfg.stream = stream;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, reinterpret_cast<MultiFn>(fn), args);
 }
 
 }  // namespace ngdbf

@@ -75,7 +75,7 @@ class ngdbf_host_stats(ctypes.Structure):
 class ngdbf_launch_info(ctypes.Structure):
     _fields_ = [("grid", ctypes.c_int32), ("block", ctypes.c_int32), ("smem_bytes", ctypes.c_int32),
                 ("state_in_smem", ctypes.c_int32), ("kernels", ctypes.c_int32),
-                ("sm_count", ctypes.c_int32), ("tables_in_smem", ctypes.c_int32)]
+                ("sm_count", ctypes.c_int32), ("tables_in_smem", ctypes.c_int32), ("cluster", ctypes.c_int32)]
 
 
 def make_params(w=0.75, theta=-0.9, eta=0.96, lam=1.0, y_max=2.5, t_max=100, smooth_window=64,
@@ -112,6 +112,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.ngdbf_batch_create.argtypes = [ctypes.POINTER(ngdbf_job), ctypes.c_int32, ctypes.c_uint64,
                                        ctypes.c_int32, vp, ctypes.POINTER(vp)]
     lib.ngdbf_batch_launch.argtypes = [vp, vp]
+    lib.ngdbf_batch_shape.argtypes = [vp, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ngdbf_launch_info)]
+    lib.ngdbf_batch_use_shape.argtypes = [vp, ctypes.c_int32]
     lib.ngdbf_batch_destroy.argtypes = [vp]
     lib.ngdbf_server_create.argtypes = [ctypes.c_size_t, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64,
                                         ctypes.POINTER(vp)]
@@ -135,7 +137,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
                "ngdbf_batch_launch", "ngdbf_batch_destroy", "ngdbf_server_create", "ngdbf_server_submit",
                "ngdbf_server_poll", "ngdbf_server_wait", "ngdbf_server_get_stats", "ngdbf_server_destroy",
                "ngdbf_gaussian_range", "ngdbf_pool_usage", "ngdbf_last_host_stats", "ngdbf_mix_probe",
-               "ngdbf_generator_table"):
+               "ngdbf_generator_table", "ngdbf_batch_shape", "ngdbf_batch_use_shape"):
         getattr(lib, fn).restype = ctypes.c_int
     if path is None:
         _lib = lib
@@ -227,6 +229,20 @@ def ngdbf_batch_create(jobs, seed: int, flags: int = 0, stream: int = 0) -> int:
 def ngdbf_batch_launch(batch: int, stream: int = 0) -> None:
     lib = load()
     _check(lib, lib.ngdbf_batch_launch(batch, stream))
+
+
+def ngdbf_batch_shape(batch: int, k: int = -1) -> tuple[int, dict]:
+    """(number of candidate shapes, description of candidate k; k < 0: the shape in use)."""
+    lib = load()
+    cnt = ctypes.c_int32()
+    info = ngdbf_launch_info()
+    _check(lib, lib.ngdbf_batch_shape(batch, k, ctypes.byref(cnt), ctypes.byref(info)))
+    return cnt.value, {f: getattr(info, f) for f, _ in info._fields_}
+
+
+def ngdbf_batch_use_shape(batch: int, k: int) -> None:
+    lib = load()
+    _check(lib, lib.ngdbf_batch_use_shape(batch, k))
 
 
 def ngdbf_batch_destroy(batch: int) -> None:
@@ -423,6 +439,17 @@ class Batch:
         s = stream if stream is not None else torch.cuda.current_stream()
         ngdbf_batch_launch(self.handle, s.cuda_stream)
         return self.outputs
+
+    def shapes(self) -> list[dict]:
+        """The candidate launch shapes (block, cluster, placement, ...)."""
+        n, _ = ngdbf_batch_shape(self.handle, 0)
+        return [ngdbf_batch_shape(self.handle, k)[1] for k in range(n)]
+
+    def shape(self) -> dict:
+        return ngdbf_batch_shape(self.handle, -1)[1]
+
+    def use_shape(self, k: int) -> None:
+        ngdbf_batch_use_shape(self.handle, k)
 
     def close(self):
         if self.handle:

@@ -136,3 +136,71 @@ def test_mixed_variants_are_rejected():
         ngdbf.Batch([(dc, y, 0.5, ngdbf.make_params(variant=0), 0), (dc, y, 0.5, ngdbf.make_params(variant=1), 0)])
     assert e.value.status == ngdbf.NGDBF_ERR_UNSUPPORTED
     dc.close()
+
+
+def _table_every_shape(O, specs, variant, precision=ngdbf.NGDBF_FP32, q_bits=0, seed=3, min_cluster=2):
+    """Decodes the table under every candidate launch shape; each result must equal one
+    ngdbf_decode per job bit for bit (and, for a sample of frames, the reference decoder)."""
+    jobs = make_jobs(specs, variant, precision, q_bits)
+    dcs = [ngdbf.DeviceCode.from_code(j["code"]) for j in jobs]
+    ys = [torch.from_numpy(j["y"]).cuda() for j in jobs]
+    try:
+        b = ngdbf.Batch([(dc, y, j["sigma"], j["gp"], j["off"]) for dc, y, j in zip(dcs, ys, jobs)],
+                        seed=seed, flags=ngdbf.NGDBF_BATCH_GRAPH)
+        single = [tuple(t.cpu().numpy() for t in dc.decode(y, j["sigma"], j["gp"], seed=seed,
+                                                          frame_offset=j["off"]))
+                  for dc, y, j in zip(dcs, ys, jobs)]
+        shapes = b.shapes()
+        clusters = sorted({sh["cluster"] for sh in shapes})
+        assert max(clusters) >= min_cluster, shapes
+        for k, sh in enumerate(shapes):
+            b.use_shape(k)
+            outs = b.launch()
+            torch.cuda.synchronize()
+            for jn, (o, ref) in enumerate(zip(outs, single)):
+                got = tuple(t.cpu().numpy() for t in o)
+                for a, c, name in zip(got, ref, ("bits", "iters", "pass")):
+                    assert np.array_equal(a, c), f"shape {sh}, job {jn}: {name} differ"
+            assert b.shape()["cluster"] == sh["cluster"]
+        b.close()
+    finally:
+        for dc in dcs:
+            dc.close()
+    # the per-job decodes themselves against the reference decoder on a few frames
+    for j, ref in zip(jobs, single):
+        F = min(24, j["y"].shape[0])
+        ob, oi, ops = O.decode_f32(j["code"], j["y"][:F], j["sigma"], j["op"], seed=seed, frame_offset=j["off"],
+                                   threads=THREADS)
+        assert np.array_equal(ob, ref[0][:F]) and np.array_equal(oi, ref[1][:F]) and np.array_equal(ops, ref[2][:F])
+    return clusters
+
+
+def _cluster_specs():
+    return [(wl.peg_code(504, 252, 3, seed=1), 70, 3.0, 120, -0.9, 0.99, 0.75, 0.95, 61, 0),
+            (wl.peg_code(2048, 384, 6, seed=1), 90, 3.75, 150, -0.7, 0.993, 0.1875, 0.65, 62, 10 ** 6),
+            (wl.peg_code(4096, 2048, 4, seed=1), 40, 2.5, 100, -0.9, 0.98, 0.75, 0.7, 63, 5),
+            (wl.peg_code(8192, 1639, 3, seed=1), 50, 3.0, 120, -0.7, 0.99, 0.5, 0.8, 64, 77)]
+
+
+@pytest.mark.parametrize("variant", [3, 0, 2, 6, 4, 3 | ngdbf.NGDBF_UNIFORM])
+def test_cluster_split_every_shape(O, variant):
+    """Codes of 2048 symbols or more split over thread-block clusters of 2, 4 and 8 CTAs (the
+    decision words exchanged through distributed shared memory), smaller ones decoded CTA by CTA,
+    every placement and block size: identical to one ngdbf_decode per job."""
+    clusters = _table_every_shape(O, _cluster_specs(), variant)
+    assert clusters[0] == 1
+
+
+@pytest.mark.parametrize("precision,q_bits", [(ngdbf.NGDBF_FP16, 0), (ngdbf.NGDBF_FIXACC, 8)])
+def test_cluster_split_precisions(O, precision, q_bits):
+    _table_every_shape(O, _cluster_specs()[1:3], 3, precision, q_bits)
+
+
+def test_cluster_split_ragged_code():
+    """A split code whose length is not a multiple of 32 (the last CTA's range ends mid-group)."""
+    H = wl.peg_code(2600, 1300, 3, seed=2).dense()[:, :2598]
+    H = H[H.sum(axis=1) > 0]
+    code = wl.code_from_dense(H)
+    O = oracle.load()
+    _table_every_shape(O, [(code, 75, 2.5, 90, -0.9, 0.99, 0.75, 0.95, 65, 3),
+                           (wl.peg_code(96, 48, 3, seed=11), 40, 2.5, 60, -0.9, 0.99, 0.75, 0.95, 66, 0)], 3)
