@@ -186,6 +186,22 @@ ngdbf_status ngdbf_decode_trace(const ngdbf_code_t* code, const float* y, int64_
                                 int64_t* trace_corr, void* stream);
 
 /*
+ * The plain per-iteration form of the same decode (the baseline the persistent kernels are
+ * measured against): per iteration t one launch forms the syndromes of every active frame
+ * (Step 1, one thread per frame and check, one byte per decision), one retires the frames
+ * that satisfy every check or reached T (outputs as ngdbf_decode's), and one runs Step 2 and
+ * Step 3b for every symbol of the active frames (one thread per frame and four symbols) --
+ * 3 T + 3 launches with the initializing one, no bit-slicing, no persistent slots.  Same
+ * arguments, layouts and results as ngdbf_decode (bit for bit).  FP32 and the multi-bit variants only (NGDBF_SINGLE
+ * and other precisions: NGDBF_ERR_UNSUPPORTED).  Scratch (about 6 n + m bytes per frame)
+ * comes from the library's pool.
+ */
+ngdbf_status ngdbf_decode_plain(const ngdbf_code_t* code, const float* y, int64_t n_frames,
+                                float sigma, const ngdbf_params* params, uint64_t seed,
+                                uint64_t frame_offset, uint8_t* bits, int32_t* iters,
+                                uint8_t* pass, void* stream);
+
+/*
  * Same decode with HOST buffers, synchronous: copies y to the device in
  * chunks on two streams, decodes each chunk as soon as it has arrived while
  * the next chunk is copied, copies the outputs back, and returns when the
@@ -309,36 +325,37 @@ ngdbf_status ngdbf_batch_launch(ngdbf_batch_t* batch, void* stream);
 ngdbf_status ngdbf_batch_destroy(ngdbf_batch_t* batch);
 
 /*
- * Serving loop (continuous batching).  A server owns a scheduler thread, a set
- * of streams and a device-memory budget.  Requests -- a code, HOST samples,
- * sigma, params, a frame offset and HOST output buffers -- may be submitted at
- * any time from any thread.  The scheduler admits pending requests in arrival
- * order while the device memory they need (samples, outputs, and the slot
- * scratch and job table of their launch) fits the budget beside the launches
- * already running, packs the admitted requests into one job-table launch
- * (copy in, decode, copy out) on a free stream, and retires a launch when its
- * stream passes it, which returns its memory for the next requests.  Launches
- * on different streams overlap on the device: the CTAs of a persistent launch
- * exit as its frames finish and the next launch's CTAs take those SMs.  Each
- * request's result equals ngdbf_decode's for the same job, alone or in any
- * mix.  Requests packed together share variant and precision; the seed of the
- * perturbation is the server's.  Page-locked host buffers let the copies run
+ * Serving loop (continuous batching).  A server owns a scheduler thread, copy streams, a
+ * device-memory budget and one resident persistent kernel.  Requests -- a code, HOST samples,
+ * sigma, params, a frame offset and HOST output buffers -- may be submitted at any time from
+ * any thread.  In arrival order, while the device memory they need (samples, outputs,
+ * thresholds, and the resident kernel's scratch) fits the budget, the scheduler copies a
+ * request in and publishes it into a ring of job descriptors the GPU reads.  The resident
+ * kernel's CTAs take the oldest published request with frames left whenever their own is
+ * exhausted, so requests that arrive while others run join the running launch and their work
+ * overlaps on the device; inside a request, converged frames free their slots at once.  When
+ * a request's last frame is done its outputs are copied back and its memory returns to the
+ * budget.  Idle CTAs exit after a few milliseconds; the kernel is launched again when work is
+ * published.  A request of another variant or precision, or whose code needs a larger
+ * shared-memory layout, than the running kernel waits until that kernel drains.  Each
+ * request's result equals ngdbf_decode's for the same job, alone or in any mix; the seed of
+ * the perturbation is the server's.  Page-locked host buffers let the copies run
  * asynchronously; with pageable ones the scheduler thread blocks on each copy.
  */
 typedef struct ngdbf_server ngdbf_server_t;
 
 typedef struct ngdbf_server_stats {
     int64_t submitted, completed, failed;
-    int64_t launches;                 /* job-table launches issued */
+    int64_t launches;                 /* launches of the resident kernel */
     int64_t frames;                   /* frames of completed requests */
-    int64_t peak_bytes_in_use;        /* largest device memory held by running launches */
-    int32_t peak_concurrent_launches; /* most launches in flight at once */
-    int32_t reserved;
+    int64_t peak_bytes_in_use;        /* most device memory held at once (requests + kernel scratch) */
+    int32_t peak_requests_on_device;  /* most requests published and not yet complete at once */
+    int32_t admitted_into_running;    /* requests published while the kernel was already running */
 } ngdbf_server_stats;
 
-/* device_budget_bytes: device memory the running launches may hold together;
- * max_inflight_launches: 1..16 streams; max_jobs_per_launch: 1..4096 requests
- * packed into one launch. */
+/* device_budget_bytes: device memory the server may hold; max_inflight_launches: 1..16 copy
+ * streams; max_jobs_per_launch: 1..4096, the most requests on the device at once (at most
+ * 1024 are used). */
 ngdbf_status ngdbf_server_create(size_t device_budget_bytes, int32_t max_inflight_launches,
                                  int32_t max_jobs_per_launch, uint64_t seed, ngdbf_server_t** out);
 

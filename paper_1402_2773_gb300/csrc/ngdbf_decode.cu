@@ -327,6 +327,27 @@ ngdbf_status choose_placement(int dev, int n, int m, int t_max, int dv_max, int 
     return NGDBF_OK;
 }
 
+ngdbf_status plan_smem(int dev, int n, int m, int t_max, int dv_max, int dc_max, bool adapt, bool state,
+                       const void* fn_st, const void* fn_nost, SmemPlan* out) {
+    int smem_optin = 0;
+    cudaError_t e = cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
+    cudaFuncAttributes fa;
+    e = cudaFuncGetAttributes(&fa, fn_nost);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncGetAttributes");
+    PlacementChoice pc;
+    ngdbf_status s = choose_placement(dev, n, m, t_max, dv_max, dc_max, adapt, state,
+                                      smem_optin - (int)fa.sharedSizeBytes,
+                                      [&](bool st) { return st ? fn_st : fn_nost; }, &pc);
+    if (s != NGDBF_OK) return s;
+    out->st_smem = pc.st_smem;
+    out->placement = pc.placement;
+    out->block = pc.block;
+    out->bps = pc.bps;
+    out->smem = pc.L.total;
+    return NGDBF_OK;
+}
+
 ngdbf_status plan_launch(const ngdbf_code* C, const ngdbf_params* P, int64_t n_frames, int dev,
                          LaunchPlan* plan, KernelFn* fn_out, int* sm_count_out) {
     int sm_count = 0, smem_optin = 0, smem_per_sm = 0;

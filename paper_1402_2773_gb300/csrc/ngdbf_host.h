@@ -39,6 +39,14 @@ void host_gen_consts(uint64_t seed, GenConsts& G);
 // Bytes of one held sample of a precision.
 size_t held_bytes(int precision);
 ngdbf_status check_params(const ngdbf_params* P, float sigma);
+// Shared-memory plan of a kernel of the slot loop for the given maxima: per-slot state in
+// shared memory when it fits (fn_st) else global (fn_nost), adjacency tables, block size.
+struct SmemPlan {
+    bool st_smem;
+    int placement, block, bps, smem;
+};
+ngdbf_status plan_smem(int dev, int n, int m, int t_max, int dv_max, int dc_max, bool adapt, bool state,
+                       const void* fn_st, const void* fn_nost, SmemPlan* out);
 // Job fields and its threshold words thr[0..t_max].
 void fill_job(const ngdbf_code* C, const ngdbf_params* P, const float* y, int64_t n_frames, float sigma,
               uint64_t frame_offset, uint8_t* bits, int32_t* iters, uint8_t* pass,

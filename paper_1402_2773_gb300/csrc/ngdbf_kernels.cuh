@@ -105,7 +105,36 @@ struct Job {
     long long* trace_c;
     long long trace_frames;
     double trace_yunit;         // FIX / FIXACC: value of one half level, Y_max 2^-Q
+    // serving (0 / nullptr otherwise): `queue` holds (gen << 32) | frames claimed and claims
+    // check the generation, so a CTA still holding an earlier job of the same ring slot never
+    // takes frames of a later one; the CTA that finishes the last frame counts it in `done` and
+    // writes `gen` into the host-visible word `notify`
+    uint32_t gen;
+    unsigned int* done;
+    unsigned int* notify;
 };
+
+// Claims up to k consecutive frames of job A: returns true and the first frame id in *base
+// (ids at or beyond A.n_frames mean no frame), or false when none is left.  Serving jobs
+// (A.gen != 0) claim by compare-and-swap within their generation, at most kClaimTries times.
+constexpr int kClaimTries = 4096;
+__device__ __forceinline__ bool claim_frames(const Job& A, unsigned k, unsigned long long* base) {
+    if (A.gen == 0u) {
+        *base = atomicAdd(A.queue, (unsigned long long)k);
+        return true;
+    }
+    unsigned long long old = *(volatile unsigned long long*)A.queue;
+    for (int it = 0; it < kClaimTries; ++it) {
+        if ((uint32_t)(old >> 32) != A.gen || (long long)(uint32_t)old >= A.n_frames) return false;
+        const unsigned long long got = atomicCAS(A.queue, old, old + k);
+        if (got == old) {
+            *base = (uint32_t)old;
+            return true;
+        }
+        old = got;
+    }
+    return false;
+}
 
 // Launch of one job: the job and its thresholds travel as kernel parameters.
 struct DecodeArgs {
@@ -188,7 +217,9 @@ __host__ __device__ inline SmemLayout smem_layout(int n, int m, int t_max, int d
     L.off_cnt = take(pad4(n_local) * cnt_bytes, 16);
     L.off_xw = take(pad4(n + 1) * 4, 16);
     L.off_sw = take((m + 1) * (dv_max <= 7 ? 16 : 4), 16);
-    L.off_thr = need_thr ? take((t_max + 1) * 4, 16) : -1;
+    // all 512 values of the 9-bit u field: an idle slot's counter may pass T (its lookups are
+    // don't-care but stay inside the table)
+    L.off_thr = need_thr ? take((kUMask + 1) * 4, 16) : -1;
     L.off_st = st_smem ? take(pad4(n_local) * kSlots * 2, 16) : -1;
     L.off_chk = (tables & kTabChk) ? take(dc_max * m * 2, 16) : -1;
     L.off_sym = (tables & kTabSym) ? take(n_local * dv_max * 2 + n_local, 16) : -1;
@@ -391,8 +422,10 @@ __device__ __forceinline__ void decode_job(const Job& A, const uint32_t* thr_src
     for (int i = tid; i < 256; i += blockDim.x) icdf[i] = G.icdf[i];
     for (int k = tid; k < pad4(n + 1); k += blockDim.x) xw[k] = 0u;
     for (int i = tid; i < (m + 1) * (WIDE ? 1 : 4); i += blockDim.x) sw[i] = 0u;
+    // a serving job's thresholds and samples were copied in while the kernel runs: read them
+    // past L1, which may still hold lines of an earlier request at the same addresses
     if constexpr (ADAPT)
-        for (int u = tid; u <= T; u += blockDim.x) thr[u] = thr_src[u];
+        for (int u = tid; u <= T; u += blockDim.x) thr[u] = A.gen ? __ldcg(thr_src + u) : thr_src[u];
     if constexpr (kState)
         for (int e = tid; e < pad4(nl) * kSlots; e += blockDim.x) st[e] = 0;
     if (tid < 2 * kSlots) best[tid] = ~0ull;
@@ -400,12 +433,13 @@ __device__ __forceinline__ void decode_job(const Job& A, const uint32_t* thr_src
         for (int c = 0; c < 8; ++c) ctl[c] = 0u;
     if (split) group_sync();        // every copy cleared before rank 0 writes the slot table
     if (tid == 0 && (!split || S.rank == 0)) {
-        const unsigned long long base = atomicAdd(A.queue, (unsigned long long)kSlots);
+        unsigned long long base = 0;
+        const bool got = claim_frames(A, kSlots, &base);
         uint32_t live = 0;
         for (int f = 0; f < kSlots; ++f) {
             const unsigned long long fid = base + f;
             lane_start[f] = 0;
-            if (fid < (unsigned long long)A.n_frames) {
+            if (got && fid < (unsigned long long)A.n_frames) {
                 lane_frame[f] = (long long)fid;
                 live |= 1u << f;
             } else {
@@ -444,7 +478,8 @@ __device__ __forceinline__ void decode_job(const Job& A, const uint32_t* thr_src
                 while (rest) {
                     const int f = __ffs(rest) - 1;
                     rest &= rest - 1;
-                    float v = __ldg(A.y + (size_t)lane_frame[f] * n + k);
+                    const float* yp = A.y + (size_t)lane_frame[f] * n + k;
+                    float v = A.gen ? __ldcg(yp) : __ldg(yp);
                     if (A.clamp) {
                         if (v > A.y_max) v = A.y_max;
                         if (v < -A.y_max) v = -A.y_max;
@@ -548,15 +583,24 @@ __device__ __forceinline__ void decode_job(const Job& A, const uint32_t* thr_src
                 A.iters[fr] = ok ? round - lane_start[f] : T;
                 A.pass[fr] = ok ? 1 : 0;
             }
+            if (A.done != nullptr) __threadfence();   // outputs visible before they are counted
             group_sync();           // every CTA is done with the finished slots' table entries
+            if (A.done != nullptr && tid == 0 && (!split || S.rank == 0)) {
+                const unsigned int before = atomicAdd(A.done, (unsigned int)nfin);
+                if ((long long)before + nfin == A.n_frames) {
+                    __threadfence_system();
+                    *(volatile unsigned int*)A.notify = A.gen;
+                }
+            }
             // ---- claim new frames for the finished slots ----
             if (tid == 0 && (!split || S.rank == 0)) {
                 uint32_t fresh = 0;
-                const unsigned long long base = atomicAdd(A.queue, (unsigned long long)nfin);
+                unsigned long long base = 0;
+                const bool got = claim_frames(A, (unsigned)nfin, &base);
                 for (int j = 0; j < nfin; ++j) {
                     const int f = nth_set_bit(fin, j);
                     const unsigned long long fid = base + j;
-                    if (fid < (unsigned long long)A.n_frames) {
+                    if (got && fid < (unsigned long long)A.n_frames) {
                         lane_frame[f] = (long long)fid;
                         lane_start[f] = round;
                         fresh |= 1u << f;
@@ -636,7 +680,7 @@ __device__ __forceinline__ void decode_job(const Job& A, const uint32_t* thr_src
             const int t = act ? round - lane_start[lane] : 0;
             const bool window = SMOOTH && act && t >= A.t_smooth;
             const int g_lo = k_lo >> 2;              // first group of this CTA's symbols
-            const uint32_t th0 = thr_src[0];    // threshold of the non-adaptive variants
+            const uint32_t th0 = A.gen ? __ldcg(thr_src) : thr_src[0];   // threshold of the non-adaptive variants
             const float scale = A.scale, wgt = A.w, fix_R = A.fix_R, acc_R = A.acc_R;
             const int32_t fix_kmax = A.fix_kmax, fix_W = A.fix_W, acc_W = A.acc_W;
             const bool uniform = A.uniform != 0;
@@ -772,12 +816,13 @@ __device__ __forceinline__ void decode_job(const Job& A, const uint32_t* thr_src
                         const uint32_t s0 = sv[j];
                         const uint32_t th = ADAPT ? thv[j] : th0;
                         const bool lower = below(th);       // evaluated for every lane, no branch
-                        flip = act && lower;
+                        // an idle slot (no frame) may flip and count too: its decision bits and
+                        // counters are cleared when it takes a frame and never reach an output
+                        flip = lower;
                         // u_k += 1 when not flipped; the window counter counts x_k = -1
-                        nvv[j] = s0 + ((ADAPT && act && !flip) ? 1u : 0u) + (window ? (xsign >> (31 - kCShift)) : 0u);
+                        nvv[j] = s0 + ((ADAPT && !flip) ? 1u : 0u) + (window ? (xsign >> (31 - kCShift)) : 0u);
                     } else {
-                        const bool lower = below(th0);
-                        flip = act && lower;
+                        flip = below(th0);              // idle slots: don't-care, as above
                     }
                     fmv[j] = __ballot_sync(0xFFFFFFFFu, flip);
                 }

@@ -1,12 +1,20 @@
-// ngdbf_server.cu -- the serving loop: a scheduler thread that admits decode requests
-// under a device-memory budget and runs them as job-table launches on several streams.
+// ngdbf_server.cu -- the serving loop: continuous batching of decode requests on a resident
+// persistent kernel.
 //
-// A launch holds, in one block from the library's stream-ordered pool:
-//   [queues | job table | thresholds | first job per CTA | slot samples | slot state |
-//    per request: samples, bits, iterations, pass flags]
-// The job table, thresholds and first jobs are staged in page-locked host memory and
-// copied with one asynchronous copy.  A host function enqueued after the output copies
-// stamps the completion time and wakes the scheduler, which then frees the block.
+// Requests (a code, host samples and host outputs) are queued in arrival order.  A scheduler
+// thread admits them while the device memory they need fits the budget: it takes a block from
+// the library's stream-ordered pool, copies the samples and thresholds in on one of the copy
+// streams, and publishes the request into a ring of job descriptors in device memory (small
+// ordered copies from a page-locked mirror, made to wait for the request's own copies).  One persistent job-table kernel serves the ring: whenever a CTA has no
+// frames left in its current request it takes the oldest published request with unclaimed
+// frames, so requests that arrive while others are on the GPU join the running launch as
+// CTAs -- and, inside a request, slots -- free up.  The CTA that finishes a request's last frame
+// writes the request's generation into a completion word in page-locked host memory; the
+// scheduler then copies the outputs back and returns the request's memory to the budget.  Idle
+// CTAs poll the ring (in device memory, backing off) for about 20 ms and then exit; the
+// scheduler launches the kernel again when new work is published.  A request whose code needs a larger shared-memory layout, or another variant or
+// precision, than the running kernel waits until it drains.  Only copy-engine operations are
+// issued while the kernel runs (no memset kernels), so nothing waits behind it for SMs.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -20,6 +28,137 @@
 #include <vector>
 
 #include "ngdbf_host.h"
+
+namespace ngdbf {
+
+constexpr int kRing = 1024;                       // descriptor slots: requests on the device at once, at most
+constexpr long long kIdleNs = 20'000'000;         // an idle CTA exits after about this long without work
+
+// In device memory; written only by copies from the host's page-locked mirror.
+struct ServeRing {
+    unsigned long long tail;          // requests [0, tail) are published
+    unsigned long long head;          // requests below head are complete (where scans start)
+    unsigned int stop_epoch;          // the kernel of epoch e exits at once when stop_epoch >= e,
+    unsigned int drain_epoch;         // and when it has no work left when drain_epoch >= e
+    unsigned long long ready[kRing];  // q + 1 while the slot holds the complete descriptor of request q
+    Job jobs[kRing];
+};
+
+// Page-locked staging of one ring slot (free again once the slot's request completes).
+struct SlotStage {
+    unsigned long long claim0;        // (gen << 32) | 0
+    unsigned int done0;               // 0
+    unsigned int pad;
+    unsigned long long ready0, ready1, tail1;   // 0, seq + 1, seq + 1
+    Job desc;
+    uint32_t thr[NGDBF_MAX_T + 1];
+};
+
+struct ServeArgs {
+    const ServeRing* ring;            // device memory
+    unsigned int* notify;             // [kRing] page-locked, mapped: a slot's generation once done
+    unsigned int epoch;
+    int32_t n_max, m_max, t_max, dv_max, dc_max, placement;
+    void* yslots;                     // [grid][pad4(n_max)/4][32][4]
+    uint16_t* st_global;              // [grid][pad4(n_max)/4][32][4] when the state is not in shared memory
+    GenConsts G;
+};
+
+// The resident serving kernel: each CTA repeatedly takes the oldest published request that
+// still has unclaimed frames (of its own generation) and runs the slot loop on it.
+template <bool ADAPT, bool SMOOTH, bool ST_SMEM, bool WIDE, int PREC>
+__global__ void __launch_bounds__(1024) ngdbf_serve_kernel(const __grid_constant__ ServeArgs A) {
+    using HeldT = typename Held<PREC>::T;
+    __shared__ Job job;
+    __shared__ int pick;
+    const SmemLayout L = smem_layout(A.n_max, A.m_max, A.t_max, A.dv_max, A.dc_max, ADAPT,
+                                     ST_SMEM && (ADAPT || SMOOTH), A.placement);
+    HeldT* ys = static_cast<HeldT*>(A.yslots) + (size_t)blockIdx.x * pad4(A.n_max) * kSlots;
+    uint16_t* st = A.st_global ? A.st_global + (size_t)blockIdx.x * pad4(A.n_max) * kSlots : nullptr;
+    const volatile ServeRing* R = A.ring;
+    long long slept = 0;
+    unsigned int nap = 500;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            int p = -1;
+            if (R->stop_epoch >= A.epoch) {
+                p = -2;
+            } else {
+                const unsigned long long tail = R->tail;
+                const unsigned long long head = R->head;
+                for (unsigned long long q = head; q < tail && q < head + kRing; ++q) {
+                    const int slot = (int)(q % kRing);
+                    // the slot must hold request q, complete, before and after the descriptor
+                    // is read (the copies clear `ready` before they rewrite a slot)
+                    if (R->ready[slot] != q + 1) continue;
+                    __threadfence();
+                    const uint32_t gen = R->jobs[slot].gen;
+                    const long long frames = R->jobs[slot].n_frames;
+                    unsigned long long* queue = R->jobs[slot].queue;
+                    const unsigned long long c = *(volatile unsigned long long*)queue;
+                    if ((uint32_t)(c >> 32) != gen || (long long)(uint32_t)c >= frames) continue;
+                    // the descriptor word by word past L1 (the slot held earlier requests)
+                    const volatile uint32_t* src = reinterpret_cast<const volatile uint32_t*>(&R->jobs[slot]);
+                    uint32_t* dst = reinterpret_cast<uint32_t*>(&job);
+                    for (int w = 0; w < (int)(sizeof(Job) / 4); ++w) dst[w] = src[w];
+                    __threadfence();
+                    if (R->ready[slot] != q + 1 || job.gen != gen) continue;
+                    p = slot;
+                    break;
+                }
+                if (p < 0 && R->drain_epoch >= A.epoch) p = -2;
+                if (p < 0 && slept > kIdleNs) p = -2;       // idle long enough: exit
+                if (p < 0) {
+                    __nanosleep(nap);
+                    slept += nap;
+                    nap = nap < 64000u ? 2 * nap : nap;
+                }
+            }
+            pick = p;
+        }
+        __syncthreads();
+        const int p = pick;
+        __syncthreads();
+        if (p == -2) break;
+        if (p < 0) continue;
+        slept = 0;
+        nap = 500;
+        decode_job<ADAPT, SMOOTH, ST_SMEM, WIDE, PREC>(job, job.thr, A.G, L, A.placement, ys, st);
+        __syncthreads();
+    }
+}
+
+namespace {
+
+using ServeFn = void (*)(ServeArgs);
+
+template <bool AD, bool SM, int PREC>
+ServeFn serve_width(bool st_smem, bool wide) {
+    if (st_smem) return wide ? ngdbf_serve_kernel<AD, SM, true, true, PREC> : ngdbf_serve_kernel<AD, SM, true, false, PREC>;
+    return wide ? ngdbf_serve_kernel<AD, SM, false, true, PREC> : ngdbf_serve_kernel<AD, SM, false, false, PREC>;
+}
+
+template <int PREC>
+ServeFn serve_variant(int variant, bool st_smem, bool wide) {
+    switch (variant & 3) {
+        case 0: return serve_width<false, false, PREC>(st_smem, wide);
+        case 1: return serve_width<true, false, PREC>(st_smem, wide);
+        case 2: return serve_width<false, true, PREC>(st_smem, wide);
+        default: return serve_width<true, true, PREC>(st_smem, wide);
+    }
+}
+
+ServeFn serve_kernel_fn(int variant, int precision, bool st_smem, bool wide) {
+    switch (precision) {
+        case NGDBF_FP16: return serve_variant<kFP16>(variant, st_smem, wide);
+        case NGDBF_FIX: return serve_variant<kFIX>(variant, st_smem, wide);
+        case NGDBF_FIXACC: return serve_variant<kFIXACC>(variant, st_smem, wide);
+        default: return serve_variant<kFP32>(variant, st_smem, wide);
+    }
+}
+
+}  // namespace
+}  // namespace ngdbf
 
 using namespace ngdbf;
 using namespace ngdbf::host;
@@ -41,18 +180,26 @@ struct Request {
     uint8_t* pass_host = nullptr;
     double t_submit = 0, t_done = 0;
     int32_t status = NGDBF_OK;
+    // on the device
+    uint64_t seq = 0;                // position in the ring
+    int slot = -1;
+    uint32_t gen = 0;
+    int stream = 0;
+    unsigned char* block = nullptr;  // samples | outputs | thresholds
+    size_t bytes = 0;
+    cudaEvent_t ev = nullptr;        // copies in done, then copies out done
+    Job dj{};                        // the descriptor the kernel reads
 };
 
-struct Launch {
-    std::vector<Request*> reqs;
-    unsigned char* block = nullptr;  // device memory of the launch
-    size_t bytes = 0;
-    unsigned char* stage = nullptr;  // page-locked staging of the job table
-    size_t stage_bytes = 0;
-    int stream = -1;
-    std::atomic<bool> done{false};
-    double t_done = 0;
-    void* server = nullptr;
+// Kind of the resident kernel: the template it instantiates and its shared-memory maxima.
+struct Kind {
+    int variant = -1, precision = -1;   // variant & 3 (ADAPT, SMOOTH) and the precision
+    int n = 0, m = 0, t_max = 0, dv = 0, dc = 0;
+    bool fits(const ngdbf_job& q) const {
+        return (q.params.variant & 3) == variant && q.params.precision == precision && q.code->n <= n &&
+               q.code->m <= m && q.params.t_max <= t_max && q.code->dv_max <= dv && q.code->dc_max <= dc &&
+               ((q.code->dv_max > 7) == (dv > 7));
+    }
 };
 
 }  // namespace
@@ -60,19 +207,40 @@ struct Launch {
 struct ngdbf_server {
     int device = 0;
     size_t budget = 0;
-    int max_launches = 1, max_jobs = 1;
+    int max_resident = 1;
     uint64_t seed = 0;
     cudaMemPool_t pool = nullptr;
-    std::vector<cudaStream_t> streams;
-    std::vector<bool> stream_busy;
+    std::vector<cudaStream_t> streams;       // copy streams
+    cudaStream_t pub_stream = nullptr;       // ring updates, in ring order
+    cudaStream_t serve_stream = nullptr;     // the resident kernel
     std::mutex mu;
     std::condition_variable cv;
-    std::deque<Request*> pending;
-    std::vector<Launch*> inflight;
-    std::vector<Request*> completed;          // not yet reported by poll
-    std::vector<std::pair<unsigned char*, size_t>> free_stage;
+    std::deque<Request*> pending;            // arrival order
+    std::vector<Request*> published;         // in the ring (copies in may still be running)
+    std::vector<Request*> leaving;           // copies out in flight
+    std::vector<Request*> completed;         // not yet reported by poll
+    ServeRing* d_ring = nullptr;             // device memory
+    unsigned int* notify_host = nullptr;     // [kRing] page-locked, mapped
+    unsigned int* notify_dev = nullptr;
+    SlotStage* stage = nullptr;              // [kRing] page-locked
+    unsigned long long* head_img = nullptr;  // page-locked words copied into the ring
+    unsigned int* epoch_img = nullptr;       // [2]: stop, drain
+    unsigned long long* d_claim = nullptr;   // [kRing] (gen << 32) | frames claimed
+    unsigned int* d_done = nullptr;          // [kRing] frames done
+    uint32_t slot_gen[kRing] = {};
+    uint64_t next_seq = 0, head = 0;
+    std::vector<uint64_t> done_seq;          // completed sequence numbers above head
+    // the resident kernel
+    bool running = false;
+    unsigned int epoch = 0;
+    Kind kind;
+    std::vector<Kind> seen;                  // per variant and precision: the largest layout so far
+    size_t kind_scratch = 0;                 // scratch the kernel of `kind` takes at launch
+    cudaEvent_t ev_kernel = nullptr;
+    unsigned char* scratch = nullptr;
+    size_t scratch_bytes = 0;
+    int rr = 0;
     size_t in_use = 0;
-    uint64_t next_id = 1;
     ngdbf_server_stats stats{};
     bool stop = false;
     std::thread worker;
@@ -80,234 +248,312 @@ struct ngdbf_server {
 
 namespace {
 
-void CUDART_CB launch_finished(void* arg) {
-    Launch* L = static_cast<Launch*>(arg);
-    // once `done` is set the scheduler may retire and delete L: read what is needed first.
-    // The server outlives this call (ngdbf_server_destroy synchronizes the streams).
-    ngdbf_server* S = static_cast<ngdbf_server*>(L->server);
-    L->t_done = now_s();
-    L->done.store(true);
-    S->cv.notify_all();
-}
-
-// Device bytes of a request's own buffers.
 size_t request_bytes(const ngdbf_job& q) {
     const int64_t n = q.code->n, nb = (n + 7) / 8;
     return align256((size_t)q.n_frames * n * 4) + align256((size_t)q.n_frames * nb) +
-           align256((size_t)q.n_frames * 4) + align256((size_t)q.n_frames);
+           align256((size_t)q.n_frames * 4) + align256((size_t)q.n_frames) + align256((size_t)(q.params.t_max + 1) * 4);
 }
 
-struct LaunchLayout {
-    TablePlan plan;
-    int grid = 0, block = 0;
-    size_t off_jobs = 0, off_thr = 0, off_first = 0, off_y = 0, off_st = 0, off_req = 0, total = 0;
-    size_t stage_bytes = 0;
-};
-
-// Plan and size one launch of the given requests (all of one variant and precision).
-ngdbf_status layout_launch(ngdbf_server* S, const std::vector<Request*>& reqs, LaunchLayout* out) {
-    std::vector<ngdbf_job> jobs;
-    for (Request* r : reqs) jobs.push_back(r->job);
-    LaunchLayout& L = *out;
-    ngdbf_status s = plan_table(jobs.data(), (int32_t)jobs.size(), S->device, &L.plan);
-    if (s != NGDBF_OK) return s;
-    const int J = (int)reqs.size();
-    int64_t groups = 0;
-    for (const ngdbf_job& q : jobs) groups += (q.n_frames + 31) / 32;
-    L.block = L.plan.shapes[0].first;
-    L.grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)L.plan.sm_count * L.plan.shapes[0].second, groups));
-    const size_t per_slot_y = (size_t)pad4(L.plan.n_max) * kSlots * held_bytes(L.plan.precision);
-    const size_t per_slot_st = L.plan.state_global ? (size_t)pad4(L.plan.n_max) * kSlots * 2 : 0;
-    L.off_jobs = align256(8 * (size_t)J);                 // queues first
-    L.off_thr = L.off_jobs + align256(sizeof(Job) * J);
-    L.off_first = L.off_thr + align256(L.plan.thr_words * 4);
-    L.off_y = L.off_first + align256(4 * (size_t)L.grid);
-    L.off_st = L.off_y + align256((size_t)L.grid * per_slot_y);
-    L.off_req = L.off_st + align256((size_t)L.grid * per_slot_st);
-    L.total = L.off_req;
-    for (const ngdbf_job& q : jobs) L.total += request_bytes(q);
-    L.stage_bytes = L.off_y - L.off_jobs;                   // job table, thresholds, first jobs
-    return NGDBF_OK;
+void finish(ngdbf_server* S, Request* r, int32_t status) {
+    r->t_done = now_s();
+    r->status = status;
+    S->completed.push_back(r);
+    S->stats.completed += 1;
+    if (status != NGDBF_OK) S->stats.failed += 1;
+    else S->stats.frames += r->job.n_frames;
 }
 
-unsigned char* take_stage(ngdbf_server* S, size_t bytes, size_t* got) {
-    for (size_t i = 0; i < S->free_stage.size(); ++i)
-        if (S->free_stage[i].second >= bytes) {
-            auto e = S->free_stage[i];
-            S->free_stage.erase(S->free_stage.begin() + i);
-            *got = e.second;
-            return e.first;
-        }
-    void* p = nullptr;
-    const size_t sz = std::max<size_t>(bytes, 1 << 16);
-    if (cudaMallocHost(&p, sz) != cudaSuccess) return nullptr;
-    *got = sz;
-    return static_cast<unsigned char*>(p);
-}
-
-// Issues copy-in, decode and copy-out of one admitted launch on stream `si`.
-ngdbf_status issue(ngdbf_server* S, Launch* Lc, const LaunchLayout& L, int si) {
+// Copies a request in and publishes it into the ring once its copies are done (every step is
+// an asynchronous copy or an event wait: nothing here needs an SM).
+ngdbf_status admit(ngdbf_server* S, Request* r) {
+    const int si = S->rr++ % (int)S->streams.size();
     cudaStream_t st = S->streams[si];
-    cudaError_t e = cudaMallocFromPoolAsync(reinterpret_cast<void**>(&Lc->block), L.total, S->pool, st);
-    if (e != cudaSuccess) { cudaGetLastError(); return fail(NGDBF_ERR_OOM, "server: device block"); }
-    Lc->bytes = L.total;
-    Lc->stage = take_stage(S, L.stage_bytes, &Lc->stage_bytes);
-    if (!Lc->stage) return fail(NGDBF_ERR_OOM, "server: staging");
-    unsigned char* base = Lc->block;
-    const int J = (int)Lc->reqs.size();
-    std::vector<int64_t> frames(J), weight(J);
-    Job* hjobs = reinterpret_cast<Job*>(Lc->stage);
-    uint32_t* hthr = reinterpret_cast<uint32_t*>(Lc->stage + (L.off_thr - L.off_jobs));
-    int32_t* hfirst = reinterpret_cast<int32_t*>(Lc->stage + (L.off_first - L.off_jobs));
-    size_t pos = L.off_req, tpos = 0;
-    for (int j = 0; j < J; ++j) {
-        Request* r = Lc->reqs[j];
-        const ngdbf_job& q = r->job;
-        const int64_t n = q.code->n, nb = (n + 7) / 8, F = q.n_frames;
-        float* dy = reinterpret_cast<float*>(base + pos);
-        pos += align256((size_t)F * n * 4);
-        uint8_t* dbits = base + pos;
-        pos += align256((size_t)F * nb);
-        int32_t* diters = reinterpret_cast<int32_t*>(base + pos);
-        pos += align256((size_t)F * 4);
-        uint8_t* dpass = base + pos;
-        pos += align256((size_t)F);
-        fill_job(q.code, &q.params, dy, F, q.sigma, q.frame_offset, dbits, diters, dpass,
-                 reinterpret_cast<unsigned long long*>(base) + j, &hjobs[j], hthr + tpos);
-        hjobs[j].thr = reinterpret_cast<const uint32_t*>(base + L.off_thr) + tpos;
-        tpos += (size_t)q.params.t_max + 1;
-        frames[j] = F;
-        weight[j] = F * n * (q.params.t_max + 1);
-        if (F > 0) {
-            e = cudaMemcpyAsync(dy, r->y_host, (size_t)F * n * 4, cudaMemcpyHostToDevice, st);
-            if (e != cudaSuccess) return cuda_fail(e, "server: copy in");
-        }
-    }
-    std::vector<int32_t> first = assign_ctas(frames, weight, L.grid);
-    std::memcpy(hfirst, first.data(), first.size() * 4);
-    e = cudaMemcpyAsync(base + L.off_jobs, Lc->stage, L.stage_bytes, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(base, 0, 8 * (size_t)J, st);
-    if (e != cudaSuccess) return cuda_fail(e, "server: job table");
-    MultiArgs A;
-    std::memset(&A, 0, sizeof(A));
-    A.jobs = reinterpret_cast<const Job*>(base + L.off_jobs);
-    A.n_jobs = J;
-    A.first_job = reinterpret_cast<const int32_t*>(base + L.off_first);
-    A.n_max = L.plan.n_max; A.m_max = L.plan.m_max; A.t_max = L.plan.t_max;
-    A.dv_max = L.plan.dv_max; A.dc_max = L.plan.dc_max;
-    A.placement = L.plan.placement;
-    A.yslots = base + L.off_y;
-    A.st_global = L.plan.state_global ? reinterpret_cast<uint16_t*>(base + L.off_st) : nullptr;
-    host_gen_consts(S->seed, A.G);
-    e = launch_multi(L.plan.fn, A, L.grid, L.block, L.plan.smem, st);
-    if (e != cudaSuccess) return cuda_fail(e, "server: launch");
-    for (int j = 0; j < J; ++j) {
-        Request* r = Lc->reqs[j];
-        const Job& hj = hjobs[j];
-        const int64_t F = r->job.n_frames, nb = (r->job.code->n + 7) / 8;
-        if (F == 0) continue;
-        e = cudaMemcpyAsync(r->bits_host, hj.bits, (size_t)F * nb, cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(r->iters_host, hj.iters, (size_t)F * 4, cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(r->pass_host, hj.pass, (size_t)F, cudaMemcpyDeviceToHost, st);
-        if (e != cudaSuccess) return cuda_fail(e, "server: copy out");
-    }
-    Lc->stream = si;
-    Lc->server = S;
-    e = cudaLaunchHostFunc(st, launch_finished, Lc);
-    if (e != cudaSuccess) return cuda_fail(e, "server: completion callback");
+    r->stream = si;
+    r->bytes = request_bytes(r->job);
+    cudaError_t e = cudaMallocFromPoolAsync(reinterpret_cast<void**>(&r->block), r->bytes, S->pool, st);
+    if (e != cudaSuccess) { cudaGetLastError(); r->block = nullptr; return fail(NGDBF_ERR_OOM, "server: device block"); }
+    const ngdbf_job& q = r->job;
+    const int64_t n = q.code->n, nb = (n + 7) / 8, F = q.n_frames;
+    unsigned char* p = r->block;
+    float* dy = reinterpret_cast<float*>(p);
+    p += align256((size_t)F * n * 4);
+    uint8_t* dbits = p;
+    p += align256((size_t)F * nb);
+    int32_t* diters = reinterpret_cast<int32_t*>(p);
+    p += align256((size_t)F * 4);
+    uint8_t* dpass = p;
+    p += align256((size_t)F);
+    uint32_t* dthr = reinterpret_cast<uint32_t*>(p);
+    r->seq = S->next_seq++;
+    r->slot = (int)(r->seq % kRing);
+    r->gen = ++S->slot_gen[r->slot];
+    if (r->gen == 0) r->gen = ++S->slot_gen[r->slot];      // 0 marks a plain job
+    SlotStage& sg = S->stage[r->slot];
+    fill_job(q.code, &q.params, dy, F, q.sigma, q.frame_offset, dbits, diters, dpass, S->d_claim + r->slot, &r->dj,
+             sg.thr);
+    r->dj.thr = dthr;
+    r->dj.gen = r->gen;
+    r->dj.done = S->d_done + r->slot;
+    r->dj.notify = S->notify_dev + r->slot;
+    sg.claim0 = (unsigned long long)r->gen << 32;
+    sg.done0 = 0;
+    sg.ready0 = 0;
+    sg.ready1 = r->seq + 1;
+    sg.tail1 = r->seq + 1;
+    sg.desc = r->dj;
+    __atomic_store_n(&S->notify_host[r->slot], 0u, __ATOMIC_RELEASE);
+    e = cudaMemcpyAsync(dy, r->y_host, (size_t)F * n * 4, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(dthr, sg.thr, ((size_t)q.params.t_max + 1) * 4, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(S->d_claim + r->slot, &sg.claim0, 8, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(S->d_done + r->slot, &sg.done0, 4, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && !r->ev) e = cudaEventCreateWithFlags(&r->ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(r->ev, st);
+    // publication, in ring order, after the request's own copies: the slot invalid, the
+    // descriptor, the slot valid for request seq, the tail
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(S->pub_stream, r->ev, 0);
+    ServeRing* R = S->d_ring;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&R->ready[r->slot], &sg.ready0, 8, cudaMemcpyHostToDevice, S->pub_stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&R->jobs[r->slot], &sg.desc, sizeof(Job), cudaMemcpyHostToDevice, S->pub_stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&R->ready[r->slot], &sg.ready1, 8, cudaMemcpyHostToDevice, S->pub_stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&R->tail, &sg.tail1, 8, cudaMemcpyHostToDevice, S->pub_stream);
+    if (e != cudaSuccess) return cuda_fail(e, "server: copy in");
     return NGDBF_OK;
 }
 
-void finish_requests(ngdbf_server* S, const std::vector<Request*>& reqs, double t, int32_t status) {
-    for (Request* r : reqs) {
-        r->t_done = t;
-        r->status = status;
-        S->completed.push_back(r);
-        S->stats.completed += 1;
-        if (status != NGDBF_OK) S->stats.failed += 1;
-        else S->stats.frames += r->job.n_frames;
+// Launch plan of the resident kernel of a kind: shared-memory plan, grid and scratch bytes.
+struct ServePlan {
+    SmemPlan sp;
+    int grid = 0;
+    size_t per_y = 0, per_st = 0, bytes = 0;
+};
+ngdbf_status plan_serve(ngdbf_server* S, const Kind& K, ServePlan* out) {
+    const bool state = (K.variant & 3) != 0, adapt = (K.variant & NGDBF_ADAPT) != 0, wide = K.dv > 7;
+    ngdbf_status s = plan_smem(S->device, K.n, K.m, K.t_max, K.dv, K.dc, adapt, state,
+                               (const void*)serve_kernel_fn(K.variant, K.precision, true, wide),
+                               (const void*)serve_kernel_fn(K.variant, K.precision, false, wide), &out->sp);
+    if (s != NGDBF_OK) return s;
+    int sms = 0;
+    cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, S->device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
+    out->grid = sms * out->sp.bps;
+    out->per_y = (size_t)pad4(K.n) * kSlots * held_bytes(K.precision);
+    out->per_st = (state && !out->sp.st_smem) ? (size_t)pad4(K.n) * kSlots * 2 : 0;
+    out->bytes = align256((size_t)out->grid * out->per_y) + align256((size_t)out->grid * out->per_st);
+    return NGDBF_OK;
+}
+
+// Launches the resident kernel for the kind of the published requests (a new epoch).
+ngdbf_status launch_kernel(ngdbf_server* S) {
+    const Kind& K = S->kind;
+    const bool wide = K.dv > 7;
+    ServePlan P;
+    ngdbf_status s = plan_serve(S, K, &P);
+    if (s != NGDBF_OK) return s;
+    const SmemPlan& sp = P.sp;
+    cudaError_t e = cudaMallocFromPoolAsync(reinterpret_cast<void**>(&S->scratch), P.bytes, S->pool, S->serve_stream);
+    if (e != cudaSuccess) { cudaGetLastError(); S->scratch = nullptr; return fail(NGDBF_ERR_OOM, "server: kernel scratch"); }
+    S->scratch_bytes = P.bytes;
+    ServeArgs A;
+    std::memset(&A, 0, sizeof(A));
+    A.ring = S->d_ring;
+    A.notify = S->notify_dev;
+    A.epoch = ++S->epoch;
+    A.n_max = K.n; A.m_max = K.m; A.t_max = K.t_max; A.dv_max = K.dv; A.dc_max = K.dc;
+    A.placement = sp.placement;
+    A.yslots = S->scratch;
+    A.st_global = P.per_st ? reinterpret_cast<uint16_t*>(S->scratch + align256((size_t)P.grid * P.per_y)) : nullptr;
+    host_gen_consts(S->seed, A.G);
+    // the kernel must see every ring update published so far
+    e = cudaEventRecord(S->ev_kernel, S->pub_stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(S->serve_stream, S->ev_kernel, 0);
+    if (e == cudaSuccess) {
+        serve_kernel_fn(K.variant, K.precision, sp.st_smem, wide)<<<P.grid, sp.block, sp.smem, S->serve_stream>>>(A);
+        e = cudaGetLastError();
     }
+    if (e == cudaSuccess) e = cudaEventRecord(S->ev_kernel, S->serve_stream);
+    if (e != cudaSuccess) {
+        cudaFreeAsync(S->scratch, S->serve_stream);
+        S->scratch = nullptr;
+        return cuda_fail(e, "server: kernel launch");
+    }
+    S->running = true;
+    S->in_use += P.bytes;
+    S->stats.launches += 1;
+    return NGDBF_OK;
+}
+
+// The kind a kernel needs for the first request to admit: the largest layout of its variant and
+// precision seen so far (so that the kernel rarely has to drain for a larger code).
+Kind kind_for(ngdbf_server* S, const Request* first) {
+    const ngdbf_job& f = first->job;
+    Kind* K = nullptr;
+    for (Kind& k : S->seen)
+        if (k.variant == (f.params.variant & 3) && k.precision == f.params.precision && (k.dv > 7) == (f.code->dv_max > 7))
+            K = &k;
+    if (!K) {
+        S->seen.push_back(Kind());
+        K = &S->seen.back();
+        K->variant = f.params.variant & 3;
+        K->precision = f.params.precision;
+    }
+    auto grow = [&](const ngdbf_job& q) {
+        if ((q.params.variant & 3) != K->variant || q.params.precision != K->precision ||
+            (q.code->dv_max > 7) != (K->dv > 7 || f.code->dv_max > 7))
+            return;
+        K->n = std::max(K->n, q.code->n);
+        K->m = std::max(K->m, q.code->m);
+        K->t_max = std::max(K->t_max, q.params.t_max);
+        K->dv = std::max(K->dv, q.code->dv_max);
+        K->dc = std::max(K->dc, q.code->dc_max);
+    };
+    grow(f);
+    for (Request* r : S->pending) grow(r->job);
+    return *K;
+}
+
+void copy_word(ngdbf_server* S, void* dst, const void* src, size_t bytes) {
+    if (cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, S->pub_stream) != cudaSuccess) cudaGetLastError();
 }
 
 void scheduler(ngdbf_server* S) {
     cudaSetDevice(S->device);
     std::unique_lock<std::mutex> lk(S->mu);
     for (;;) {
-        // requests completed or launches issued in this pass: waiters are woken after it
-        // (ngdbf_server_wait sleeps on the same condition until every request completed)
         bool progressed = false;
-        // retire finished launches
-        for (size_t i = 0; i < S->inflight.size();) {
-            Launch* L = S->inflight[i];
-            if (!L->done.load()) { ++i; continue; }
-            cudaFreeAsync(L->block, S->streams[L->stream]);
-            S->free_stage.push_back({L->stage, L->stage_bytes});
-            S->in_use -= L->bytes;
-            S->stream_busy[L->stream] = false;
-            finish_requests(S, L->reqs, L->t_done, NGDBF_OK);
-            delete L;
-            S->inflight.erase(S->inflight.begin() + i);
+        // 1. requests whose last frame is done: copy the outputs out
+        for (size_t i = 0; i < S->published.size();) {
+            Request* r = S->published[i];
+            if (__atomic_load_n(&S->notify_host[r->slot], __ATOMIC_ACQUIRE) != r->gen) { ++i; continue; }
+            cudaStream_t st = S->streams[r->stream];
+            const int64_t F = r->job.n_frames, nb = (r->job.code->n + 7) / 8;
+            cudaError_t e = cudaMemcpyAsync(r->bits_host, r->dj.bits, (size_t)F * nb, cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(r->iters_host, r->dj.iters, (size_t)F * 4, cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(r->pass_host, r->dj.pass, (size_t)F, cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaEventRecord(r->ev, st);
+            if (e != cudaSuccess) { cudaGetLastError(); r->status = NGDBF_ERR_CUDA; }
+            S->leaving.push_back(r);
+            S->published.erase(S->published.begin() + i);
             progressed = true;
         }
-        // admit pending requests in arrival order into one launch per free stream
+        // 2. outputs written: the request is complete, its memory and ring slot free
+        for (size_t i = 0; i < S->leaving.size();) {
+            Request* r = S->leaving[i];
+            if (r->status == NGDBF_OK && cudaEventQuery(r->ev) == cudaErrorNotReady) { ++i; continue; }
+            cudaGetLastError();
+            cudaFreeAsync(r->block, S->streams[r->stream]);
+            cudaEventDestroy(r->ev);
+            r->ev = nullptr;
+            S->in_use -= r->bytes;
+            S->done_seq.push_back(r->seq);
+            finish(S, r, r->status);
+            S->leaving.erase(S->leaving.begin() + i);
+            progressed = true;
+        }
+        // the scan start of the kernel: the oldest sequence number not yet complete
+        std::sort(S->done_seq.begin(), S->done_seq.end());
+        size_t adv = 0;
+        while (adv < S->done_seq.size() && S->done_seq[adv] == S->head + adv) ++adv;
+        if (adv) {
+            S->head += adv;
+            S->done_seq.erase(S->done_seq.begin(), S->done_seq.begin() + adv);
+            *S->head_img = S->head;             // a copy may read a later head: still valid
+            copy_word(S, &S->d_ring->head, S->head_img, 8);
+        }
+        // 3. the resident kernel exited (idle, drained or stopped)
+        if (S->running && cudaEventQuery(S->ev_kernel) != cudaErrorNotReady) {
+            cudaGetLastError();
+            S->running = false;
+            cudaFreeAsync(S->scratch, S->serve_stream);
+            S->scratch = nullptr;
+            S->in_use -= S->scratch_bytes;
+            S->scratch_bytes = 0;
+            progressed = true;
+        }
+        // 4. admission in arrival order, while memory, ring slots and the kernel's kind allow
         while (!S->pending.empty() && !S->stop) {
-            int si = -1;
-            for (int k = 0; k < (int)S->streams.size(); ++k)
-                if (!S->stream_busy[k]) { si = k; break; }
-            if (si < 0) break;
-            std::vector<Request*> group;
-            LaunchLayout L;
-            const int variant = S->pending.front()->job.params.variant;
-            const int precision = S->pending.front()->job.params.precision;
-            for (Request* r : S->pending) {
-                if ((int)group.size() >= S->max_jobs) break;
-                if (r->job.params.variant != variant || r->job.params.precision != precision) break;
-                group.push_back(r);
-                LaunchLayout trial;
-                if (layout_launch(S, group, &trial) != NGDBF_OK || S->in_use + trial.total > S->budget) {
-                    group.pop_back();
-                    break;
-                }
-                L = trial;
+            Request* r = S->pending.front();
+            if (r->job.n_frames == 0) {
+                S->pending.pop_front();
+                finish(S, r, NGDBF_OK);
+                progressed = true;
+                continue;
             }
-            if (group.empty()) {
-                Request* r = S->pending.front();
-                LaunchLayout alone;
-                ngdbf_status s = layout_launch(S, {r}, &alone);
-                if (s != NGDBF_OK || (alone.total > S->budget)) {
-                    // can never run: report it and go on
+            const size_t bytes = request_bytes(r->job);
+            const bool on_device = S->running || !S->published.empty();
+            if (on_device && !S->kind.fits(r->job)) {
+                // another kind or a larger code: let the running work drain first
+                if (S->running && S->epoch_img[1] != S->epoch) {
+                    S->epoch_img[1] = S->epoch;
+                    copy_word(S, &S->d_ring->drain_epoch, &S->epoch_img[1], 4);
+                }
+                break;
+            }
+            if (S->next_seq - S->head >= (uint64_t)S->max_resident) break;
+            Kind K = S->kind;
+            if (!on_device) {
+                K = kind_for(S, r);
+                ServePlan P;
+                if (plan_serve(S, K, &P) != NGDBF_OK) {
                     S->pending.pop_front();
-                    finish_requests(S, {r}, now_s(), s != NGDBF_OK ? s : NGDBF_ERR_OOM);
+                    finish(S, r, NGDBF_ERR_UNSUPPORTED);
                     progressed = true;
                     continue;
                 }
-                break;                       // wait for memory to be returned
+                S->kind_scratch = P.bytes;
             }
-            for (size_t k = 0; k < group.size(); ++k) S->pending.pop_front();
-            Launch* Lc = new Launch;
-            Lc->reqs = group;
-            S->stream_busy[si] = true;
-            ngdbf_status s = issue(S, Lc, L, si);
+            const size_t reserve = S->running ? 0 : S->kind_scratch;   // scratch of a kernel still to be launched
+            if (S->in_use + reserve + bytes > S->budget) {
+                if (!on_device && reserve + bytes > S->budget) {          // can never run
+                    S->pending.pop_front();
+                    finish(S, r, NGDBF_ERR_OOM);
+                    progressed = true;
+                    continue;
+                }
+                break;                                   // wait for memory to be returned
+            }
+            if (!on_device) S->kind = K;
+            S->pending.pop_front();
+            ngdbf_status s = admit(S, r);
             if (s != NGDBF_OK) {
-                cudaStreamSynchronize(S->streams[si]);
-                if (Lc->block) cudaFreeAsync(Lc->block, S->streams[si]);
-                if (Lc->stage) S->free_stage.push_back({Lc->stage, Lc->stage_bytes});
-                S->stream_busy[si] = false;
-                finish_requests(S, group, now_s(), s);
-                delete Lc;
+                // nothing of it was published: give its slot and memory back
+                cudaStreamSynchronize(S->streams[r->stream]);
+                if (r->block) cudaFreeAsync(r->block, S->streams[r->stream]);
+                if (r->ev) { cudaEventDestroy(r->ev); r->ev = nullptr; }
+                S->done_seq.push_back(r->seq);
+                finish(S, r, s);
             } else {
-                S->in_use += L.total;
-                S->inflight.push_back(Lc);
-                S->stats.launches += 1;
-                S->stats.peak_bytes_in_use = std::max<int64_t>(S->stats.peak_bytes_in_use, (int64_t)S->in_use);
-                S->stats.peak_concurrent_launches =
-                    std::max<int32_t>(S->stats.peak_concurrent_launches, (int32_t)S->inflight.size());
+                S->in_use += r->bytes;
+                if (S->running) S->stats.admitted_into_running += 1;
+                S->published.push_back(r);
+                S->stats.peak_requests_on_device =
+                    std::max<int32_t>(S->stats.peak_requests_on_device, (int32_t)S->published.size());
+                S->stats.peak_bytes_in_use = std::max<int64_t>(
+                    S->stats.peak_bytes_in_use, (int64_t)(S->in_use + (S->running ? 0 : S->kind_scratch)));
             }
             progressed = true;
         }
+        // 5. published work and no kernel: launch one
+        if (!S->running && !S->published.empty() && !S->stop) {
+            ngdbf_status s = launch_kernel(S);
+            if (s != NGDBF_OK) {
+                // nothing can decode these: report them once their copies are done
+                cudaStreamSynchronize(S->pub_stream);
+                for (Request* r : S->published) {
+                    cudaFreeAsync(r->block, S->streams[r->stream]);
+                    if (r->ev) { cudaEventDestroy(r->ev); r->ev = nullptr; }
+                    S->in_use -= r->bytes;
+                    S->done_seq.push_back(r->seq);
+                    finish(S, r, s);
+                }
+                S->published.clear();
+            }
+            S->stats.peak_bytes_in_use = std::max<int64_t>(S->stats.peak_bytes_in_use, (int64_t)S->in_use);
+            progressed = true;
+        }
         if (progressed) S->cv.notify_all();
-        if (S->stop && S->inflight.empty()) break;
-        S->cv.wait_for(lk, std::chrono::microseconds(200));
+        if (S->stop && S->published.empty() && S->leaving.empty() && !S->running) break;
+        S->cv.wait_for(lk, std::chrono::microseconds(S->running ? 50 : 200));
     }
 }
 
@@ -319,7 +565,7 @@ extern "C" ngdbf_status ngdbf_server_create(size_t device_budget_bytes, int32_t 
     *out = nullptr;
     if (device_budget_bytes == 0) return fail(NGDBF_ERR_INVALID_ARG, "budget must be > 0");
     if (max_inflight_launches < 1 || max_inflight_launches > 16)
-        return fail(NGDBF_ERR_INVALID_ARG, "max_inflight_launches must be 1..16");
+        return fail(NGDBF_ERR_INVALID_ARG, "max_inflight_launches (copy streams) must be 1..16");
     if (max_jobs_per_launch < 1 || max_jobs_per_launch > 4096)
         return fail(NGDBF_ERR_INVALID_ARG, "max_jobs_per_launch must be 1..4096");
     ngdbf_server* S = new (std::nothrow) ngdbf_server;
@@ -329,20 +575,46 @@ extern "C" ngdbf_status ngdbf_server_create(size_t device_budget_bytes, int32_t 
     ngdbf_status s = get_pool(S->device, &S->pool);
     if (s != NGDBF_OK) { delete S; return s; }
     S->budget = device_budget_bytes;
-    S->max_launches = max_inflight_launches;
-    S->max_jobs = max_jobs_per_launch;
+    S->max_resident = std::min(max_jobs_per_launch, kRing);
     S->seed = seed;
-    for (int k = 0; k < max_inflight_launches; ++k) {
+    e = cudaHostAlloc(reinterpret_cast<void**>(&S->notify_host), sizeof(unsigned int) * kRing, cudaHostAllocMapped);
+    if (e == cudaSuccess) {
+        std::memset(S->notify_host, 0, sizeof(unsigned int) * kRing);
+        e = cudaHostGetDevicePointer(reinterpret_cast<void**>(&S->notify_dev), S->notify_host, 0);
+    }
+    if (e == cudaSuccess) e = cudaHostAlloc(reinterpret_cast<void**>(&S->stage), sizeof(SlotStage) * kRing, cudaHostAllocDefault);
+    if (e == cudaSuccess) e = cudaHostAlloc(reinterpret_cast<void**>(&S->head_img), 8, cudaHostAllocDefault);
+    if (e == cudaSuccess) e = cudaHostAlloc(reinterpret_cast<void**>(&S->epoch_img), 8, cudaHostAllocDefault);
+    if (e == cudaSuccess) e = cudaMalloc(&S->d_ring, sizeof(ServeRing));
+    if (e == cudaSuccess) e = cudaMalloc(&S->d_claim, sizeof(unsigned long long) * kRing);
+    if (e == cudaSuccess) e = cudaMalloc(&S->d_done, sizeof(unsigned int) * kRing);
+    if (e == cudaSuccess) e = cudaMemset(S->d_ring, 0, sizeof(ServeRing));
+    if (e == cudaSuccess) e = cudaMemset(S->d_claim, 0, sizeof(unsigned long long) * kRing);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&S->ev_kernel, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->serve_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->pub_stream, cudaStreamNonBlocking);
+    for (int k = 0; k < max_inflight_launches && e == cudaSuccess; ++k) {
         cudaStream_t st;
         e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
-        if (e != cudaSuccess) {
-            for (cudaStream_t t : S->streams) cudaStreamDestroy(t);
-            delete S;
-            return cuda_fail(e, "server streams");
-        }
-        S->streams.push_back(st);
-        S->stream_busy.push_back(false);
+        if (e == cudaSuccess) S->streams.push_back(st);
     }
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        for (cudaStream_t t : S->streams) cudaStreamDestroy(t);
+        if (S->serve_stream) cudaStreamDestroy(S->serve_stream);
+        if (S->pub_stream) cudaStreamDestroy(S->pub_stream);
+        if (S->ev_kernel) cudaEventDestroy(S->ev_kernel);
+        cudaFree(S->d_ring);
+        cudaFree(S->d_claim);
+        cudaFree(S->d_done);
+        if (S->stage) cudaFreeHost(S->stage);
+        if (S->head_img) cudaFreeHost(S->head_img);
+        if (S->epoch_img) cudaFreeHost(S->epoch_img);
+        if (S->notify_host) cudaFreeHost(S->notify_host);
+        delete S;
+        return cuda_fail(e, "server set-up");
+    }
+    S->epoch_img[0] = S->epoch_img[1] = 0;
     S->worker = std::thread(scheduler, S);
     *out = S;
     return NGDBF_OK;
@@ -356,6 +628,7 @@ extern "C" ngdbf_status ngdbf_server_submit(ngdbf_server_t* S, const ngdbf_code_
     ngdbf_status s = check_params(params, sigma);
     if (s != NGDBF_OK) return s;
     if (n_frames < 0) return fail(NGDBF_ERR_INVALID_ARG, "n_frames < 0");
+    if (n_frames >= (1ll << 31)) return fail(NGDBF_ERR_UNSUPPORTED, "a request holds fewer than 2^31 frames");
     if (n_frames > 0 && (!y_host || !bits_host || !iters_host || !pass_host))
         return fail(NGDBF_ERR_INVALID_ARG, "NULL buffer");
     if (code->device != S->device) return fail(NGDBF_ERR_INVALID_ARG, "code tables belong to another device");
@@ -372,10 +645,9 @@ extern "C" ngdbf_status ngdbf_server_submit(ngdbf_server_t* S, const ngdbf_code_
     r->pass_host = pass_host;
     {
         std::lock_guard<std::mutex> lk(S->mu);
-        r->id = S->next_id++;
+        r->id = ++S->stats.submitted;
         r->t_submit = now_s();
         S->pending.push_back(r);
-        S->stats.submitted += 1;
     }
     S->cv.notify_all();
     if (request_id) *request_id = r->id;
@@ -427,12 +699,25 @@ extern "C" ngdbf_status ngdbf_server_destroy(ngdbf_server_t* S) {
         S->pending.clear();
     }
     S->cv.notify_all();
-    if (S->worker.joinable()) S->worker.join();
+    if (S->worker.joinable()) S->worker.join();     // admitted requests finish first, the kernel idles out
+    S->epoch_img[0] = S->epoch;                     // and any kernel left exits at once
+    cudaMemcpyAsync(&S->d_ring->stop_epoch, &S->epoch_img[0], 4, cudaMemcpyHostToDevice, S->pub_stream);
+    cudaStreamSynchronize(S->pub_stream);
+    cudaStreamSynchronize(S->serve_stream);
     for (cudaStream_t st : S->streams) {
         cudaStreamSynchronize(st);
         cudaStreamDestroy(st);
     }
-    for (auto& b : S->free_stage) cudaFreeHost(b.first);
+    cudaStreamDestroy(S->serve_stream);
+    cudaStreamDestroy(S->pub_stream);
+    cudaEventDestroy(S->ev_kernel);
+    cudaFree(S->d_ring);
+    cudaFree(S->d_claim);
+    cudaFree(S->d_done);
+    cudaFreeHost(S->stage);
+    cudaFreeHost(S->head_img);
+    cudaFreeHost(S->epoch_img);
+    cudaFreeHost(S->notify_host);
     for (Request* r : S->completed) delete r;
     delete S;
     return NGDBF_OK;

@@ -63,7 +63,7 @@ NGDBF_BATCH_GRAPH = 2
 class ngdbf_server_stats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("failed", ctypes.c_int64),
                 ("launches", ctypes.c_int64), ("frames", ctypes.c_int64), ("peak_bytes_in_use", ctypes.c_int64),
-                ("peak_concurrent_launches", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("peak_requests_on_device", ctypes.c_int32), ("admitted_into_running", ctypes.c_int32)]
 
 
 class ngdbf_host_stats(ctypes.Structure):
@@ -107,6 +107,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
                                       ctypes.POINTER(ngdbf_params), ctypes.c_uint64, ctypes.c_uint64,
                                       vp, vp, vp, ctypes.c_int64]
     lib.ngdbf_decode_noalloc.argtypes = lib.ngdbf_decode.argtypes
+    lib.ngdbf_decode_plain.argtypes = lib.ngdbf_decode.argtypes
     lib.ngdbf_decode_trace.argtypes = [vp, vp, ctypes.c_int64, ctypes.c_float, ctypes.POINTER(ngdbf_params),
                                        ctypes.c_uint64, ctypes.c_uint64, vp, vp, vp, ctypes.c_int64, vp, vp, vp]
     lib.ngdbf_batch_create.argtypes = [ctypes.POINTER(ngdbf_job), ctypes.c_int32, ctypes.c_uint64,
@@ -137,7 +138,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
                "ngdbf_batch_launch", "ngdbf_batch_destroy", "ngdbf_server_create", "ngdbf_server_submit",
                "ngdbf_server_poll", "ngdbf_server_wait", "ngdbf_server_get_stats", "ngdbf_server_destroy",
                "ngdbf_gaussian_range", "ngdbf_pool_usage", "ngdbf_last_host_stats", "ngdbf_mix_probe",
-               "ngdbf_generator_table", "ngdbf_batch_shape", "ngdbf_batch_use_shape"):
+               "ngdbf_generator_table", "ngdbf_batch_shape", "ngdbf_batch_use_shape", "ngdbf_decode_plain"):
         getattr(lib, fn).restype = ctypes.c_int
     if path is None:
         _lib = lib
@@ -189,6 +190,13 @@ def ngdbf_decode(code: int, y_ptr: int, n_frames: int, sigma: float, params: ngd
     lib = load()
     _check(lib, lib.ngdbf_decode(code, y_ptr, n_frames, sigma, ctypes.byref(params), seed, frame_offset,
                                  bits_ptr, iters_ptr, pass_ptr, stream))
+
+
+def ngdbf_decode_plain(code: int, y_ptr: int, n_frames: int, sigma: float, params: ngdbf_params, seed: int,
+                       frame_offset: int, bits_ptr: int, iters_ptr: int, pass_ptr: int, stream: int = 0) -> None:
+    lib = load()
+    _check(lib, lib.ngdbf_decode_plain(code, y_ptr, n_frames, sigma, ctypes.byref(params), seed, frame_offset,
+                                       bits_ptr, iters_ptr, pass_ptr, stream))
 
 
 def ngdbf_decode_trace(code: int, y_ptr: int, n_frames: int, sigma: float, params: ngdbf_params, seed: int,
@@ -285,7 +293,7 @@ def ngdbf_server_get_stats(server: int) -> dict:
     lib = load()
     st = ngdbf_server_stats()
     _check(lib, lib.ngdbf_server_get_stats(server, ctypes.byref(st)))
-    return {f: getattr(st, f) for f, _ in st._fields_ if f != "reserved"}
+    return {f: getattr(st, f) for f, _ in st._fields_}
 
 
 def ngdbf_server_destroy(server: int) -> None:
@@ -377,6 +385,21 @@ class DeviceCode:
         s = stream if stream is not None else torch.cuda.current_stream(y.device)
         ngdbf_decode(self.handle, y.data_ptr(), F, float(sigma), params, int(seed), int(frame_offset),
                      bits.data_ptr(), iters.data_ptr(), pas.data_ptr(), s.cuda_stream)
+        return bits, iters, pas
+
+    def decode_plain(self, y, sigma: float, params: ngdbf_params, seed: int = 1, frame_offset: int = 0,
+                     out=None, stream=None):
+        """decode() by the plain per-iteration kernels (baseline form; same results)."""
+        import torch
+        assert y.is_cuda and y.dtype == torch.float32 and y.is_contiguous() and y.shape[-1] == self.n
+        F = y.shape[0]
+        if out is None:
+            out = (torch.empty((F, (self.n + 7) // 8), dtype=torch.uint8, device=y.device),
+                   torch.empty(F, dtype=torch.int32, device=y.device), torch.empty(F, dtype=torch.uint8, device=y.device))
+        bits, iters, pas = out
+        s = stream if stream is not None else torch.cuda.current_stream(y.device)
+        ngdbf_decode_plain(self.handle, y.data_ptr(), F, float(sigma), params, int(seed), int(frame_offset),
+                           bits.data_ptr(), iters.data_ptr(), pas.data_ptr(), s.cuda_stream)
         return bits, iters, pas
 
     def decode_trace(self, y, sigma: float, params: ngdbf_params, trace_frames: int, seed: int = 1,

@@ -220,3 +220,40 @@ def test_convergence_error_from_gpu_outputs(O):
         assert np.allclose(f[gps == 1], dg.f_max(code, y, gb, y_max=2.5)[gps == 1])
     assert eps["M-NGDBF"] > eps["M-GDBF"] and eps["AT-NGDBF"] > eps["M-GDBF"]
     assert eps["M-NGDBF uniform"] > eps["M-GDBF"]
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 3 | U])
+def test_plain_per_iteration_form(O, variant):
+    """The plain per-iteration kernels give ngdbf_decode's results bit for bit (and the reference
+    decoder's), on a small code, the (3,6) N=1008 code and the (6,32) N=2048 code."""
+    for code, F, eb, kw in ((wl.peg_code(96, 48, 3, seed=11), 150, 2.5, dict(lam=0.95, t_max=60, smooth_window=16)),
+                            (wl.code_c1(), 300, 3.5, dict(lam=0.99, t_max=100, smooth_window=40)),
+                            (wl.code_c2(), 120, 3.75, dict(w=0.1875, theta=-0.7, eta=0.65, lam=0.993, y_max=2.0,
+                                                           t_max=200, smooth_window=64))):
+        y, _, sig = wl.frames(code, F, eb, seed=48)
+        gp, op = params_pair(variant=variant, **kw)
+        dc = ngdbf.DeviceCode.from_code(code)
+        try:
+            yt = torch.from_numpy(y).cuda()
+            a = [t.cpu().numpy() for t in dc.decode_plain(yt, sig, gp, seed=5, frame_offset=9)]
+            assert ngdbf.ngdbf_last_launch()["kernels"] == 3 * gp.t_max + 3
+            b = [t.cpu().numpy() for t in dc.decode(yt, sig, gp, seed=5, frame_offset=9)]
+        finally:
+            dc.close()
+        for u, v, name in zip(a, b, ("bits", "iters", "pass")):
+            assert np.array_equal(u, v), f"{code.name}: {name} differ from ngdbf_decode"
+        ob, oi, ops = O.decode_f32(code, y[:40], sig, op, seed=5, frame_offset=9, threads=THREADS)
+        assert np.array_equal(a[0][:40], ob) and np.array_equal(a[1][:40], oi) and np.array_equal(a[2][:40], ops)
+
+
+def test_plain_form_rejects_what_it_lacks():
+    code = wl.peg_code(96, 48, 3, seed=11)
+    dc = ngdbf.DeviceCode.from_code(code)
+    try:
+        y = torch.zeros((4, 96), dtype=torch.float32, device="cuda")
+        for kw in (dict(variant=4), dict(precision=ngdbf.NGDBF_FP16)):
+            with pytest.raises(ngdbf.NgdbfError) as e:
+                dc.decode_plain(y, 0.5, ngdbf.make_params(**kw))
+            assert e.value.status == ngdbf.NGDBF_ERR_UNSUPPORTED
+    finally:
+        dc.close()
