@@ -207,9 +207,10 @@ ngdbf_status ngdbf_decode_plain(const ngdbf_code_t* code, const float* y, int64_
  * the next chunk is copied, copies the outputs back, and returns when the
  * host outputs are written.  Page-locked host buffers give overlapped
  * copies; pageable ones work but serialize.  Same layouts as ngdbf_decode.
- * chunk_frames <= 0 picks a chunk size automatically: a quarter of the call,
- * between 256 MB and 2 GB of samples (at least 4096 frames); two chunks of
- * device scratch are held at a time.
+ * chunk_frames <= 0 picks chunk sizes automatically: a quarter of the call
+ * (between 256 MB and 2 GB of samples, at least 4096 frames), reached by doubling
+ * from an eighth of it so that little copying precedes the first decode; two
+ * chunks of device scratch are held at a time.
  */
 ngdbf_status ngdbf_decode_host(const ngdbf_code_t* code, const float* y_host, int64_t n_frames,
                                float sigma, const ngdbf_params* params, uint64_t seed,
@@ -278,7 +279,7 @@ ngdbf_status ngdbf_pool_usage(int32_t reset_high, int64_t* used_now, int64_t* us
  * and iteration limit, each with its own frames, sigma and parameters -- in
  * ONE persistent launch.  CTAs start on jobs in proportion to their estimated
  * work (frames x n x (T + 1)); a CTA whose job has no unclaimed frame left and
- * whose slots are idle moves to the job with the most unclaimed frames.  Each
+ * whose slots are idle moves to the job with the most unclaimed work.  Each
  * frame's result is the one ngdbf_decode gives for the same job (same seed,
  * frame id = frame_offset + index): bit for bit, alone or in any mix.
  * Restrictions within one table: every job has the same params.variant and

@@ -742,15 +742,19 @@ ngdbf_status ngdbf_decode_host(const ngdbf_code_t* C, const float* y_host, int64
     if (n_frames == 0) return NGDBF_OK;
     if (!y_host || !bits_host || !iters_host || !pass_host) return fail(NGDBF_ERR_INVALID_ARG, "NULL buffer");
     const int64_t n = C->n, nb = (C->n + 7) / 8;
+    // chunk sizes: the caller's, or a ramp -- an eighth of a quarter of the call first (so
+    // that little copying is exposed before the first decode), doubling up to a quarter of
+    // the call (so that only the last chunk's tail, where a CTA waits for its slowest frame,
+    // is exposed), chunks between 256 MB and 2 GB of samples and at least 4096 frames
+    int64_t first_chunk = chunk_frames;
     if (chunk_frames <= 0) {
-        // A quarter of the call per chunk (so that copies overlap decoding and only the
-        // last chunk's tail, where a CTA waits for its slowest frame, is exposed), between
-        // 256 MB and 2 GB of samples, at least 4096 frames.
         const int64_t lo = std::max<int64_t>(4096, (int64_t)(256ll << 20) / (4 * n));
         const int64_t hi = std::max<int64_t>(lo, (int64_t)(2048ll << 20) / (4 * n));
         chunk_frames = std::min(hi, std::max(lo, (n_frames + 3) / 4));
+        first_chunk = std::max<int64_t>(std::min<int64_t>(4096, chunk_frames), chunk_frames / 8);
     }
     chunk_frames = std::min(chunk_frames, n_frames);
+    first_chunk = std::min(first_chunk, chunk_frames);
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
@@ -783,9 +787,10 @@ ngdbf_status ngdbf_decode_host(const ngdbf_code_t* C, const float* y_host, int64
         }
     };
     int64_t kernels = 0, chunks = 0;
-    for (int64_t off = 0, c = 0; off < n_frames && rs == NGDBF_OK; off += chunk_frames, ++c) {
+    for (int64_t off = 0, c = 0, size = first_chunk; off < n_frames && rs == NGDBF_OK;
+         off += size, size = std::min(2 * size, chunk_frames), ++c) {
         const int b = (int)(c & 1);
-        const int64_t F = std::min(chunk_frames, n_frames - off);
+        const int64_t F = std::min(size, n_frames - off);
         unsigned char* p = static_cast<unsigned char*>(buf[b]);
         float* dy = reinterpret_cast<float*>(p);
         uint8_t* dbits = p + align256(by);
@@ -1013,6 +1018,25 @@ std::vector<int32_t> assign_ctas_capped(const std::vector<int64_t>& frames, cons
     return first;
 }
 
+// Dynamic shared memory of a job-table launch in which every job gets its own layout
+// (job_layout, as the kernels evaluate it): the largest job's bytes, each job taking as many
+// of the `tables` as fit in `limit`; -1 when some job does not fit at all.  With a cluster of
+// C > 1 CTAs, jobs of at least split_min_n symbols hold their share of the symbols per CTA.
+int table_smem(const ngdbf_job* jobs, int32_t n_jobs, int C, int split_min_n, bool adapt, bool st, bool wide,
+               int tables, int limit) {
+    int total = 0;
+    for (int j = 0; j < n_jobs; ++j) {
+        const ngdbf_code* c = jobs[j].code;
+        const int n_local = (C > 1 && c->n >= split_min_n) ? split_local_max(c->n, C) : c->n;
+        int tb = 0;
+        const SmemLayout L = job_layout(c->n, c->m, jobs[j].params.t_max, c->dv_max, c->dc_max, adapt, st, wide,
+                                        tables, n_local, limit, &tb);
+        if (L.total > limit) return -1;
+        total = std::max(total, L.total);
+    }
+    return total;
+}
+
 ngdbf_status plan_table(const ngdbf_job* jobs, int32_t n_jobs, int dev, TablePlan* out) {
     TablePlan& T = *out;
     T = TablePlan();
@@ -1046,20 +1070,39 @@ ngdbf_status plan_table(const ngdbf_job* jobs, int32_t n_jobs, int dev, TablePla
     e = cudaFuncGetAttributes(&fa, multi_kernel_fn(variant, precision, state, T.wide));
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncGetAttributes");
     const int limit = smem_optin - (int)fa.sharedSizeBytes;
-    PlacementChoice pc;
-    ngdbf_status s = choose_placement(dev, T.n_max, T.m_max, T.t_max, T.dv_max, T.dc_max, adapt, state, limit,
-                                      [&](bool st) { return (const void*)multi_kernel_fn(variant, precision, st, T.wide); },
-                                      &pc);
-    if (s != NGDBF_OK) return s;
-    void* fn = multi_kernel_fn(variant, precision, pc.st_smem, T.wide);
-    T.fn = fn;
-    T.smem = pc.L.total;
-    T.st_smem = pc.st_smem;
-    T.placement = pc.placement;
-    T.state_global = state && !pc.st_smem;
+    // the state in shared memory whenever every job fits with it there; then the most resident
+    // warps per SM, the most CTAs per SM, more tables in shared memory (as in choose_placement)
+    int best_warps = 0, best_bps = 0;
+    for (const bool st : {true, false}) {
+        if (st && !state) continue;
+        if (best_bps > 0) break;
+        void* fn = multi_kernel_fn(variant, precision, st, T.wide);
+        e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, limit);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+        for (const int tb : {kTabChk | kTabSym, kTabChk, 0}) {
+            const int total = table_smem(jobs, n_jobs, 1, INT32_MAX, adapt, st, T.wide, tb, limit);
+            if (total < 0) continue;
+            for (const int block : {1024, 512, 256}) {
+                int bps = 0;
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, (const void*)fn, block, total);
+                if (e != cudaSuccess) return cuda_fail(e, "occupancy");
+                const int warps = bps * block / 32;
+                if (bps > 0 && (warps > best_warps || (warps == best_warps && bps > best_bps))) {
+                    best_warps = warps;
+                    best_bps = bps;
+                    T.fn = fn;
+                    T.smem = total;
+                    T.st_smem = st;
+                    T.placement = tb;
+                }
+            }
+        }
+    }
+    if (best_bps == 0) return fail(NGDBF_ERR_UNSUPPORTED, "code too large for the shared-memory decision words");
+    T.state_global = state && !T.st_smem;
     for (int block : {1024, 512, 256}) {
         int bps = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, (const void*)fn, block, pc.L.total);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, (const void*)T.fn, block, T.smem);
         if (e != cudaSuccess) return cuda_fail(e, "occupancy");
         if (bps > 0) T.shapes.push_back({block, bps});
     }
@@ -1094,15 +1137,15 @@ ngdbf_status table_shapes(const TablePlan& T, const ngdbf_job* jobs, int32_t n_j
         const int limit = smem_optin - (int)fa.sharedSizeBytes;
         for (const int tb : {kTabChk | kTabSym, kTabChk, 0}) {
             if (tb == T.placement) continue;
-            const SmemLayout L = smem_layout(T.n_max, T.m_max, T.t_max, T.dv_max, T.dc_max, adapt, T.st_smem, tb);
-            if (L.total > limit) continue;
+            const int total = table_smem(jobs, n_jobs, 1, INT32_MAX, adapt, T.st_smem, wide, tb, limit);
+            if (total < 0 || total == T.smem) continue;    // no fit, or the same layouts as the plan's
             for (const int block : {1024, 512}) {
                 int bps = 0;
-                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, (const void*)T.fn, block, L.total);
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, (const void*)T.fn, block, total);
                 if (e != cudaSuccess) return cuda_fail(e, "occupancy");
                 if (bps <= 0) continue;
                 TableShape c;
-                c.fn = T.fn; c.block = block; c.cluster = 1; c.grid_max = T.sm_count * bps; c.smem = L.total;
+                c.fn = T.fn; c.block = block; c.cluster = 1; c.grid_max = T.sm_count * bps; c.smem = total;
                 c.placement = tb; c.n_local = T.n_max; c.split_min_n = INT32_MAX;
                 c.st_smem = T.st_smem; c.state_global = T.state_global;
                 out->push_back(c);
@@ -1132,14 +1175,16 @@ ngdbf_status table_shapes(const TablePlan& T, const ngdbf_job* jobs, int32_t n_j
             e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, limit);
             if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
             bool any = false;
+            int prev = -1;
             for (const int tb : {kTabChk | kTabSym, kTabChk, 0}) {
-                const SmemLayout L = smem_layout(T.n_max, T.m_max, T.t_max, T.dv_max, T.dc_max, adapt, st, tb, n_local);
-                if (L.total > limit) continue;
+                const int total = table_smem(jobs, n_jobs, C, kSplitMinN, adapt, st, wide, tb, limit);
+                if (total < 0 || total == prev) continue;    // no fit, or the same layouts again
+                prev = total;
                 for (const int block : {1024, 512}) {
-                    const int clusters = max_active_clusters(fn, C, block, L.total);
+                    const int clusters = max_active_clusters(fn, C, block, total);
                     if (clusters <= 0) continue;
                     TableShape c;
-                    c.fn = fn; c.block = block; c.cluster = C; c.grid_max = clusters * C; c.smem = L.total;
+                    c.fn = fn; c.block = block; c.cluster = C; c.grid_max = clusters * C; c.smem = total;
                     c.placement = tb; c.n_local = n_local; c.split_min_n = kSplitMinN;
                     c.st_smem = st; c.state_global = state && !st;
                     out->push_back(c);
@@ -1180,6 +1225,7 @@ ngdbf_status batch_set_shape(ngdbf_batch* B, int k) {
     B->args.cluster = C;
     B->args.split_min_n = sh.split_min_n;
     B->args.n_local = sh.n_local;
+    B->args.smem_bytes = sh.smem;
     B->args.st_global = sh.state_global ? reinterpret_cast<uint16_t*>(B->d_st) : nullptr;
     std::vector<int64_t> cap(B->n_jobs);
     int64_t clusters = 0;

@@ -148,7 +148,8 @@ struct DecodeArgs {
 
 // Launch of a job table: CTA c starts with job first_job[c] and, once that job has
 // no unclaimed frame left and its slots are idle, moves to the job with the most
-// unclaimed frames.  Shared memory is laid out for the largest code and T.
+// unclaimed work (frames x n x (T + 1)).  Each job gets its own shared-memory layout
+// (job_layout); the launch has room for the largest.
 struct MultiArgs {
     const Job* jobs;
     int32_t n_jobs;
@@ -158,6 +159,7 @@ struct MultiArgs {
     // cluster launches: jobs with n >= split_min_n are split over the `cluster` CTAs of a
     // cluster (n_local symbols per CTA at most); the per-CTA arrays hold n_local symbols
     int32_t cluster, split_min_n, n_local;
+    int32_t smem_bytes;         // dynamic shared memory of the launch (every job's layout fits)
     void* yslots;               // [grid][pad4(n_local)/4][32][4]
     uint16_t* st_global;        // [grid][pad4(n_local)/4][32][4] when the state is not in shared memory
     GenConsts G;
@@ -196,9 +198,13 @@ struct SmemLayout {
 // the 32-bit unsatisfied mask of each check and cnt, per symbol, the bit-sliced count
 // (seven words, bit f for slot f) and d_v(k) (32 bytes).  xw has room for whole groups
 // and the zero sentinel word at index n.
+// `wide` (< 0: from dv_max) selects the count and syndrome formats, which follow the kernel's
+// WIDE template argument when a job table lays out a job of lower degree.
 __host__ __device__ inline SmemLayout smem_layout(int n, int m, int t_max, int dv_max, int dc_max,
-                                                  bool need_thr, bool st_smem, int tables, int n_local = -1) {
+                                                  bool need_thr, bool st_smem, int tables, int n_local = -1,
+                                                  int wide = -1) {
     if (n_local < 0) n_local = n;   // symbols whose counts, state and M(k) rows this CTA holds
+    const bool wd = wide < 0 ? dv_max > 7 : wide != 0;
     SmemLayout L;
     int o = 0;
     auto take = [&](int bytes, int align) {
@@ -207,7 +213,7 @@ __host__ __device__ inline SmemLayout smem_layout(int n, int m, int t_max, int d
         o += bytes;
         return r;
     };
-    const int cnt_bytes = dv_max <= 7 ? 16 : 32;
+    const int cnt_bytes = wd ? 32 : 16;
     L.off_frame = take(kSlots * 8, 16);
     L.off_start = take(kSlots * 4, 16);
     L.off_ctl = take(8 * 4, 16);
@@ -216,7 +222,7 @@ __host__ __device__ inline SmemLayout smem_layout(int n, int m, int t_max, int d
     L.off_icdf = take(256 * 16, 16);       // inverse normal CDF coefficients
     L.off_cnt = take(pad4(n_local) * cnt_bytes, 16);
     L.off_xw = take(pad4(n + 1) * 4, 16);
-    L.off_sw = take((m + 1) * (dv_max <= 7 ? 16 : 4), 16);
+    L.off_sw = take((m + 1) * (wd ? 4 : 16), 16);
     // all 512 values of the 9-bit u field: an idle slot's counter may pass T (its lookups are
     // don't-care but stay inside the table)
     L.off_thr = need_thr ? take((kUMask + 1) * 4, 16) : -1;
@@ -224,6 +230,25 @@ __host__ __device__ inline SmemLayout smem_layout(int n, int m, int t_max, int d
     L.off_chk = (tables & kTabChk) ? take(dc_max * m * 2, 16) : -1;
     L.off_sym = (tables & kTabSym) ? take(n_local * dv_max * 2 + n_local, 16) : -1;
     L.total = (o + 15) / 16 * 16;
+    return L;
+}
+
+// Layout of one job of a job table: arrays sized for the job's own code (n_local symbols per
+// CTA: its share when split over a cluster) in the launch's count and syndrome format, with
+// as many of the adjacency tables that `tables` allows as fit in `bytes` (both, then N(i)
+// alone, then none); *tables_out receives the placement taken.  Host planning and the kernel
+// evaluate it alike, so the launch's shared memory is the largest job's, not the layout of
+// the table's maxima.
+__host__ __device__ inline SmemLayout job_layout(int n, int m, int t_max, int dv_max, int dc_max, bool need_thr,
+                                                 bool st_smem, bool wide, int tables, int n_local, int bytes,
+                                                 int* tables_out) {
+    const int opts[3] = {tables & (kTabChk | kTabSym), tables & kTabChk, 0};
+    SmemLayout L{};
+    for (int i = 0; i < 3; ++i) {
+        L = smem_layout(n, m, t_max, dv_max, dc_max, need_thr, st_smem, opts[i], n_local, wide ? 1 : 0);
+        *tables_out = opts[i];
+        if (L.total <= bytes) break;
+    }
     return L;
 }
 

@@ -10,24 +10,29 @@ __global__ void __launch_bounds__(1024) ngdbf_multi_kernel(const __grid_constant
     using HeldT = typename Held<PREC>::T;
     __shared__ Job job;
     __shared__ int32_t next_job;
-    const SmemLayout L = smem_layout(A.n_max, A.m_max, A.t_max, A.dv_max, A.dc_max, ADAPT,
-                                     ST_SMEM && (ADAPT || SMOOTH), A.placement);
     HeldT* ys = static_cast<HeldT*>(A.yslots) + (size_t)blockIdx.x * pad4(A.n_max) * kSlots;
     uint16_t* st = A.st_global ? A.st_global + (size_t)blockIdx.x * pad4(A.n_max) * kSlots : nullptr;
     int j = A.first_job[blockIdx.x];
     while (j >= 0) {
         if (threadIdx.x == 0) job = A.jobs[j];
         __syncthreads();
-        decode_job<ADAPT, SMOOTH, ST_SMEM, WIDE, PREC>(job, job.thr, A.G, L, A.placement, ys, st);
-        // the next job: the one with the most unclaimed frames (none left: done)
+        // shared memory laid out for this job's code (the launch has room for the largest)
+        int tables = 0;
+        const SmemLayout L = job_layout(job.n, job.m, job.t_max, job.dv_max, job.dc_max, ADAPT,
+                                        ST_SMEM && (ADAPT || SMOOTH), WIDE, A.placement, job.n, A.smem_bytes,
+                                        &tables);
+        decode_job<ADAPT, SMOOTH, ST_SMEM, WIDE, PREC>(job, job.thr, A.G, L, tables, ys, st);
+        // the next job: the one with the most unclaimed work (none left: done)
         if (threadIdx.x == 0) {
             long long best = 0;
             int pick = -1;
             for (int i = 0; i < A.n_jobs; ++i) {
                 const unsigned long long claimed = *(volatile unsigned long long*)A.jobs[i].queue;
                 const long long left = A.jobs[i].n_frames - (long long)min(claimed, (unsigned long long)A.jobs[i].n_frames);
-                if (left > best) {
-                    best = left;
+                // its estimated remaining work: unclaimed frames x n x (T + 1)
+                const long long work = left * A.jobs[i].n * (long long)(A.jobs[i].t_max + 1);
+                if (work > best) {
+                    best = work;
                     pick = i;
                 }
             }

@@ -18,16 +18,21 @@ __global__ void __launch_bounds__(1024) ngdbf_multi_cluster_kernel(const __grid_
     __shared__ Job job;
     __shared__ int32_t next_job;
     const int C = (int)cluster.num_blocks(), rank = (int)cluster.block_rank();
-    const SmemLayout L = smem_layout(A.n_max, A.m_max, A.t_max, A.dv_max, A.dc_max, ADAPT,
-                                     ST_SMEM && (ADAPT || SMOOTH), A.placement, A.n_local);
     HeldT* ys = static_cast<HeldT*>(A.yslots) + (size_t)blockIdx.x * pad4(A.n_local) * kSlots;
     uint16_t* st = A.st_global ? A.st_global + (size_t)blockIdx.x * pad4(A.n_local) * kSlots : nullptr;
     int j = A.first_job[blockIdx.x / C];
     while (j >= 0) {
         if (threadIdx.x == 0) job = A.jobs[j];
         __syncthreads();
-        const Split S = job.n >= A.split_min_n ? split_range(rank, C, job.n) : Split{0, 1, 0, job.n};
-        decode_job<ADAPT, SMOOTH, ST_SMEM, WIDE, PREC, true>(job, job.thr, A.G, L, A.placement, ys, st, S);
+        const bool sp = job.n >= A.split_min_n;
+        const Split S = sp ? split_range(rank, C, job.n) : Split{0, 1, 0, job.n};
+        // shared memory laid out for this job's share of symbols (the same in every CTA of
+        // the cluster, so peer addresses agree)
+        int tables = 0;
+        const SmemLayout L = job_layout(job.n, job.m, job.t_max, job.dv_max, job.dc_max, ADAPT,
+                                        ST_SMEM && (ADAPT || SMOOTH), WIDE, A.placement,
+                                        sp ? split_local_max(job.n, C) : job.n, A.smem_bytes, &tables);
+        decode_job<ADAPT, SMOOTH, ST_SMEM, WIDE, PREC, true>(job, job.thr, A.G, L, tables, ys, st, S);
         cluster.sync();
         if (rank == 0 && threadIdx.x == 0) {
             long long best = 0;
@@ -35,8 +40,10 @@ __global__ void __launch_bounds__(1024) ngdbf_multi_cluster_kernel(const __grid_
             for (int i = 0; i < A.n_jobs; ++i) {
                 const unsigned long long claimed = *(volatile unsigned long long*)A.jobs[i].queue;
                 const long long left = A.jobs[i].n_frames - (long long)min(claimed, (unsigned long long)A.jobs[i].n_frames);
-                if (left > best) {
-                    best = left;
+                // its estimated remaining work: unclaimed frames x n x (T + 1)
+                const long long work = left * A.jobs[i].n * (long long)(A.jobs[i].t_max + 1);
+                if (work > best) {
+                    best = work;
                     pick = i;
                 }
             }
