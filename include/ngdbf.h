@@ -275,6 +275,23 @@ ngdbf_status ngdbf_decode_noalloc(const ngdbf_code_t* code, const float* y, int6
 ngdbf_status ngdbf_pool_usage(int32_t reset_high, int64_t* used_now, int64_t* used_high);
 
 /*
+ * Page-locked host memory for the host-buffer entry points (ngdbf_decode_host, the server).
+ * A copy engine reading page-locked memory translates every page it touches; small pages
+ * scattered in physical memory make those translations miss, and copies from such a buffer
+ * were measured at 8-20 GB/s against 211 GB/s from other buffers of the same process on a
+ * GB300 host.  Requests of at least one transparent huge page (ngdbf_host_huge_page_bytes:
+ * 512 MiB with 64 KiB base pages, 2 MiB with 4 KiB ones) are mapped on huge-page boundaries,
+ * advised for huge pages and registered with CUDA (the mapping rounded up to whole huge
+ * pages); smaller requests, and systems where that fails, get cudaHostAlloc memory.  Contents
+ * are undefined.  The caller owns the block and returns it with ngdbf_host_free (NULL: no-op).
+ * Errors: INVALID_ARG (NULL out, bytes == 0, a pointer not from ngdbf_host_alloc), OOM, CUDA.
+ */
+ngdbf_status ngdbf_host_alloc(size_t bytes, void** out);
+ngdbf_status ngdbf_host_free(void* p);
+/* Transparent huge-page size the allocator aligns to (0 when the system reports none). */
+ngdbf_status ngdbf_host_huge_page_bytes(int64_t* out);
+
+/*
  * Job tables: several decode jobs -- codes of different length, rate, degree
  * and iteration limit, each with its own frames, sigma and parameters -- in
  * ONE persistent launch.  CTAs start on jobs in proportion to their estimated

@@ -9,7 +9,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 LIB_PATH = os.path.join(PKG, "libngdbf.so")
 SOURCES = [os.path.join(CSRC, f) for f in ("ngdbf_decode.cu", "ngdbf_multi.cu", "ngdbf_multi_cluster.cu",
-                                           "ngdbf_server.cu", "ngdbf_plain.cu")]
+                                           "ngdbf_server.cu", "ngdbf_plain.cu", "ngdbf_hostmem.cu")]
 HEADERS = [os.path.join(CSRC, h) for h in ("ngdbf_device.cuh", "ngdbf_kernels.cuh", "ngdbf_multi.h", "ngdbf_host.h")]
 DEPS = SOURCES + HEADERS + [os.path.join(ROOT, "include", "ngdbf.h")]
 

@@ -129,6 +129,9 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.ngdbf_generator_table.argtypes = [ctypes.POINTER(ctypes.c_float)]
     lib.ngdbf_mix_probe.argtypes = [ctypes.c_int32, vp, ctypes.POINTER(ctypes.c_int64), vp]
     lib.ngdbf_pool_usage.argtypes = [ctypes.c_int32, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
+    lib.ngdbf_host_alloc.argtypes = [ctypes.c_size_t, ctypes.POINTER(vp)]
+    lib.ngdbf_host_free.argtypes = [vp]
+    lib.ngdbf_host_huge_page_bytes.argtypes = [ctypes.POINTER(ctypes.c_int64)]
     lib.ngdbf_last_launch.argtypes = [ctypes.POINTER(ngdbf_launch_info)]
     lib.ngdbf_last_host_stats.argtypes = [ctypes.POINTER(ngdbf_host_stats)]
     lib.ngdbf_last_error.argtypes = []
@@ -138,7 +141,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
                "ngdbf_batch_launch", "ngdbf_batch_destroy", "ngdbf_server_create", "ngdbf_server_submit",
                "ngdbf_server_poll", "ngdbf_server_wait", "ngdbf_server_get_stats", "ngdbf_server_destroy",
                "ngdbf_gaussian_range", "ngdbf_pool_usage", "ngdbf_last_host_stats", "ngdbf_mix_probe",
-               "ngdbf_generator_table", "ngdbf_batch_shape", "ngdbf_batch_use_shape", "ngdbf_decode_plain"):
+               "ngdbf_generator_table", "ngdbf_batch_shape", "ngdbf_batch_use_shape", "ngdbf_decode_plain",
+               "ngdbf_host_alloc", "ngdbf_host_free", "ngdbf_host_huge_page_bytes"):
         getattr(lib, fn).restype = ctypes.c_int
     if path is None:
         _lib = lib
@@ -328,6 +332,42 @@ def ngdbf_pool_usage(reset_high: bool = False) -> tuple[int, int]:
     now, high = ctypes.c_int64(), ctypes.c_int64()
     _check(lib, lib.ngdbf_pool_usage(1 if reset_high else 0, ctypes.byref(now), ctypes.byref(high)))
     return now.value, high.value
+
+
+def ngdbf_host_alloc(nbytes: int) -> int:
+    """Page-locked host block of nbytes (huge-page backed when large); free with ngdbf_host_free."""
+    lib = load()
+    p = ctypes.c_void_p()
+    _check(lib, lib.ngdbf_host_alloc(nbytes, ctypes.byref(p)))
+    return p.value
+
+
+def ngdbf_host_free(ptr: int) -> None:
+    lib = load()
+    _check(lib, lib.ngdbf_host_free(ptr))
+
+
+def ngdbf_host_huge_page_bytes() -> int:
+    lib = load()
+    v = ctypes.c_int64()
+    _check(lib, lib.ngdbf_host_huge_page_bytes(ctypes.byref(v)))
+    return v.value
+
+
+def host_empty(shape, dtype=np.float32):
+    """A CPU torch tensor over a block from ngdbf_host_alloc (page-locked; returned to the
+    library when the tensor and its views are gone)."""
+    import weakref
+    import torch
+    shape = tuple(int(d) for d in (shape if isinstance(shape, (tuple, list)) else (shape,)))
+    dt = np.dtype(dtype)
+    nbytes = max(1, int(np.prod(shape, dtype=np.int64)) * dt.itemsize)
+    ptr = ngdbf_host_alloc(nbytes)
+    raw = (ctypes.c_uint8 * nbytes).from_address(ptr)
+    weakref.finalize(raw, ngdbf_host_free, ptr)
+    arr = np.frombuffer(raw, dtype=np.uint8, count=nbytes)
+    arr = arr[: int(np.prod(shape, dtype=np.int64)) * dt.itemsize].view(dt).reshape(shape)
+    return torch.from_numpy(arr)
 
 
 def ngdbf_last_host_stats() -> dict:

@@ -148,3 +148,21 @@ def test_generator_table_equals_the_reference_and_an_independent_derivation():
             ulp = np.spacing(np.abs(w)).astype(np.float64)
             worst = max(worst, float(np.max(np.abs(c - w.astype(np.float64)) / ulp)))
     assert worst <= 1.0, f"{worst:.2f} ulp"
+
+
+def test_host_allocator_validation_without_a_device(lib):
+    """ngdbf_host_alloc/free: argument errors and the huge-page size need no device."""
+    p = ctypes.c_void_p()
+    assert lib.ngdbf_host_alloc(0, ctypes.byref(p)) == ngdbf.NGDBF_ERR_INVALID_ARG
+    assert lib.ngdbf_host_alloc(64, None) == ngdbf.NGDBF_ERR_INVALID_ARG
+    assert lib.ngdbf_host_free(None) == ngdbf.NGDBF_OK
+    buf = ctypes.create_string_buffer(64)
+    assert lib.ngdbf_host_free(ctypes.addressof(buf)) == ngdbf.NGDBF_ERR_INVALID_ARG
+    assert "ngdbf_host_alloc" in lib.ngdbf_last_error().decode()
+    hp = ctypes.c_int64(-1)
+    assert lib.ngdbf_host_huge_page_bytes(ctypes.byref(hp)) == ngdbf.NGDBF_OK
+    try:
+        want = int(open("/sys/kernel/mm/transparent_hugepage/hpage_pmd_size").read())
+    except OSError:
+        want = 0
+    assert hp.value == want

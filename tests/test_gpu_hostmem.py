@@ -1,0 +1,58 @@
+"""Page-locked host blocks from ngdbf_host_alloc: pinned, usable by the host-buffer decode
+(bit-identical to the same decode from torch's pinned memory), returned on free."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_1402_2773_gb300 import ngdbf
+from paper_1402_2773_gb300 import workload as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.init()
+    return ngdbf.load()
+
+
+def test_large_block_is_huge_page_aligned_and_pinned():
+    hp = ngdbf.ngdbf_host_huge_page_bytes()
+    nbytes = max(hp, 1 << 21) + 12345          # at least one huge page: the mapped path
+    t = ngdbf.host_empty(nbytes, np.uint8)
+    assert t.is_pinned()
+    if hp:
+        assert t.data_ptr() % hp == 0
+    t.numpy()[:] = 7
+    d = t.cuda()
+    assert int(d[-1].item()) == 7 and int(d.sum().item()) == 7 * nbytes
+
+
+def test_small_block_and_free():
+    p = ngdbf.ngdbf_host_alloc(4096)
+    ngdbf.ngdbf_host_free(p)
+    with pytest.raises(ngdbf.NgdbfError):
+        ngdbf.ngdbf_host_free(p)                  # already returned
+
+
+def test_decode_host_from_library_blocks_matches_torch_pinned():
+    code = wl.code_c1()
+    F = 3000
+    y, _, sig = wl.frames(code, F, 3.5, seed=77)
+    dc = ngdbf.DeviceCode.from_code(code)
+    gp = ngdbf.make_params(w=0.75, theta=-0.9, eta=0.96, y_max=2.5, t_max=100, variant=0)
+    nb = (code.n + 7) // 8
+    ya = ngdbf.host_empty((F, code.n), np.float32)
+    ya.numpy()[:] = y
+    outs_a = (ngdbf.host_empty((F, nb), np.uint8), ngdbf.host_empty(F, np.int32), ngdbf.host_empty(F, np.uint8))
+    yb = torch.from_numpy(y).pin_memory()
+    outs_b = (torch.empty((F, nb), dtype=torch.uint8).pin_memory(), torch.empty(F, dtype=torch.int32).pin_memory(),
+              torch.empty(F, dtype=torch.uint8).pin_memory())
+    dc.decode_host(ya, sig, gp, seed=5, out=outs_a, chunk_frames=1024)
+    dc.decode_host(yb, sig, gp, seed=5, out=outs_b, chunk_frames=1024)
+    for a, b in zip(outs_a, outs_b):
+        assert torch.equal(a, b)
+    dc.close()
