@@ -112,6 +112,19 @@ def max_over_ranks(value: float, device) -> float:
     return float(t.item())
 
 
+def host_blocks(ngdbf, tensors):
+    """Page-locked blocks under `tensors`: bytes and the share the kernel backs with huge pages."""
+    tot = huge = 0
+    for t in tensors:
+        try:
+            b, h = ngdbf.ngdbf_host_block_info(t.data_ptr())
+        except Exception:
+            return None
+        tot += b
+        huge += max(h, 0)
+    return {"bytes": tot, "huge_page_fraction": round(huge / tot, 4) if tot else None}
+
+
 def make_inputs(code, frames, rank, world, pinned=False):
     """Seeded frames per Eb/N0 point; pinned=True puts them in page-locked host blocks from the
     library's allocator (huge-page backed, so copies from them run at the link rate)."""
@@ -361,7 +374,8 @@ def run_ours(args):
            "h2d_bytes_per_step": F * code.n * 4 * len(EBN0_DB),
            "d2h_bytes_per_step": F * (nb + 4 + 1) * len(EBN0_DB), "steps": e2e_steps,
            "matches_device_run": bool(e2e_ok),
-           "host_buffers": "page-locked, from ngdbf_host_alloc (huge-page backed)",
+           "host_buffers": "page-locked, from ngdbf_host_alloc (huge pages requested)",
+           "host_input_blocks": host_blocks(ngdbf, ys_host),
            # CUDA events around each chunk of ngdbf_decode_host (device clock)
            "h2d_gbs": tot["h2d_bytes"] / max(tot["h2d_ms"], 1e-9) / 1e6,
            "d2h_gbs": tot["d2h_bytes"] / max(tot["d2h_ms"], 1e-9) / 1e6,
@@ -447,8 +461,11 @@ def run_multicode(args):
         sig.append(s_)
         gps.append(ngdbf.make_params(**jb["params"]))
     stream = torch.cuda.current_stream()
+    tune = args.shape is None
     batch = ngdbf.Batch([(dc, y, s_, gp, jb["offset"]) for dc, y, s_, gp, jb in zip(dcs, ys, sig, gps, jobs)],
-                        seed=DECODER_SEED, flags=ngdbf.NGDBF_BATCH_GRAPH | ngdbf.NGDBF_BATCH_TUNE)
+                        seed=DECODER_SEED, flags=ngdbf.NGDBF_BATCH_GRAPH | (ngdbf.NGDBF_BATCH_TUNE if tune else 0))
+    if not tune:
+        batch.use_shape(args.shape)
     batch.launch(stream)
     launch = ngdbf.ngdbf_last_launch()
     shapes = batch.shapes()
@@ -509,7 +526,8 @@ def run_multicode(args):
             "data": "synthetic (seeded PEG codes, random information words, AWGN)",
             "config": {"workload": "uneven multi-code batch: five PEG codes, geometric frame counts "
                                    "(mean 4096), per-code Eb/N0 and T, SM-NGDBF, one persistent launch "
-                                   "(CUDA graph; shape tuned over block size x cluster size x table placement)",
+                                   "(CUDA graph; shape tuned over block size x cluster size x table placement)"
+                                   if tune else f"... candidate shape {args.shape} (not tuned)",
                        "codes": per_code, "tuned_shape": batch.shape(), "candidate_shapes": len(shapes),
                        "l2": "inputs and slot state smaller than L2 between launches (both arms alike)"},
             "plain_per_iteration": {"value": fps_iter, "unit": "frames/s", "ms_per_step": t_iter / args.steps * 1e3,
@@ -564,6 +582,7 @@ def run_serving(args):
     ngdbf.load()
     specs = multicode_jobs(rank)
     codes = [jb["code"] for jb in specs]
+    dvs = [int(c.dense().sum(axis=0).max()) for c in codes]
     dcs = [ngdbf.DeviceCode.from_code(c) for c in codes]
     params = [ngdbf.make_params(**jb["params"]) for jb in specs]
     # every input pool in one page-locked block from the library's allocator
@@ -576,6 +595,7 @@ def run_serving(args):
             pos += SERVE_POOL * code.n
             _, _, sig = wl.frames(code, SERVE_POOL, eb, seed=DATA_SEED + 100 * c + b, out=buf.numpy())
             pools[(c, b)] = (buf, sig)
+    pool_blocks = host_blocks(ngdbf, [flat])
 
     def outputs(trace):
         return [(torch.empty((F, (codes[c].n + 7) // 8), dtype=torch.uint8, pin_memory=True),
@@ -631,6 +651,9 @@ def run_serving(args):
             lat_s, span_s, stats, outs_s = run_server(trace)
             lat_p, span_p, outs_p = run_plain(trace)
             same = all(all(torch.equal(a, b) for a, b in zip(x, y)) for x, y in zip(outs_s, outs_p))
+            # algorithmic lane operations of the iterations the frames needed (FP32 count)
+            ops = sum(float(o[1].numpy().astype(np.int64).sum()) * codes[c].n * ops_per_symbol_iter(dvs[c])
+                      for (_, c, _, _, _, _), o in zip(trace, outs_s))
             res[label] = {
                 "rate_requests_per_s": rate, "requests": n_req, "frames": frames,
                 "server_frames_per_s": frames / span_s, "server_requests_per_s": n_req / span_s,
@@ -639,8 +662,12 @@ def run_serving(args):
                 "plain_frames_per_s": frames / span_p,
                 "plain_latency_ms": {"p50": float(np.percentile(lat_p, 50)) * 1e3,
                                      "p99": float(np.percentile(lat_p, 99)) * 1e3},
-                "results_identical": bool(same), "server_stats": stats}
+                "results_identical": bool(same), "server_stats": stats,
+                "server_lane_op_s": ops / span_s}
+        probe = mix_probe(ngdbf, torch.cuda.current_stream())
     clocks = clk.summary()
+    for label in res:
+        res[label]["server_alu_frac"] = res[label]["server_lane_op_s"] / probe["lane_op_s"]
     if rank == 0:
         off = res["offered"]
         print(json.dumps({
@@ -652,7 +679,7 @@ def run_serving(args):
                                    "codes, Eb/N0 uniform 3-5 dB, SM-NGDBF, 8 GiB device budget, 4 streams, "
                                    "up to 256 requests per launch; input pools page-locked (ngdbf_host_alloc)",
                        "codes": [c.name for c in codes]},
-            "serving": res, "clocks": clocks,
+            "serving": res, "clocks": clocks, "input_pool_blocks": pool_blocks,
             "e2e": {"value": off["server_frames_per_s"], "unit": "frames/s",
                     "h2d_bytes_per_step": None, "d2h_bytes_per_step": None,
                     "note": "serving is measured end to end (host buffers, copies included)"},
@@ -729,6 +756,8 @@ def main():
     ap.add_argument("--rate", type=float, default=2e5, help="serving workload: offered requests/s")
     ap.add_argument("--precision", choices=sorted(PRECISIONS), default="fp32",
                     help="arithmetic of the held samples and E_k (the perturbation stays FP32)")
+    ap.add_argument("--shape", type=int, default=None,
+                    help="multicode workload: use candidate launch shape K of the job table instead of tuning")
     ap.add_argument("--frames-per-point", type=int, default=FRAMES_PER_POINT,
                     help="frames per Eb/N0 batch (the benchmark workload is 10^6; smaller only for profiling)")
     args = ap.parse_args()

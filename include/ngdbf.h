@@ -205,8 +205,11 @@ ngdbf_status ngdbf_decode_plain(const ngdbf_code_t* code, const float* y, int64_
  * Same decode with HOST buffers, synchronous: copies y to the device in
  * chunks on two streams, decodes each chunk as soon as it has arrived while
  * the next chunk is copied, copies the outputs back, and returns when the
- * host outputs are written.  Page-locked host buffers give overlapped
- * copies; pageable ones work but serialize.  Same layouts as ngdbf_decode.
+ * host outputs are written.  Samples go through the library's staging buffers
+ * (ngdbf_set_host_copy_mode), so any host buffer copies at full rate; with
+ * direct copies, page-locked buffers overlap and pageable ones serialize.
+ * Outputs are copied straight into the caller's buffers.  Same layouts as
+ * ngdbf_decode.
  * chunk_frames <= 0 picks chunk sizes automatically: a quarter of the call
  * (between 256 MB and 2 GB of samples, at least 4096 frames), reached by doubling
  * from an eighth of it so that little copying precedes the first decode; two
@@ -216,6 +219,22 @@ ngdbf_status ngdbf_decode_host(const ngdbf_code_t* code, const float* y_host, in
                                float sigma, const ngdbf_params* params, uint64_t seed,
                                uint64_t frame_offset, uint8_t* bits_host, int32_t* iters_host,
                                uint8_t* pass_host, int64_t chunk_frames);
+
+/*
+ * How ngdbf_decode_host moves samples to the device (process-wide):
+ * NGDBF_HOST_COPY_STAGED (default): host threads (up to 16) copy each piece of up to 128 MB
+ * into one of two page-locked staging buffers that the library keeps and reuses, and the
+ * device copies from there; works at the host's memcpy rate (about 120 GB/s on a 16-core
+ * Grace host) whether the caller's buffer is page-locked or not, and whatever its pages.
+ * NGDBF_HOST_COPY_DIRECT: the device copies straight from the caller's buffer (no host
+ * threads; about 210 GB/s from page-locked memory whose translations are cheap, but on the
+ * GB300 hosts measured first copies from the first several GB of page-locked memory a
+ * process registered ran at 2-20 GB/s).
+ * Errors: INVALID_ARG (unknown mode, NULL out).
+ */
+enum { NGDBF_HOST_COPY_STAGED = 0, NGDBF_HOST_COPY_DIRECT = 1 };
+ngdbf_status ngdbf_set_host_copy_mode(int32_t mode);
+ngdbf_status ngdbf_get_host_copy_mode(int32_t* mode);
 
 /* Timing of the most recent ngdbf_decode_host on the calling thread, from CUDA events
  * recorded around each chunk's copy in, decode and copy out (device clock, ms): summed
@@ -276,20 +295,22 @@ ngdbf_status ngdbf_pool_usage(int32_t reset_high, int64_t* used_now, int64_t* us
 
 /*
  * Page-locked host memory for the host-buffer entry points (ngdbf_decode_host, the server).
- * A copy engine reading page-locked memory translates every page it touches; small pages
- * scattered in physical memory make those translations miss, and copies from such a buffer
- * were measured at 8-20 GB/s against 211 GB/s from other buffers of the same process on a
- * GB300 host.  Requests of at least one transparent huge page (ngdbf_host_huge_page_bytes:
- * 512 MiB with 64 KiB base pages, 2 MiB with 4 KiB ones) are mapped on huge-page boundaries,
- * advised for huge pages and registered with CUDA (the mapping rounded up to whole huge
- * pages); smaller requests, and systems where that fails, get cudaHostAlloc memory.  Contents
- * are undefined.  The caller owns the block and returns it with ngdbf_host_free (NULL: no-op).
+ * Requests of at least one transparent huge page (ngdbf_host_huge_page_bytes: 512 MiB with
+ * 64 KiB base pages, 2 MiB with 4 KiB ones) are mapped on huge-page boundaries, advised for
+ * huge pages (fewer translations for the copy engines) and registered with CUDA as one range
+ * (the mapping rounded up to whole huge pages); smaller requests, and systems where that
+ * fails, get cudaHostAlloc memory.  Contents are undefined.  The caller owns the block and
+ * returns it with ngdbf_host_free (NULL: no-op).
  * Errors: INVALID_ARG (NULL out, bytes == 0, a pointer not from ngdbf_host_alloc), OOM, CUDA.
  */
 ngdbf_status ngdbf_host_alloc(size_t bytes, void** out);
 ngdbf_status ngdbf_host_free(void* p);
 /* Transparent huge-page size the allocator aligns to (0 when the system reports none). */
 ngdbf_status ngdbf_host_huge_page_bytes(int64_t* out);
+/* A block from ngdbf_host_alloc: *bytes = its mapped length (0 for a cudaHostAlloc block) and
+ * *huge_bytes = how much of it the kernel backs with huge pages (from /proc/self/smaps; -1 when
+ * that cannot be read; huge pages are requested, not guaranteed). */
+ngdbf_status ngdbf_host_block_info(const void* p, int64_t* bytes, int64_t* huge_bytes);
 
 /*
  * Job tables: several decode jobs -- codes of different length, rate, degree

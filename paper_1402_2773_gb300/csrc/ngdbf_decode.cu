@@ -413,6 +413,7 @@ void fill_job(const ngdbf_code* C, const ngdbf_params* P, const float* y, int64_
     J.t_max = P->t_max;
     J.t_smooth = std::max(0, P->t_max - P->smooth_window);
     J.queue = queue;
+    J.work = (long long)C->n * (P->t_max + 1);
     J.single = (P->variant & NGDBF_SINGLE) ? 1 : 0;
     if (P->precision == NGDBF_FIX || P->precision == NGDBF_FIXACC) {
         J.fix_R = (float)(std::ldexp(1.0, P->q_bits) / (2.0 * (double)P->y_max));
@@ -786,6 +787,9 @@ ngdbf_status ngdbf_decode_host(const ngdbf_code_t* C, const float* y_host, int64
             ev.push_back(nullptr);
         }
     };
+    // samples through the library's staging buffers (host threads + copies from reused
+    // page-locked memory) unless direct copies were asked for
+    Staging* stage = host_copy_mode() == NGDBF_HOST_COPY_STAGED ? staging_acquire(dev) : nullptr;
     int64_t kernels = 0, chunks = 0;
     for (int64_t off = 0, c = 0, size = first_chunk; off < n_frames && rs == NGDBF_OK;
          off += size, size = std::min(2 * size, chunk_frames), ++c) {
@@ -797,7 +801,8 @@ ngdbf_status ngdbf_decode_host(const ngdbf_code_t* C, const float* y_host, int64
         int32_t* diters = reinterpret_cast<int32_t*>(dbits + align256(bb));
         uint8_t* dpass = reinterpret_cast<uint8_t*>(diters) + align256(bi);
         mark(st[b]);
-        e = cudaMemcpyAsync(dy, y_host + off * n, (size_t)F * n * 4, cudaMemcpyHostToDevice, st[b]);
+        e = stage ? staged_h2d(stage, dy, y_host + off * n, (size_t)F * n * 4, st[b])
+                  : cudaMemcpyAsync(dy, y_host + off * n, (size_t)F * n * 4, cudaMemcpyHostToDevice, st[b]);
         if (e != cudaSuccess) { rs = cuda_fail(e, "host-to-device copy"); break; }
         mark(st[b]);
         rs = decode_impl(C, dy, F, sigma, P, seed, frame_offset + (uint64_t)off, dbits, diters, dpass, st[b]);
@@ -821,6 +826,7 @@ ngdbf_status ngdbf_decode_host(const ngdbf_code_t* C, const float* y_host, int64
             cudaStreamDestroy(st[b]);
         }
     }
+    staging_release(stage);     // every copy out of it has completed
     if (rs == NGDBF_OK && chunks > 0 && ev.size() == (size_t)chunks * 4) {
         auto ms = [&](cudaEvent_t a, cudaEvent_t b_) {
             float v = 0.0f;

@@ -77,6 +77,17 @@ struct TableShape {
 // first is the default (no cluster, the plan's own placement, the largest block).
 ngdbf_status table_shapes(const TablePlan& T, const ngdbf_job* jobs, int32_t n_jobs, int dev,
                           std::vector<TableShape>* out);
+// Staged host-to-device copies (ngdbf_hostmem.cu): a pair of page-locked staging buffers of
+// kStageBytes with the events that free them, taken from and returned to a library cache.
+constexpr size_t kStageBytes = 128ull << 20;
+struct Staging;
+int host_copy_mode();
+Staging* staging_acquire(int dev);      // nullptr when none can be allocated
+void staging_release(Staging* s);
+// bytes from host src to device dst on stream st: host threads fill a free staging buffer,
+// the device copies out of it; returns when the last piece is queued.
+cudaError_t staged_h2d(Staging* s, void* dst, const void* src, size_t bytes, cudaStream_t st);
+
 // First job of every CTA, in proportion to the estimated work of each job.
 std::vector<int32_t> assign_ctas(const std::vector<int64_t>& frames, const std::vector<int64_t>& weight, int grid);
 std::vector<int32_t> assign_ctas_capped(const std::vector<int64_t>& frames, const std::vector<int64_t>& weight,

@@ -97,6 +97,7 @@ struct Job {
     // single-job launch passes them inline instead)
     const uint32_t* thr;
     unsigned long long* queue;  // next unclaimed frame of this job
+    long long work;             // job tables: estimated work of one frame, n x (T + 1)
     int32_t single;             // Step 3a: flip only the symbol with the least E_k (ties: lowest k)
     int32_t uniform;            // Sec. V-B: uniform perturbation of the same variance
     // objective trace of frames 0 .. trace_frames-1 (nullptr: off): unsatisfied checks U(t) and
@@ -148,7 +149,7 @@ struct DecodeArgs {
 
 // Launch of a job table: CTA c starts with job first_job[c] and, once that job has
 // no unclaimed frame left and its slots are idle, moves to the job with the most
-// unclaimed work (frames x n x (T + 1)).  Each job gets its own shared-memory layout
+// unclaimed work (frames x Job::work).  Each job gets its own shared-memory layout
 // (job_layout); the launch has room for the largest.
 struct MultiArgs {
     const Job* jobs;

@@ -29,8 +29,8 @@ __global__ void __launch_bounds__(1024) ngdbf_multi_kernel(const __grid_constant
             for (int i = 0; i < A.n_jobs; ++i) {
                 const unsigned long long claimed = *(volatile unsigned long long*)A.jobs[i].queue;
                 const long long left = A.jobs[i].n_frames - (long long)min(claimed, (unsigned long long)A.jobs[i].n_frames);
-                // its estimated remaining work: unclaimed frames x n x (T + 1)
-                const long long work = left * A.jobs[i].n * (long long)(A.jobs[i].t_max + 1);
+                // its estimated remaining work: unclaimed frames x work per frame
+                const long long work = left * A.jobs[i].work;
                 if (work > best) {
                     best = work;
                     pick = i;

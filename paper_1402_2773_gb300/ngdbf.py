@@ -132,6 +132,9 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.ngdbf_host_alloc.argtypes = [ctypes.c_size_t, ctypes.POINTER(vp)]
     lib.ngdbf_host_free.argtypes = [vp]
     lib.ngdbf_host_huge_page_bytes.argtypes = [ctypes.POINTER(ctypes.c_int64)]
+    lib.ngdbf_host_block_info.argtypes = [vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
+    lib.ngdbf_set_host_copy_mode.argtypes = [ctypes.c_int32]
+    lib.ngdbf_get_host_copy_mode.argtypes = [ctypes.POINTER(ctypes.c_int32)]
     lib.ngdbf_last_launch.argtypes = [ctypes.POINTER(ngdbf_launch_info)]
     lib.ngdbf_last_host_stats.argtypes = [ctypes.POINTER(ngdbf_host_stats)]
     lib.ngdbf_last_error.argtypes = []
@@ -142,7 +145,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
                "ngdbf_server_poll", "ngdbf_server_wait", "ngdbf_server_get_stats", "ngdbf_server_destroy",
                "ngdbf_gaussian_range", "ngdbf_pool_usage", "ngdbf_last_host_stats", "ngdbf_mix_probe",
                "ngdbf_generator_table", "ngdbf_batch_shape", "ngdbf_batch_use_shape", "ngdbf_decode_plain",
-               "ngdbf_host_alloc", "ngdbf_host_free", "ngdbf_host_huge_page_bytes"):
+               "ngdbf_host_alloc", "ngdbf_host_free", "ngdbf_host_huge_page_bytes", "ngdbf_host_block_info",
+               "ngdbf_set_host_copy_mode", "ngdbf_get_host_copy_mode"):
         getattr(lib, fn).restype = ctypes.c_int
     if path is None:
         _lib = lib
@@ -351,6 +355,30 @@ def ngdbf_host_huge_page_bytes() -> int:
     lib = load()
     v = ctypes.c_int64()
     _check(lib, lib.ngdbf_host_huge_page_bytes(ctypes.byref(v)))
+    return v.value
+
+
+def ngdbf_host_block_info(ptr: int) -> tuple[int, int]:
+    """(mapped bytes, bytes backed by huge pages) of a block from ngdbf_host_alloc."""
+    lib = load()
+    b, h = ctypes.c_int64(), ctypes.c_int64()
+    _check(lib, lib.ngdbf_host_block_info(ptr, ctypes.byref(b), ctypes.byref(h)))
+    return b.value, h.value
+
+
+NGDBF_HOST_COPY_STAGED = 0
+NGDBF_HOST_COPY_DIRECT = 1
+
+
+def ngdbf_set_host_copy_mode(mode: int) -> None:
+    lib = load()
+    _check(lib, lib.ngdbf_set_host_copy_mode(mode))
+
+
+def ngdbf_get_host_copy_mode() -> int:
+    lib = load()
+    v = ctypes.c_int32()
+    _check(lib, lib.ngdbf_get_host_copy_mode(ctypes.byref(v)))
     return v.value
 
 

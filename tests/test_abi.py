@@ -166,3 +166,14 @@ def test_host_allocator_validation_without_a_device(lib):
     except OSError:
         want = 0
     assert hp.value == want
+
+
+def test_host_copy_mode_without_a_device(lib):
+    m = ctypes.c_int32(-1)
+    assert lib.ngdbf_get_host_copy_mode(ctypes.byref(m)) == ngdbf.NGDBF_OK
+    assert m.value == ngdbf.NGDBF_HOST_COPY_STAGED              # the default
+    assert lib.ngdbf_set_host_copy_mode(7) == ngdbf.NGDBF_ERR_INVALID_ARG
+    assert lib.ngdbf_set_host_copy_mode(ngdbf.NGDBF_HOST_COPY_DIRECT) == ngdbf.NGDBF_OK
+    assert lib.ngdbf_get_host_copy_mode(ctypes.byref(m)) == ngdbf.NGDBF_OK and m.value == ngdbf.NGDBF_HOST_COPY_DIRECT
+    assert lib.ngdbf_set_host_copy_mode(ngdbf.NGDBF_HOST_COPY_STAGED) == ngdbf.NGDBF_OK
+    assert lib.ngdbf_get_host_copy_mode(None) == ngdbf.NGDBF_ERR_INVALID_ARG

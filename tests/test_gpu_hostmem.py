@@ -26,6 +26,10 @@ def test_large_block_is_huge_page_aligned_and_pinned():
     assert t.is_pinned()
     if hp:
         assert t.data_ptr() % hp == 0
+    mapped, huge = ngdbf.ngdbf_host_block_info(t.data_ptr())
+    if hp:
+        assert mapped % hp == 0 and mapped >= nbytes
+        assert -1 <= huge <= mapped
     t.numpy()[:] = 7
     d = t.cuda()
     assert int(d[-1].item()) == 7 and int(d.sum().item()) == 7 * nbytes
@@ -55,4 +59,28 @@ def test_decode_host_from_library_blocks_matches_torch_pinned():
     dc.decode_host(yb, sig, gp, seed=5, out=outs_b, chunk_frames=1024)
     for a, b in zip(outs_a, outs_b):
         assert torch.equal(a, b)
+    dc.close()
+
+
+@pytest.mark.parametrize("mode", ["staged", "direct"])
+@pytest.mark.parametrize("pinned", [True, False])
+def test_decode_host_copy_modes_give_the_same_bits(mode, pinned):
+    """Staged and direct copies, from page-locked and pageable buffers, decode the same frames
+    bit for bit (small chunks, so that several staging pieces and chunks are in flight)."""
+    code = wl.code_c2()
+    F = 2500
+    y, _, sig = wl.frames(code, F, 4.0, seed=78)
+    dc = ngdbf.DeviceCode.from_code(code)
+    gp = ngdbf.make_params(w=0.1875, theta=-0.7, eta=0.65, lam=0.993, y_max=2.0, t_max=300, variant=3)
+    ref = dc.decode(torch.from_numpy(y).cuda(), sig, gp, seed=9)
+    yin = torch.from_numpy(y).pin_memory() if pinned else torch.from_numpy(y.copy())
+    old = ngdbf.ngdbf_get_host_copy_mode()
+    try:
+        ngdbf.ngdbf_set_host_copy_mode(ngdbf.NGDBF_HOST_COPY_STAGED if mode == "staged" else ngdbf.NGDBF_HOST_COPY_DIRECT)
+        bits, iters, pas = dc.decode_host(yin, sig, gp, seed=9, chunk_frames=700)
+    finally:
+        ngdbf.ngdbf_set_host_copy_mode(old)
+    assert np.array_equal(bits, ref[0].cpu().numpy())
+    assert np.array_equal(iters, ref[1].cpu().numpy())
+    assert np.array_equal(pas, ref[2].cpu().numpy())
     dc.close()
