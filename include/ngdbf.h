@@ -378,8 +378,10 @@ ngdbf_status ngdbf_batch_destroy(ngdbf_batch_t* batch);
  * published.  A request of another variant or precision, or whose code needs a larger
  * shared-memory layout, than the running kernel waits until that kernel drains.  Each
  * request's result equals ngdbf_decode's for the same job, alone or in any mix; the seed of
- * the perturbation is the server's.  Page-locked host buffers let the copies run
- * asynchronously; with pageable ones the scheduler thread blocks on each copy.
+ * the perturbation is the server's.  Samples are copied in through the library's staging
+ * buffers (ngdbf_set_host_copy_mode), so any host buffer serves; with direct copies,
+ * page-locked buffers let the copies run asynchronously and with pageable ones the scheduler
+ * thread blocks on each copy.  Outputs are copied straight into the caller's buffers.
  */
 typedef struct ngdbf_server ngdbf_server_t;
 

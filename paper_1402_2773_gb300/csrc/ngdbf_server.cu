@@ -3,17 +3,20 @@
 //
 // Requests (a code, host samples and host outputs) are queued in arrival order.  A scheduler
 // thread admits them while the device memory they need fits the budget: it takes a block from
-// the library's stream-ordered pool, copies the samples and thresholds in on one of the copy
-// streams, and publishes the request into a ring of job descriptors in device memory (small
-// ordered copies from a page-locked mirror, made to wait for the request's own copies).  One persistent job-table kernel serves the ring: whenever a CTA has no
+// the library's stream-ordered pool, copies the samples (staged, like ngdbf_decode_host, unless
+// direct copies are selected) and thresholds in on one of the copy streams, and publishes the
+// request into a ring of job descriptors in device memory (small ordered copies from a
+// page-locked mirror, made to wait for the request's own copies).  One persistent job-table
+// kernel serves the ring: whenever a CTA has no
 // frames left in its current request it takes the oldest published request with unclaimed
 // frames, so requests that arrive while others are on the GPU join the running launch as
 // CTAs -- and, inside a request, slots -- free up.  The CTA that finishes a request's last frame
 // writes the request's generation into a completion word in page-locked host memory; the
 // scheduler then copies the outputs back and returns the request's memory to the budget.  Idle
 // CTAs poll the ring (in device memory, backing off) for about 20 ms and then exit; the
-// scheduler launches the kernel again when new work is published.  A request whose code needs a larger shared-memory layout, or another variant or
-// precision, than the running kernel waits until it drains.  Only copy-engine operations are
+// scheduler launches the kernel again when new work is published.  A request whose code
+// needs a larger shared-memory layout, or another variant or precision, than the running
+// kernel waits until it drains.  Only copy-engine operations are
 // issued while the kernel runs (no memset kernels), so nothing waits behind it for SMs.
 #include <cuda_runtime.h>
 
@@ -211,6 +214,7 @@ struct ngdbf_server {
     uint64_t seed = 0;
     cudaMemPool_t pool = nullptr;
     std::vector<cudaStream_t> streams;       // copy streams
+    std::vector<Staging*> stages;            // per copy stream, staged copies of request samples
     cudaStream_t pub_stream = nullptr;       // ring updates, in ring order
     cudaStream_t serve_stream = nullptr;     // the resident kernel
     std::mutex mu;
@@ -302,7 +306,13 @@ ngdbf_status admit(ngdbf_server* S, Request* r) {
     sg.tail1 = r->seq + 1;
     sg.desc = r->dj;
     __atomic_store_n(&S->notify_host[r->slot], 0u, __ATOMIC_RELEASE);
-    e = cudaMemcpyAsync(dy, r->y_host, (size_t)F * n * 4, cudaMemcpyHostToDevice, st);
+    // the samples through the stream's staging buffers (host threads + copies from reused
+    // page-locked memory) unless direct copies were asked for
+    if (host_copy_mode() == NGDBF_HOST_COPY_STAGED && !S->stages[si]) S->stages[si] = staging_acquire(S->device);
+    if (host_copy_mode() == NGDBF_HOST_COPY_STAGED && S->stages[si])
+        e = staged_h2d(S->stages[si], dy, r->y_host, (size_t)F * n * 4, st);
+    else
+        e = cudaMemcpyAsync(dy, r->y_host, (size_t)F * n * 4, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(dthr, sg.thr, ((size_t)q.params.t_max + 1) * 4, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(S->d_claim + r->slot, &sg.claim0, 8, cudaMemcpyHostToDevice, st);
@@ -597,6 +607,7 @@ extern "C" ngdbf_status ngdbf_server_create(size_t device_budget_bytes, int32_t 
         cudaStream_t st;
         e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
         if (e == cudaSuccess) S->streams.push_back(st);
+        if (e == cudaSuccess) S->stages.push_back(nullptr);
     }
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
@@ -708,6 +719,7 @@ extern "C" ngdbf_status ngdbf_server_destroy(ngdbf_server_t* S) {
         cudaStreamSynchronize(st);
         cudaStreamDestroy(st);
     }
+    for (Staging* sg : S->stages) staging_release(sg);     // every copy out of them has completed
     cudaStreamDestroy(S->serve_stream);
     cudaStreamDestroy(S->pub_stream);
     cudaEventDestroy(S->ev_kernel);
