@@ -372,7 +372,9 @@ ngdbf_status ngdbf_batch_destroy(ngdbf_batch_t* batch);
  * request in and publishes it into a ring of job descriptors the GPU reads.  The resident
  * kernel's CTAs take the oldest published request with frames left whenever their own is
  * exhausted, so requests that arrive while others run join the running launch and their work
- * overlaps on the device; inside a request, converged frames free their slots at once.  When
+ * overlaps on the device; inside a request, converged frames free their slots at once.  While
+ * 16 or more published requests have frames left, a CTA whose request runs out of frames fills
+ * its free slots with frames of other requests of the same code and params (chaining).  When
  * a request's last frame is done its outputs are copied back and its memory returns to the
  * budget.  Idle CTAs exit after a few milliseconds; the kernel is launched again when work is
  * published.  A request of another variant or precision, or whose code needs a larger

@@ -113,6 +113,25 @@ struct Job {
     uint32_t gen;
     unsigned int* done;
     unsigned int* notify;
+    // serving: jobs with the same nonzero chain_key have the same code and decoding parameters
+    // (they differ only in samples, sigma, frame offset, outputs and counters), so a CTA may
+    // decode frames of several of them in its slots at once
+    unsigned long long chain_key;
+};
+
+// Chaining of serving jobs inside one CTA (decode_job with CHAIN): the jobs whose frames the
+// slots hold (entries of jl, slot f holds a frame of jl[slot_e[f]]), the entry frames are
+// claimed from, and `next`, which finds another published job with the same chain_key.
+constexpr int kChain = 8;
+struct NoNext {
+    __device__ bool operator()(unsigned long long, Job&) const { return false; }
+};
+template <class Next>
+struct ChainCtx {
+    Job* jl;                    // [kChain] shared memory
+    int8_t* slot_e;             // [kSlots] shared memory
+    int* cur_e;                 // shared memory
+    Next next;
 };
 
 // Claims up to k consecutive frames of job A: returns true and the first frame id in *base
@@ -377,6 +396,50 @@ __device__ __forceinline__ void load_held4(const int8_t* p, int8_t v[4]) {
 // parameters or a shared-memory copy), `thr_src` its thresholds, `L` the shared-memory
 // layout of the launch, `ys`/`st_cta` this CTA's slot scratch.
 //
+// Thread 0 of a CTA whose slots chain serving jobs: gives the slots in `want` new frames,
+// claimed from the current entry and, when its job has none left, from other published jobs
+// with the same chain key, which ch.next copies into a free entry (one that no slot of `busy`
+// or of those just filled refers to).  Sets lane_frame (frame index within its job; -1 for a
+// slot left empty), lane_start = start and ch.slot_e for the filled slots; returns them.
+template <class Next>
+__device__ uint32_t fill_chained(ChainCtx<Next>& ch, unsigned long long key, uint32_t want, uint32_t busy,
+                                 int start, long long* lane_frame, int32_t* lane_start) {
+    uint32_t fresh = 0;
+    for (int step = 0; step <= kChain; ++step) {
+        const uint32_t left = want & ~fresh;
+        if (!left) break;
+        const Job& E = ch.jl[*ch.cur_e];
+        const int k = __popc(left);
+        unsigned long long base = 0;
+        if (claim_frames(E, (unsigned)k, &base)) {
+            for (int j = 0; j < k; ++j) {
+                const int f = nth_set_bit(left, j);
+                const unsigned long long fid = base + j;
+                if (fid < (unsigned long long)E.n_frames) {
+                    lane_frame[f] = (long long)fid;
+                    lane_start[f] = start;
+                    ch.slot_e[f] = (int8_t)*ch.cur_e;
+                    fresh |= 1u << f;
+                }
+            }
+        }
+        if (!(want & ~fresh) || key == 0ull) break;
+        // the current job has no frames left: another with the same key, into a free entry
+        const uint32_t held = busy | fresh;
+        int e2 = -1;
+        for (int e = 0; e < kChain && e2 < 0; ++e) {
+            if (e == *ch.cur_e) continue;
+            bool used = false;
+            for (uint32_t r = held; r; r &= r - 1) used |= ch.slot_e[__ffs(r) - 1] == e;
+            if (!used) e2 = e;
+        }
+        if (e2 < 0 || !ch.next(key, ch.jl[e2])) break;
+        *ch.cur_e = e2;
+    }
+    for (uint32_t r = want & ~fresh; r; r &= r - 1) lane_frame[__ffs(r) - 1] = -1;
+    return fresh;
+}
+
 // Cluster split (CL, S.size > 1): the S.size CTAs of a thread-block cluster decode the same
 // 32 slots, each the symbols [S.k_lo, S.k_hi) (samples, state, counts and M(k) rows of those
 // only), with a full copy of the decision words in every CTA: each computes all syndromes (so
@@ -385,12 +448,26 @@ __device__ __forceinline__ void load_held4(const int8_t* p, int8_t v[4]) {
 // writes the slot table into every CTA.  Cluster barriers separate the phases; every CTA
 // takes the same branches (they depend only on the vote and the slot table), so all of them
 // reach every barrier.
-template <bool ADAPT, bool SMOOTH, bool ST_SMEM, bool WIDE, int PREC, bool CL = false>
+//
+// Chaining (CHAIN, serving): A is ch.jl[0]; when A has no unclaimed frame left, free slots take
+// frames of other published jobs with A's chain key (fill_chained), so the CTA keeps its slots
+// busy across requests instead of waiting for A's slowest frame; the loop returns when no such
+// job has frames left and every slot is idle.
+template <bool ADAPT, bool SMOOTH, bool ST_SMEM, bool WIDE, int PREC, bool CL = false, bool CHAIN = false,
+          class Next = NoNext>
 __device__ __forceinline__ void decode_job(const Job& A, const uint32_t* thr_src, const GenConsts& G,
                                            const SmemLayout& L, int tables,
                                            typename Held<PREC>::T* ys, uint16_t* st_cta,
-                                           Split S = Split{0, 1, 0, 0}) {
+                                           Split S = Split{0, 1, 0, 0},
+                                           ChainCtx<Next> ch = ChainCtx<Next>{nullptr, nullptr, nullptr, Next{}}) {
+    static_assert(!(CL && CHAIN), "chained jobs are not split over clusters");
     constexpr bool kState = ADAPT || SMOOTH;
+    // the job whose frame slot f holds (per-request fields: samples, sigma, frame offset,
+    // outputs, counters); every other field is the same for all chained jobs
+    auto job_of = [&](int f) -> const Job& {
+        if constexpr (CHAIN) return ch.jl[ch.slot_e[f]];
+        return A;
+    };
     using HeldT = typename Held<PREC>::T;
     extern __shared__ __align__(16) unsigned char smem[];
     const int n = A.n, m = A.m, T = A.t_max, dv_max = A.dv_max, dc_max = A.dc_max;
@@ -452,6 +529,9 @@ __device__ __forceinline__ void decode_job(const Job& A, const uint32_t* thr_src
     // past L1, which may still hold lines of an earlier request at the same addresses
     if constexpr (ADAPT)
         for (int u = tid; u <= T; u += blockDim.x) thr[u] = A.gen ? __ldcg(thr_src + u) : thr_src[u];
+    // threshold of the non-adaptive variants; chained jobs read it once here, since the first
+    // job's memory is returned when that job completes
+    const uint32_t th0_once = CHAIN ? __ldcg(thr_src) : 0u;
     if constexpr (kState)
         for (int e = tid; e < pad4(nl) * kSlots; e += blockDim.x) st[e] = 0;
     if (tid < 2 * kSlots) best[tid] = ~0ull;
@@ -459,17 +539,23 @@ __device__ __forceinline__ void decode_job(const Job& A, const uint32_t* thr_src
         for (int c = 0; c < 8; ++c) ctl[c] = 0u;
     if (split) group_sync();        // every copy cleared before rank 0 writes the slot table
     if (tid == 0 && (!split || S.rank == 0)) {
-        unsigned long long base = 0;
-        const bool got = claim_frames(A, kSlots, &base);
         uint32_t live = 0;
-        for (int f = 0; f < kSlots; ++f) {
-            const unsigned long long fid = base + f;
-            lane_start[f] = 0;
-            if (got && fid < (unsigned long long)A.n_frames) {
-                lane_frame[f] = (long long)fid;
-                live |= 1u << f;
-            } else {
-                lane_frame[f] = -1;
+        if constexpr (CHAIN) {
+            *ch.cur_e = 0;
+            for (int f = 0; f < kSlots; ++f) ch.slot_e[f] = 0;     // every slot names a loaded entry
+            live = fill_chained(ch, A.chain_key, 0xFFFFFFFFu, 0u, 0, lane_frame, lane_start);
+        } else {
+            unsigned long long base = 0;
+            const bool got = claim_frames(A, kSlots, &base);
+            for (int f = 0; f < kSlots; ++f) {
+                const unsigned long long fid = base + f;
+                lane_start[f] = 0;
+                if (got && fid < (unsigned long long)A.n_frames) {
+                    lane_frame[f] = (long long)fid;
+                    live |= 1u << f;
+                } else {
+                    lane_frame[f] = -1;
+                }
             }
         }
         ctl[2] = live;
@@ -504,8 +590,9 @@ __device__ __forceinline__ void decode_job(const Job& A, const uint32_t* thr_src
                 while (rest) {
                     const int f = __ffs(rest) - 1;
                     rest &= rest - 1;
-                    const float* yp = A.y + (size_t)lane_frame[f] * n + k;
-                    float v = A.gen ? __ldcg(yp) : __ldg(yp);
+                    const Job& Jf = job_of(f);
+                    const float* yp = Jf.y + (size_t)lane_frame[f] * n + k;
+                    float v = Jf.gen ? __ldcg(yp) : __ldg(yp);
                     if (A.clamp) {
                         if (v > A.y_max) v = A.y_max;
                         if (v < -A.y_max) v = -A.y_max;
@@ -600,38 +687,59 @@ __device__ __forceinline__ void decode_job(const Job& A, const uint32_t* thr_src
                         byte |= bit << q;
                     }
                 }
-                A.bits[(size_t)lane_frame[f] * A.nb + b] = (uint8_t)byte;
+                job_of(f).bits[(size_t)lane_frame[f] * A.nb + b] = (uint8_t)byte;
             }
             if (tid < nfin && (!split || S.rank == 0)) {
                 const int f = nth_set_bit(fin, tid);
                 const bool ok = (conv >> f) & 1u;
                 const long long fr = lane_frame[f];
-                A.iters[fr] = ok ? round - lane_start[f] : T;
-                A.pass[fr] = ok ? 1 : 0;
+                const Job& Jf = job_of(f);
+                Jf.iters[fr] = ok ? round - lane_start[f] : T;
+                Jf.pass[fr] = ok ? 1 : 0;
             }
             if (A.done != nullptr) __threadfence();   // outputs visible before they are counted
             group_sync();           // every CTA is done with the finished slots' table entries
             if (A.done != nullptr && tid == 0 && (!split || S.rank == 0)) {
-                const unsigned int before = atomicAdd(A.done, (unsigned int)nfin);
-                if ((long long)before + nfin == A.n_frames) {
-                    __threadfence_system();
-                    *(volatile unsigned int*)A.notify = A.gen;
+                if constexpr (CHAIN) {
+                    // the finished frames counted in their own jobs
+                    for (int e = 0; e < kChain; ++e) {
+                        int cnt = 0;
+                        for (uint32_t r = fin; r; r &= r - 1)
+                            cnt += ch.slot_e[__ffs(r) - 1] == e ? 1 : 0;
+                        if (!cnt) continue;
+                        const Job& E = ch.jl[e];
+                        const unsigned int before = atomicAdd(E.done, (unsigned int)cnt);
+                        if ((long long)before + cnt == E.n_frames) {
+                            __threadfence_system();
+                            *(volatile unsigned int*)E.notify = E.gen;
+                        }
+                    }
+                } else {
+                    const unsigned int before = atomicAdd(A.done, (unsigned int)nfin);
+                    if ((long long)before + nfin == A.n_frames) {
+                        __threadfence_system();
+                        *(volatile unsigned int*)A.notify = A.gen;
+                    }
                 }
             }
             // ---- claim new frames for the finished slots ----
             if (tid == 0 && (!split || S.rank == 0)) {
                 uint32_t fresh = 0;
-                unsigned long long base = 0;
-                const bool got = claim_frames(A, (unsigned)nfin, &base);
-                for (int j = 0; j < nfin; ++j) {
-                    const int f = nth_set_bit(fin, j);
-                    const unsigned long long fid = base + j;
-                    if (got && fid < (unsigned long long)A.n_frames) {
-                        lane_frame[f] = (long long)fid;
-                        lane_start[f] = round;
-                        fresh |= 1u << f;
-                    } else {
-                        lane_frame[f] = -1;
+                if constexpr (CHAIN) {
+                    fresh = fill_chained(ch, A.chain_key, fin, live & ~fin, round, lane_frame, lane_start);
+                } else {
+                    unsigned long long base = 0;
+                    const bool got = claim_frames(A, (unsigned)nfin, &base);
+                    for (int j = 0; j < nfin; ++j) {
+                        const int f = nth_set_bit(fin, j);
+                        const unsigned long long fid = base + j;
+                        if (got && fid < (unsigned long long)A.n_frames) {
+                            lane_frame[f] = (long long)fid;
+                            lane_start[f] = round;
+                            fresh |= 1u << f;
+                        } else {
+                            lane_frame[f] = -1;
+                        }
                     }
                 }
                 ctl[2] = (live & ~fin) | fresh;
@@ -701,13 +809,15 @@ __device__ __forceinline__ void decode_job(const Job& A, const uint32_t* thr_src
         {
             const bool act = (live >> lane) & 1u;
             const long long fr = lane_frame[lane];
-            const uint64_t fid = A.frame_offset + (uint64_t)(act ? fr : 0);
+            const Job& Jl = job_of(lane);           // an idle lane's entry is stale: don't-care
+            const uint64_t fid = Jl.frame_offset + (uint64_t)(act ? fr : 0);
             const uint32_t flo = (uint32_t)fid, fhi = (uint32_t)(fid >> 32);
             const int t = act ? round - lane_start[lane] : 0;
             const bool window = SMOOTH && act && t >= A.t_smooth;
             const int g_lo = k_lo >> 2;              // first group of this CTA's symbols
-            const uint32_t th0 = A.gen ? __ldcg(thr_src) : thr_src[0];   // threshold of the non-adaptive variants
-            const float scale = A.scale, wgt = A.w, fix_R = A.fix_R, acc_R = A.acc_R;
+            // threshold of the non-adaptive variants
+            const uint32_t th0 = CHAIN ? th0_once : (A.gen ? __ldcg(thr_src) : thr_src[0]);
+            const float scale = Jl.scale, wgt = A.w, fix_R = A.fix_R, acc_R = A.acc_R;
             const int32_t fix_kmax = A.fix_kmax, fix_W = A.fix_W, acc_W = A.acc_W;
             const bool uniform = A.uniform != 0;
             const bool single = !ADAPT && A.single;

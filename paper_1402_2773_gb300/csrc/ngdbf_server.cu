@@ -26,7 +26,9 @@
 #include <condition_variable>
 #include <cstring>
 #include <deque>
+#include <map>
 #include <mutex>
+#include <string>
 #include <thread>
 #include <vector>
 
@@ -67,12 +69,65 @@ struct ServeArgs {
     GenConsts G;
 };
 
+// A CTA chains to another request only while at least kChainMinPending published requests have
+// unclaimed frames (the server is saturated: chaining keeps slots busy across requests); with
+// fewer, requests are taken in arrival order by the picker, whatever their code.
+constexpr int kChainMinPending = 16;
+
+// Finds, for a CTA whose request has no frames left, another published request with the same
+// chain key and unclaimed frames (the oldest) and copies its descriptor into `out` (thread 0).
+// A search that failed is not repeated for the same key until more requests are published.
+struct RingNext {
+    const volatile ServeRing* R;
+    unsigned long long* fail;           // shared memory: [0] the ring tail, [1] the key of the last failed search
+    __device__ bool operator()(unsigned long long key, Job& out) const {
+        const unsigned long long tail = R->tail, head = R->head;
+        if (tail == fail[0] && key == fail[1]) return false;
+        int pending = 0, found = -1;
+        uint32_t found_gen = 0;
+        unsigned long long found_q = 0;
+        for (unsigned long long q = head; q < tail && q < head + kRing; ++q) {
+            const int slot = (int)(q % kRing);
+            if (R->ready[slot] != q + 1) continue;
+            __threadfence();
+            const uint32_t gen = R->jobs[slot].gen;
+            const long long frames = R->jobs[slot].n_frames;
+            unsigned long long* queue = R->jobs[slot].queue;
+            const unsigned long long c = *(volatile unsigned long long*)queue;
+            if ((uint32_t)(c >> 32) != gen || (long long)(uint32_t)c >= frames) continue;
+            ++pending;
+            if (found < 0 && R->jobs[slot].chain_key == key) {
+                found = slot;
+                found_gen = gen;
+                found_q = q;
+            }
+            if (found >= 0 && pending >= kChainMinPending) break;
+        }
+        if (found >= 0 && pending >= kChainMinPending) {
+            const volatile uint32_t* src = reinterpret_cast<const volatile uint32_t*>(&R->jobs[found]);
+            uint32_t* dst = reinterpret_cast<uint32_t*>(&out);
+            for (int w = 0; w < (int)(sizeof(Job) / 4); ++w) dst[w] = src[w];
+            __threadfence();
+            if (R->ready[found] == found_q + 1 && out.gen == found_gen) return true;
+        }
+        fail[0] = tail;
+        fail[1] = key;
+        return false;
+    }
+};
+
 // The resident serving kernel: each CTA repeatedly takes the oldest published request that
-// still has unclaimed frames (of its own generation) and runs the slot loop on it.
+// still has unclaimed frames (of its own generation) and runs the slot loop on it, chaining
+// further requests of the same code and parameters into its free slots.
 template <bool ADAPT, bool SMOOTH, bool ST_SMEM, bool WIDE, int PREC>
 __global__ void __launch_bounds__(1024) ngdbf_serve_kernel(const __grid_constant__ ServeArgs A) {
     using HeldT = typename Held<PREC>::T;
-    __shared__ Job job;
+    __shared__ Job jl[kChain];      // jl[0]: the request picked; the others: chained requests
+    __shared__ int8_t slot_e[kSlots];
+    __shared__ int cur_e;
+    __shared__ unsigned long long fail[2];
+    Job& job = jl[0];
+    if (threadIdx.x == 0) fail[0] = fail[1] = ~0ull;
     __shared__ int pick;
     const SmemLayout L = smem_layout(A.n_max, A.m_max, A.t_max, A.dv_max, A.dc_max, ADAPT,
                                      ST_SMEM && (ADAPT || SMOOTH), A.placement);
@@ -126,7 +181,9 @@ __global__ void __launch_bounds__(1024) ngdbf_serve_kernel(const __grid_constant
         if (p < 0) continue;
         slept = 0;
         nap = 500;
-        decode_job<ADAPT, SMOOTH, ST_SMEM, WIDE, PREC>(job, job.thr, A.G, L, A.placement, ys, st);
+        decode_job<ADAPT, SMOOTH, ST_SMEM, WIDE, PREC, false, true, RingNext>(
+            job, job.thr, A.G, L, A.placement, ys, st, Split{0, 1, 0, 0},
+            ChainCtx<RingNext>{jl, slot_e, &cur_e, RingNext{R, fail}});
         __syncthreads();
     }
 }
@@ -215,6 +272,7 @@ struct ngdbf_server {
     cudaMemPool_t pool = nullptr;
     std::vector<cudaStream_t> streams;       // copy streams
     std::vector<Staging*> stages;            // per copy stream, staged copies of request samples
+    std::map<std::string, unsigned long long> chain_ids;   // (code, params) -> chain key
     cudaStream_t pub_stream = nullptr;       // ring updates, in ring order
     cudaStream_t serve_stream = nullptr;     // the resident kernel
     std::mutex mu;
@@ -297,6 +355,15 @@ ngdbf_status admit(ngdbf_server* S, Request* r) {
              sg.thr);
     r->dj.thr = dthr;
     r->dj.gen = r->gen;
+    // requests of the same code and parameters share a chain key: the kernel decodes frames
+    // of several of them in one CTA's slots (they differ only in samples, sigma, offset, outputs)
+    {
+        std::string k(reinterpret_cast<const char*>(&q.code), sizeof(q.code));
+        k.append(reinterpret_cast<const char*>(&q.params), sizeof(q.params));
+        auto it = S->chain_ids.find(k);
+        if (it == S->chain_ids.end()) it = S->chain_ids.emplace(k, (unsigned long long)S->chain_ids.size() + 1).first;
+        r->dj.chain_key = it->second;
+    }
     r->dj.done = S->d_done + r->slot;
     r->dj.notify = S->notify_dev + r->slot;
     sg.claim0 = (unsigned long long)r->gen << 32;

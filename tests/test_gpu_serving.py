@@ -158,3 +158,28 @@ def test_requests_join_a_running_launch(codes):
     assert stats["peak_requests_on_device"] >= 2, stats
     for dc in dcs:
         dc.close()
+
+
+def test_chained_requests_of_one_code(codes):
+    """Many requests of the same code and parameters pending at once (different samples, sigma,
+    sizes and frame offsets): CTAs decode frames of several of them in their slots at once, and
+    every result still equals the request decoded alone (per-slot sigma, offset, outputs and
+    completion counts).  A second parameter set in the mix keeps its own chain."""
+    dcs = [ngdbf.DeviceCode.from_code(c) for c in codes]
+    rng = np.random.default_rng(21)
+    kw_a = dict(w=0.1875, theta=-0.7, eta=0.65, lam=0.993, y_max=2.0, t_max=150, smooth_window=64, variant=3)
+    kw_b = dict(w=0.75, theta=-0.9, eta=0.9, lam=0.99, y_max=2.5, t_max=120, smooth_window=64, variant=3)
+    reqs = []
+    for r in range(96):
+        c, kw = (3, kw_a) if r % 4 else (1, kw_b)
+        F = int(rng.integers(1, 120))
+        y, _, sig = wl.frames(codes[c], F, float(rng.uniform(3.0, 4.5)), seed=3000 + r)
+        reqs.append(dict(c=c, y=torch.from_numpy(y).pin_memory(), sigma=sig, kw=kw, off=1000 * r + 17))
+    alone = decode_alone(dcs, reqs, seed=12)
+    got, done, stats = serve(dcs, reqs, budget=4 << 30, inflight=4, max_jobs=256, seed=12)
+    assert len(done) == len(reqs) and all(st == 0 for _, _, st in done)
+    for g, a in zip(got, alone):
+        assert all((x == y).all() for x, y in zip(g, a)), "served result differs from the request alone"
+    assert stats["peak_requests_on_device"] >= 16, stats
+    for dc in dcs:
+        dc.close()
