@@ -521,25 +521,12 @@ __device__ __forceinline__ void decode_job(const Job& A, const uint32_t* thr_src
         sym_base = k_lo;
     }
 
-    // ---- set-up: generator table, zero the state, sentinels, thresholds, first 32 frames ----
-    for (int i = tid; i < 256; i += blockDim.x) icdf[i] = G.icdf[i];
-    for (int k = tid; k < pad4(n + 1); k += blockDim.x) xw[k] = 0u;
-    for (int i = tid; i < (m + 1) * (WIDE ? 1 : 4); i += blockDim.x) sw[i] = 0u;
-    // a serving job's thresholds and samples were copied in while the kernel runs: read them
-    // past L1, which may still hold lines of an earlier request at the same addresses
-    if constexpr (ADAPT)
-        for (int u = tid; u <= T; u += blockDim.x) thr[u] = A.gen ? __ldcg(thr_src + u) : thr_src[u];
-    // threshold of the non-adaptive variants; chained jobs read it once here, since the first
-    // job's memory is returned when that job completes
-    const uint32_t th0_once = CHAIN ? __ldcg(thr_src) : 0u;
-    if constexpr (kState)
-        for (int e = tid; e < pad4(nl) * kSlots; e += blockDim.x) st[e] = 0;
-    if (tid < 2 * kSlots) best[tid] = ~0ull;
-    if (tid == 0)
-        for (int c = 0; c < 8; ++c) ctl[c] = 0u;
-    if (split) group_sync();        // every copy cleared before rank 0 writes the slot table
-    if (tid == 0 && (!split || S.rank == 0)) {
+    // ---- the first 32 frames, then the set-up: generator table, zeroed state, sentinels,
+    // thresholds.  Unsplit, the claim comes first, so that a CTA that finds every frame taken
+    // (several CTAs pick a job at once) returns without the set-up. ----
+    auto claim_first = [&]() {          // thread 0 (rank 0 when split): slot table and live mask
         uint32_t live = 0;
+        for (int c = 0; c < 8; ++c) ctl[c] = 0u;
         if constexpr (CHAIN) {
             *ch.cur_e = 0;
             for (int f = 0; f < kSlots; ++f) ch.slot_e[f] = 0;     // every slot names a loaded entry
@@ -560,18 +547,44 @@ __device__ __forceinline__ void decode_job(const Job& A, const uint32_t* thr_src
         }
         ctl[2] = live;
         ctl[3] = live;
-        if constexpr (CL) {
-            for (int r = 0; split && r < S.size; ++r) {
-                if (r == S.rank) continue;
-                long long* pf = peer(lane_frame, r);
-                int32_t* ps = peer(lane_start, r);
-                uint32_t* pc = peer(ctl, r);
-                for (int f = 0; f < kSlots; ++f) {
-                    pf[f] = lane_frame[f];
-                    ps[f] = 0;
+        return live;
+    };
+    if (!split) {
+        if (tid == 0) claim_first();
+        __syncthreads();
+        if (ctl[2] == 0u) return;
+    }
+    for (int i = tid; i < 256; i += blockDim.x) icdf[i] = G.icdf[i];
+    for (int k = tid; k < pad4(n + 1); k += blockDim.x) xw[k] = 0u;
+    for (int i = tid; i < (m + 1) * (WIDE ? 1 : 4); i += blockDim.x) sw[i] = 0u;
+    // a serving job's thresholds and samples were copied in while the kernel runs: read them
+    // past L1, which may still hold lines of an earlier request at the same addresses
+    if constexpr (ADAPT)
+        for (int u = tid; u <= T; u += blockDim.x) thr[u] = A.gen ? __ldcg(thr_src + u) : thr_src[u];
+    // threshold of the non-adaptive variants; chained jobs read it once here, since the first
+    // job's memory is returned when that job completes
+    const uint32_t th0_once = CHAIN ? __ldcg(thr_src) : 0u;
+    if constexpr (kState)
+        for (int e = tid; e < pad4(nl) * kSlots; e += blockDim.x) st[e] = 0;
+    if (tid < 2 * kSlots) best[tid] = ~0ull;
+    if (split) {
+        group_sync();        // every copy cleared before rank 0 writes the slot table
+        if (tid == 0 && S.rank == 0) {
+            const uint32_t live = claim_first();
+            if constexpr (CL) {
+                for (int r = 0; r < S.size; ++r) {
+                    if (r == S.rank) continue;
+                    long long* pf = peer(lane_frame, r);
+                    int32_t* ps = peer(lane_start, r);
+                    uint32_t* pc = peer(ctl, r);
+                    for (int f = 0; f < kSlots; ++f) {
+                        pf[f] = lane_frame[f];
+                        ps[f] = 0;
+                    }
+                    for (int c = 0; c < 8; ++c) pc[c] = 0u;
+                    pc[2] = live;
+                    pc[3] = live;
                 }
-                pc[2] = live;
-                pc[3] = live;
             }
         }
     }

@@ -70,9 +70,11 @@ struct ServeArgs {
 };
 
 // A CTA chains to another request only while at least kChainMinPending published requests have
-// unclaimed frames (the server is saturated: chaining keeps slots busy across requests); with
-// fewer, requests are taken in arrival order by the picker, whatever their code.
+// unclaimed frames (the server is saturated: chaining keeps slots busy across requests), and
+// only to one among the kChainWindow oldest of those, so that requests of other codes are not
+// overtaken without bound; with fewer pending, the picker takes requests in arrival order.
 constexpr int kChainMinPending = 16;
+constexpr int kChainWindow = 32;
 
 // Finds, for a CTA whose request has no frames left, another published request with the same
 // chain key and unclaimed frames (the oldest) and copies its descriptor into `out` (thread 0).
@@ -95,7 +97,7 @@ struct RingNext {
             unsigned long long* queue = R->jobs[slot].queue;
             const unsigned long long c = *(volatile unsigned long long*)queue;
             if ((uint32_t)(c >> 32) != gen || (long long)(uint32_t)c >= frames) continue;
-            ++pending;
+            if (++pending > kChainWindow) break;
             if (found < 0 && R->jobs[slot].chain_key == key) {
                 found = slot;
                 found_gen = gen;
@@ -103,7 +105,7 @@ struct RingNext {
             }
             if (found >= 0 && pending >= kChainMinPending) break;
         }
-        if (found >= 0 && pending >= kChainMinPending) {
+        if (found >= 0 && pending >= kChainMinPending) {     // (pending counts at most kChainWindow + 1)
             const volatile uint32_t* src = reinterpret_cast<const volatile uint32_t*>(&R->jobs[found]);
             uint32_t* dst = reinterpret_cast<uint32_t*>(&out);
             for (int w = 0; w < (int)(sizeof(Job) / 4); ++w) dst[w] = src[w];
@@ -541,7 +543,11 @@ void scheduler(ngdbf_server* S) {
         if (S->running && cudaEventQuery(S->ev_kernel) != cudaErrorNotReady) {
             cudaGetLastError();
             S->running = false;
-            cudaFreeAsync(S->scratch, S->serve_stream);
+            // freed on the publication stream, not on the kernel's: the pool lets later
+            // allocations reuse a block by waiting for the freeing stream's work, and the
+            // kernel's stream would by then run the next resident kernel, which only exits
+            // when it runs out of work (requests' copies would wait for it)
+            cudaFreeAsync(S->scratch, S->pub_stream);
             S->scratch = nullptr;
             S->in_use -= S->scratch_bytes;
             S->scratch_bytes = 0;
