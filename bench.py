@@ -86,9 +86,9 @@ def mix_probe(ngdbf, stream, reps=5, warmup=2):
             "symbols_per_launch": symbols, "ops_per_symbol": PROBE_OPS_PER_SYMBOL}
 # DRAM bytes (read + write) per decoded frame of the decode kernel, from an ncu capture of
 # this workload at 2*10^4 frames per Eb/N0 point (samples 164 MB per launch, larger than L2):
-# 166.1 MB read + 8.0 MB written at 3.5 dB; traffic scales with frames, each frame's samples
+# 167.6 MB read + 8.0 MB written at 3.5 dB; traffic scales with frames, each frame's samples
 # being read once.  Set to None when the kernel changes without a new capture.
-DRAM_BYTES_PER_FRAME = 8_704
+DRAM_BYTES_PER_FRAME = 8_778
 
 
 def env_rank():
