@@ -339,9 +339,9 @@ typedef struct ngdbf_batch ngdbf_batch_t;   /* opaque; owns device scratch and t
 
 enum {
     NGDBF_BATCH_TUNE = 1,   /* time the candidate launch shapes on this table -- block size x
-                               thread-block cluster size (1, 2, 4, 8: codes of 2048 symbols or more
-                               split over the CTAs of a cluster) x adjacency tables in shared
-                               memory -- and keep the fastest */
+                               thread-block cluster size (1, 2, 4, 8) x split threshold (codes of
+                               at least 2048, or 1024 or 4096, symbols split over the CTAs of a
+                               cluster) x adjacency tables in shared memory -- and keep the fastest */
     NGDBF_BATCH_GRAPH = 2   /* capture the launch (queue reset + kernel) in a CUDA graph */
 };
 
@@ -469,14 +469,16 @@ typedef struct ngdbf_launch_info {
     int32_t kernels;         /* kernels launched by the call */
     int32_t sm_count;        /* SMs of the device */
     int32_t tables_in_smem;  /* adjacency tables copied to shared memory: 1 N(i), 2 M(k), 3 both */
-    int32_t cluster;         /* CTAs per thread-block cluster (1: none); codes of 2048 symbols or
-                                more are split over a cluster, smaller ones decoded CTA by CTA */
+    int32_t cluster;         /* CTAs per thread-block cluster (1: none) */
+    int32_t split_min_n;     /* with a cluster: codes of at least this many symbols are split over
+                                it, smaller ones decoded CTA by CTA (0 without a cluster) */
 } ngdbf_launch_info;
 
 ngdbf_status ngdbf_last_launch(ngdbf_launch_info* out);
 
 /* The candidate launch shapes of a batch, the ones NGDBF_BATCH_TUNE times (block size x
- * cluster size x adjacency tables in shared memory; candidate 0 is the default).  *count
+ * cluster size x split threshold x adjacency tables in shared memory; candidate 0 is the
+ * default).  *count
  * (may be NULL) receives their number; info (may be NULL) receives candidate k (k < 0: the
  * shape in use): grid = the most CTAs resident at once, block, shared memory, placements
  * and cluster size. */

@@ -105,6 +105,7 @@ ngdbf_status fail(ngdbf_status s, const std::string& msg) {
 void set_last_launch(int grid, int block, int smem, int state_in_smem, int tables_in_smem, int kernels,
                      int sm_count) {
     g_last_launch.cluster = 1;
+    g_last_launch.split_min_n = 0;
     g_last_launch.grid = grid;
     g_last_launch.block = block;
     g_last_launch.smem_bytes = smem;
@@ -1158,32 +1159,35 @@ ngdbf_status table_shapes(const TablePlan& T, const ngdbf_job* jobs, int32_t n_j
             }
         }
     }
-    for (const int C : {2, 4, 8}) {
+    // cluster candidates: codes of at least smin symbols split over the C CTAs of a cluster
+    // (smin = kSplitMinN first, so that the candidates' order does not depend on the others;
+    // then the other thresholds where they split a different set of codes)
+    auto cluster_shapes = [&](int C, int smin) -> ngdbf_status {
         // symbols per CTA: the share of a split code, or a whole code decoded per CTA
         int n_local = 0, n_split = 0;
         for (int j = 0; j < n_jobs; ++j) {
             const int n = jobs[j].code->n;
-            if (n >= kSplitMinN) {
+            if (n >= smin) {
                 n_local = std::max(n_local, split_local_max(n, C));
                 ++n_split;
             } else {
                 n_local = std::max(n_local, n);
             }
         }
-        if (n_split == 0) break;            // nothing to split
+        if (n_split == 0) return NGDBF_OK;     // nothing to split
         cudaFuncAttributes fa;
-        e = cudaFuncGetAttributes(&fa, multi_cluster_kernel_fn(variant, precision, state, wide));
-        if (e != cudaSuccess) return cuda_fail(e, "cudaFuncGetAttributes");
+        cudaError_t e2 = cudaFuncGetAttributes(&fa, multi_cluster_kernel_fn(variant, precision, state, wide));
+        if (e2 != cudaSuccess) return cuda_fail(e2, "cudaFuncGetAttributes");
         const int limit = smem_optin - (int)fa.sharedSizeBytes;
         for (const bool st : {true, false}) {
             if (st && !state) continue;
             void* fn = multi_cluster_kernel_fn(variant, precision, st, wide);
-            e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, limit);
-            if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+            e2 = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, limit);
+            if (e2 != cudaSuccess) return cuda_fail(e2, "cudaFuncSetAttribute");
             bool any = false;
             int prev = -1;
             for (const int tb : {kTabChk | kTabSym, kTabChk, 0}) {
-                const int total = table_smem(jobs, n_jobs, C, kSplitMinN, adapt, st, wide, tb, limit);
+                const int total = table_smem(jobs, n_jobs, C, smin, adapt, st, wide, tb, limit);
                 if (total < 0 || total == prev) continue;    // no fit, or the same layouts again
                 prev = total;
                 for (const int block : {1024, 512}) {
@@ -1191,13 +1195,30 @@ ngdbf_status table_shapes(const TablePlan& T, const ngdbf_job* jobs, int32_t n_j
                     if (clusters <= 0) continue;
                     TableShape c;
                     c.fn = fn; c.block = block; c.cluster = C; c.grid_max = clusters * C; c.smem = total;
-                    c.placement = tb; c.n_local = n_local; c.split_min_n = kSplitMinN;
+                    c.placement = tb; c.n_local = n_local; c.split_min_n = smin;
                     c.st_smem = st; c.state_global = state && !st;
                     out->push_back(c);
                     any = true;
                 }
             }
             if (any) break;                  // the state fits shared memory: keep it there
+        }
+        return NGDBF_OK;
+    };
+    auto split_set = [&](int smin) {
+        std::vector<bool> v(n_jobs);
+        for (int j = 0; j < n_jobs; ++j) v[j] = jobs[j].code->n >= smin;
+        return v;
+    };
+    for (const int C : {2, 4, 8}) {
+        ngdbf_status s = cluster_shapes(C, kSplitMinN);
+        if (s != NGDBF_OK) return s;
+    }
+    for (const int smin : {1024, 4096}) {
+        if (split_set(smin) == split_set(kSplitMinN)) continue;
+        for (const int C : {2, 4, 8}) {
+            ngdbf_status s = cluster_shapes(C, smin);
+            if (s != NGDBF_OK) return s;
         }
     }
     return NGDBF_OK;
@@ -1406,6 +1427,7 @@ extern "C" ngdbf_status ngdbf_batch_shape(const ngdbf_batch_t* B, int32_t k, int
     info->sm_count = B->sm_count;
     info->tables_in_smem = sh.placement;
     info->cluster = sh.cluster;
+    info->split_min_n = sh.cluster > 1 ? sh.split_min_n : 0;
     return NGDBF_OK;
 }
 
@@ -1431,6 +1453,7 @@ extern "C" ngdbf_status ngdbf_batch_launch(ngdbf_batch_t* B, void* stream_ptr) {
     if (e != cudaSuccess) return cuda_fail(e, "job table launch");
     set_last_launch(B->grid, B->block, B->smem, B->state_in_smem, B->tables_in_smem, 1, B->sm_count);
     g_last_launch.cluster = B->cluster;
+    g_last_launch.split_min_n = B->cluster > 1 ? B->args.split_min_n : 0;
     return NGDBF_OK;
 }
 

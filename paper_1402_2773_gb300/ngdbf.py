@@ -75,7 +75,8 @@ class ngdbf_host_stats(ctypes.Structure):
 class ngdbf_launch_info(ctypes.Structure):
     _fields_ = [("grid", ctypes.c_int32), ("block", ctypes.c_int32), ("smem_bytes", ctypes.c_int32),
                 ("state_in_smem", ctypes.c_int32), ("kernels", ctypes.c_int32),
-                ("sm_count", ctypes.c_int32), ("tables_in_smem", ctypes.c_int32), ("cluster", ctypes.c_int32)]
+                ("sm_count", ctypes.c_int32), ("tables_in_smem", ctypes.c_int32), ("cluster", ctypes.c_int32),
+                ("split_min_n", ctypes.c_int32)]
 
 
 def make_params(w=0.75, theta=-0.9, eta=0.96, lam=1.0, y_max=2.5, t_max=100, smooth_window=64,
