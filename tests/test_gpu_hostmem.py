@@ -84,3 +84,40 @@ def test_decode_host_copy_modes_give_the_same_bits(mode, pinned):
     assert np.array_equal(iters, ref[1].cpu().numpy())
     assert np.array_equal(pas, ref[2].cpu().numpy())
     dc.close()
+
+
+def test_concurrent_host_decodes_share_the_staging_pool():
+    """Several threads call ngdbf_decode_host at once (staged copies: the library's staging
+    buffers and host copy threads are shared); each result equals the device-buffer decode."""
+    import threading
+    code = wl.code_c1()
+    gp = ngdbf.make_params(w=0.75, theta=-0.9, eta=0.96, y_max=2.5, t_max=100, variant=0)
+    dc = ngdbf.DeviceCode.from_code(code)
+    inputs = []
+    for t in range(4):
+        y, _, sig = wl.frames(code, 1500 + 300 * t, 3.75, seed=500 + t)
+        inputs.append((y, sig))
+    refs = []
+    for t, (y, sig) in enumerate(inputs):
+        b, i, p = dc.decode(torch.from_numpy(y).cuda(), sig, gp, seed=31, frame_offset=10 ** 6 * t)
+        refs.append((b.cpu().numpy(), i.cpu().numpy(), p.cpu().numpy()))
+    got = [None] * len(inputs)
+    errors = []
+
+    def run(t):
+        try:
+            torch.cuda.set_device(0)
+            y, sig = inputs[t]
+            got[t] = dc.decode_host(y, sig, gp, seed=31, frame_offset=10 ** 6 * t, chunk_frames=400)
+        except Exception as e:          # reported below
+            errors.append(e)
+
+    ths = [threading.Thread(target=run, args=(t,)) for t in range(len(inputs))]
+    for th in ths:
+        th.start()
+    for th in ths:
+        th.join()
+    assert not errors, errors
+    for g, r in zip(got, refs):
+        assert all(np.array_equal(a, b) for a, b in zip(g, r))
+    dc.close()

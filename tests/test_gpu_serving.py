@@ -183,3 +183,21 @@ def test_chained_requests_of_one_code(codes):
     assert stats["peak_requests_on_device"] >= 16, stats
     for dc in dcs:
         dc.close()
+
+
+def test_direct_copy_mode_serves_the_same_results(codes):
+    """The server with direct copies (no staging) gives the same results as each request alone."""
+    dcs = [ngdbf.DeviceCode.from_code(c) for c in codes]
+    reqs = requests(codes, 16, seed=7)
+    alone = decode_alone(dcs, reqs, seed=9)
+    old = ngdbf.ngdbf_get_host_copy_mode()
+    try:
+        ngdbf.ngdbf_set_host_copy_mode(ngdbf.NGDBF_HOST_COPY_DIRECT)
+        got, done, stats = serve(dcs, reqs, budget=1 << 30, inflight=2, max_jobs=8, seed=9)
+    finally:
+        ngdbf.ngdbf_set_host_copy_mode(old)
+    assert len(done) == len(reqs) and all(st == 0 for _, _, st in done)
+    for g, a in zip(got, alone):
+        assert all((x == y).all() for x, y in zip(g, a))
+    for dc in dcs:
+        dc.close()
