@@ -376,8 +376,8 @@ ngdbf_status ngdbf_batch_destroy(ngdbf_batch_t* batch);
  * 16 or more published requests have frames left, a CTA whose request runs out of frames fills
  * its free slots with frames of other requests of the same code and params (chaining).  When
  * a request's last frame is done its outputs are copied back and its memory returns to the
- * budget.  Idle CTAs exit after a few milliseconds; the kernel is launched again when work is
- * published.  A request of another variant or precision, or whose code needs a larger
+ * budget.  When a CTA has found no work for about 20 ms the whole kernel retires (no CTA takes
+ * new frames; every CTA leaves); it is launched again when work is published.  A request of another variant or precision, or whose code needs a larger
  * shared-memory layout, than the running kernel waits until that kernel drains.  Each
  * request's result equals ngdbf_decode's for the same job, alone or in any mix; the seed of
  * the perturbation is the server's.  Samples are copied in through the library's staging

@@ -113,6 +113,7 @@ struct Job {
     uint32_t gen;
     unsigned int* done;
     unsigned int* notify;
+    const unsigned int* retire;     // serving: nonzero once the resident kernel is retiring (no claims)
     // serving: jobs with the same nonzero chain_key have the same code and decoding parameters
     // (they differ only in samples, sigma, frame offset, outputs and counters), so a CTA may
     // decode frames of several of them in its slots at once
@@ -143,6 +144,9 @@ __device__ __forceinline__ bool claim_frames(const Job& A, unsigned k, unsigned 
         *base = atomicAdd(A.queue, (unsigned long long)k);
         return true;
     }
+    // a retiring resident kernel takes no new frames: they wait for the next launch, which
+    // has every CTA, instead of being decoded by the few CTAs still finishing
+    if (A.retire != nullptr && *(const volatile unsigned int*)A.retire != 0u) return false;
     unsigned long long old = *(volatile unsigned long long*)A.queue;
     for (int it = 0; it < kClaimTries; ++it) {
         if ((uint32_t)(old >> 32) != A.gen || (long long)(uint32_t)old >= A.n_frames) return false;

@@ -13,11 +13,12 @@
 // CTAs -- and, inside a request, slots -- free up.  The CTA that finishes a request's last frame
 // writes the request's generation into a completion word in page-locked host memory; the
 // scheduler then copies the outputs back and returns the request's memory to the budget.  Idle
-// CTAs poll the ring (in device memory, backing off) for about 20 ms and then exit; the
-// scheduler launches the kernel again when new work is published.  A request whose code
-// needs a larger shared-memory layout, or another variant or precision, than the running
-// kernel waits until it drains.  Only copy-engine operations are
-// issued while the kernel runs (no memset kernels), so nothing waits behind it for SMs.
+// CTAs poll the ring (in device memory, backing off); the first that has found no work for
+// about 20 ms retires the whole kernel (every CTA leaves, none takes new frames), and the
+// scheduler launches the kernel again when new work is published.  A request whose code needs
+// a larger shared-memory layout, or another variant or precision, than the running kernel
+// waits until it drains.  While the kernel runs only copy-engine operations are issued (the one
+// memset clears the retire word between launches), so nothing waits behind it for SMs.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -37,7 +38,7 @@
 namespace ngdbf {
 
 constexpr int kRing = 1024;                       // descriptor slots: requests on the device at once, at most
-constexpr long long kIdleNs = 20'000'000;         // an idle CTA exits after about this long without work
+constexpr long long kIdleNs = 20'000'000;         // a CTA this long without work retires the kernel
 
 // In device memory; written only by copies from the host's page-locked mirror.
 struct ServeRing {
@@ -62,6 +63,10 @@ struct SlotStage {
 struct ServeArgs {
     const ServeRing* ring;            // device memory
     unsigned int* notify;             // [kRing] page-locked, mapped: a slot's generation once done
+    // device, zeroed before each launch: set by the first CTA that has been idle long enough;
+    // then every CTA leaves at its next pick and no CTA claims new frames, so the kernel exits
+    // as a whole (CTAs leaving one by one would leave it running on a few of them)
+    unsigned int* retire;
     unsigned int epoch;
     int32_t n_max, m_max, t_max, dv_max, dc_max, placement;
     void* yslots;                     // [grid][pad4(n_max)/4][32][4]
@@ -141,7 +146,7 @@ __global__ void __launch_bounds__(1024) ngdbf_serve_kernel(const __grid_constant
     for (;;) {
         if (threadIdx.x == 0) {
             int p = -1;
-            if (R->stop_epoch >= A.epoch) {
+            if (R->stop_epoch >= A.epoch || *(volatile unsigned int*)A.retire != 0u) {
                 p = -2;
             } else {
                 const unsigned long long tail = R->tail;
@@ -167,7 +172,10 @@ __global__ void __launch_bounds__(1024) ngdbf_serve_kernel(const __grid_constant
                     break;
                 }
                 if (p < 0 && R->drain_epoch >= A.epoch) p = -2;
-                if (p < 0 && slept > kIdleNs) p = -2;       // idle long enough: exit
+                if (p < 0 && slept > kIdleNs) {                 // idle long enough: the kernel retires
+                    atomicExch(A.retire, 1u);
+                    p = -2;
+                }
                 if (p < 0) {
                     __nanosleep(nap);
                     slept += nap;
@@ -291,6 +299,7 @@ struct ngdbf_server {
     unsigned int* epoch_img = nullptr;       // [2]: stop, drain
     unsigned long long* d_claim = nullptr;   // [kRing] (gen << 32) | frames claimed
     unsigned int* d_done = nullptr;          // [kRing] frames done
+    unsigned int* d_retire = nullptr;        // set by the resident kernel when it retires
     uint32_t slot_gen[kRing] = {};
     uint64_t next_seq = 0, head = 0;
     std::vector<uint64_t> done_seq;          // completed sequence numbers above head
@@ -367,6 +376,7 @@ ngdbf_status admit(ngdbf_server* S, Request* r) {
         r->dj.chain_key = it->second;
     }
     r->dj.done = S->d_done + r->slot;
+    r->dj.retire = S->d_retire;
     r->dj.notify = S->notify_dev + r->slot;
     sg.claim0 = (unsigned long long)r->gen << 32;
     sg.done0 = 0;
@@ -437,14 +447,17 @@ ngdbf_status launch_kernel(ngdbf_server* S) {
     std::memset(&A, 0, sizeof(A));
     A.ring = S->d_ring;
     A.notify = S->notify_dev;
+    A.retire = S->d_retire;
     A.epoch = ++S->epoch;
     A.n_max = K.n; A.m_max = K.m; A.t_max = K.t_max; A.dv_max = K.dv; A.dc_max = K.dc;
     A.placement = sp.placement;
     A.yslots = S->scratch;
     A.st_global = P.per_st ? reinterpret_cast<uint16_t*>(S->scratch + align256((size_t)P.grid * P.per_y)) : nullptr;
     host_gen_consts(S->seed, A.G);
-    // the kernel must see every ring update published so far
-    e = cudaEventRecord(S->ev_kernel, S->pub_stream);
+    // the previous kernel retired (or drained): clear the word before this one starts; and the
+    // kernel must see every ring update published so far
+    e = cudaMemsetAsync(S->d_retire, 0, sizeof(unsigned int), S->pub_stream);
+    if (e == cudaSuccess) e = cudaEventRecord(S->ev_kernel, S->pub_stream);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(S->serve_stream, S->ev_kernel, 0);
     if (e == cudaSuccess) {
         serve_kernel_fn(K.variant, K.precision, sp.st_smem, wide)<<<P.grid, sp.block, sp.smem, S->serve_stream>>>(A);
@@ -671,6 +684,8 @@ extern "C" ngdbf_status ngdbf_server_create(size_t device_budget_bytes, int32_t 
     if (e == cudaSuccess) e = cudaMalloc(&S->d_ring, sizeof(ServeRing));
     if (e == cudaSuccess) e = cudaMalloc(&S->d_claim, sizeof(unsigned long long) * kRing);
     if (e == cudaSuccess) e = cudaMalloc(&S->d_done, sizeof(unsigned int) * kRing);
+    if (e == cudaSuccess) e = cudaMalloc(&S->d_retire, sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaMemset(S->d_retire, 0, sizeof(unsigned int));
     if (e == cudaSuccess) e = cudaMemset(S->d_ring, 0, sizeof(ServeRing));
     if (e == cudaSuccess) e = cudaMemset(S->d_claim, 0, sizeof(unsigned long long) * kRing);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&S->ev_kernel, cudaEventDisableTiming);
@@ -691,6 +706,7 @@ extern "C" ngdbf_status ngdbf_server_create(size_t device_budget_bytes, int32_t 
         cudaFree(S->d_ring);
         cudaFree(S->d_claim);
         cudaFree(S->d_done);
+        cudaFree(S->d_retire);
         if (S->stage) cudaFreeHost(S->stage);
         if (S->head_img) cudaFreeHost(S->head_img);
         if (S->epoch_img) cudaFreeHost(S->epoch_img);
@@ -799,6 +815,7 @@ extern "C" ngdbf_status ngdbf_server_destroy(ngdbf_server_t* S) {
     cudaFree(S->d_ring);
     cudaFree(S->d_claim);
     cudaFree(S->d_done);
+    cudaFree(S->d_retire);
     cudaFreeHost(S->stage);
     cudaFreeHost(S->head_img);
     cudaFreeHost(S->epoch_img);
