@@ -201,3 +201,32 @@ def test_direct_copy_mode_serves_the_same_results(codes):
         assert all((x == y).all() for x, y in zip(g, a))
     for dc in dcs:
         dc.close()
+
+
+def test_requests_across_kernel_retirements(codes):
+    """Requests arriving with gaps longer than the idle time: the resident kernel retires as a
+    whole between them and is launched again; a request that arrives while it retires waits for
+    the next launch.  Every result equals the request decoded alone."""
+    import time
+    dcs = [ngdbf.DeviceCode.from_code(c) for c in codes]
+    reqs = requests(codes, 10, seed=11)
+    alone = decode_alone(dcs, reqs, seed=13)
+    srv = ngdbf.Server(1 << 30, max_inflight=2, max_jobs=16, seed=13)
+    outs = []
+    for k, q in enumerate(reqs):
+        F, n = q["y"].shape[0], dcs[q["c"]].n
+        buf = (torch.empty((F, (n + 7) // 8), dtype=torch.uint8).pin_memory(),
+               torch.empty(F, dtype=torch.int32).pin_memory(), torch.empty(F, dtype=torch.uint8).pin_memory())
+        srv.submit(dcs[q["c"]], q["y"], q["sigma"], ngdbf.make_params(**q["kw"]), q["off"], out=buf)
+        outs.append(buf)
+        time.sleep(0.005 if k % 3 == 2 else 0.045)     # mostly longer than the idle time
+    srv.wait(600)
+    done = srv.poll()
+    stats = srv.stats()
+    srv.close()
+    assert len(done) == len(reqs) and all(st == 0 for _, _, st in done)
+    for o, a in zip(outs, alone):
+        assert all((x.numpy() == y).all() for x, y in zip(o, a))
+    assert stats["launches"] >= 3, stats
+    for dc in dcs:
+        dc.close()
