@@ -377,8 +377,12 @@ ngdbf_status ngdbf_batch_destroy(ngdbf_batch_t* batch);
  * its free slots with frames of other requests of the same code and params (chaining).  When
  * a request's last frame is done its outputs are copied back and its memory returns to the
  * budget.  When a CTA has found no work for about 20 ms the whole kernel retires (no CTA takes
- * new frames; every CTA leaves); it is launched again when work is published.  A request of another variant or precision, or whose code needs a larger
- * shared-memory layout, than the running kernel waits until that kernel drains.  Each
+ * new frames; every CTA leaves); it is launched again when work is published.  The kernel's
+ * shared memory is sized for the largest code of the mix; each request is decoded in a layout
+ * of its own code within it, with its per-slot state in shared memory whenever that fits
+ * (requests of a code whose state does not fit use global scratch).  A request of another
+ * variant or precision, or whose code needs a larger shared-memory layout, than the running
+ * kernel waits until that kernel drains.  Each
  * request's result equals ngdbf_decode's for the same job, alone or in any mix; the seed of
  * the perturbation is the server's.  Samples are copied in through the library's staging
  * buffers (ngdbf_set_host_copy_mode), so any host buffer serves; with direct copies,

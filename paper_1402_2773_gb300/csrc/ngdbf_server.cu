@@ -69,6 +69,7 @@ struct ServeArgs {
     unsigned int* retire;
     unsigned int epoch;
     int32_t n_max, m_max, t_max, dv_max, dc_max, placement;
+    int32_t smem_bytes;               // the launch's dynamic shared memory
     void* yslots;                     // [grid][pad4(n_max)/4][32][4]
     uint16_t* st_global;              // [grid][pad4(n_max)/4][32][4] when the state is not in shared memory
     GenConsts G;
@@ -125,10 +126,15 @@ struct RingNext {
 
 // The resident serving kernel: each CTA repeatedly takes the oldest published request that
 // still has unclaimed frames (of its own generation) and runs the slot loop on it, chaining
-// further requests of the same code and parameters into its free slots.
+// further requests of the same code and parameters into its free slots.  Every request is
+// decoded in a shared-memory layout of its own code within the launch's bytes: with ST_SMEM
+// (the largest code's state fits) the state is always in shared memory; otherwise a request
+// whose code's state fits keeps it there too (in the 4-bit count format), and only the others
+// use the global slot state.
 template <bool ADAPT, bool SMOOTH, bool ST_SMEM, bool WIDE, int PREC>
 __global__ void __launch_bounds__(1024) ngdbf_serve_kernel(const __grid_constant__ ServeArgs A) {
     using HeldT = typename Held<PREC>::T;
+    constexpr bool kState = ADAPT || SMOOTH;
     __shared__ Job jl[kChain];      // jl[0]: the request picked; the others: chained requests
     __shared__ int8_t slot_e[kSlots];
     __shared__ int cur_e;
@@ -136,8 +142,6 @@ __global__ void __launch_bounds__(1024) ngdbf_serve_kernel(const __grid_constant
     Job& job = jl[0];
     if (threadIdx.x == 0) fail[0] = fail[1] = ~0ull;
     __shared__ int pick;
-    const SmemLayout L = smem_layout(A.n_max, A.m_max, A.t_max, A.dv_max, A.dc_max, ADAPT,
-                                     ST_SMEM && (ADAPT || SMOOTH), A.placement);
     HeldT* ys = static_cast<HeldT*>(A.yslots) + (size_t)blockIdx.x * pad4(A.n_max) * kSlots;
     uint16_t* st = A.st_global ? A.st_global + (size_t)blockIdx.x * pad4(A.n_max) * kSlots : nullptr;
     const volatile ServeRing* R = A.ring;
@@ -191,9 +195,25 @@ __global__ void __launch_bounds__(1024) ngdbf_serve_kernel(const __grid_constant
         if (p < 0) continue;
         slept = 0;
         nap = 500;
-        decode_job<ADAPT, SMOOTH, ST_SMEM, WIDE, PREC, false, true, RingNext>(
-            job, job.thr, A.G, L, A.placement, ys, st, Split{0, 1, 0, 0},
-            ChainCtx<RingNext>{jl, slot_e, &cur_e, RingNext{R, fail}});
+        int tables = 0;
+        const ChainCtx<RingNext> ch{jl, slot_e, &cur_e, RingNext{R, fail}};
+        bool done = false;
+        if constexpr (kState && !ST_SMEM && !WIDE) {
+            const SmemLayout Ls = job_layout(job.n, job.m, job.t_max, job.dv_max, job.dc_max, ADAPT, true, WIDE,
+                                             A.placement, job.n, A.smem_bytes, &tables);
+            if (Ls.total <= A.smem_bytes) {
+                decode_job<ADAPT, SMOOTH, true, WIDE, PREC, false, true, RingNext>(
+                    job, job.thr, A.G, Ls, tables, ys, nullptr, Split{0, 1, 0, 0}, ch);
+                done = true;
+            }
+        }
+        if (!done) {
+            // (a code no larger than the kind's maxima always fits without its state)
+            const SmemLayout L = job_layout(job.n, job.m, job.t_max, job.dv_max, job.dc_max, ADAPT,
+                                            ST_SMEM && kState, WIDE, A.placement, job.n, A.smem_bytes, &tables);
+            decode_job<ADAPT, SMOOTH, ST_SMEM, WIDE, PREC, false, true, RingNext>(
+                job, job.thr, A.G, L, tables, ys, st, Split{0, 1, 0, 0}, ch);
+        }
         __syncthreads();
     }
 }
@@ -451,6 +471,7 @@ ngdbf_status launch_kernel(ngdbf_server* S) {
     A.epoch = ++S->epoch;
     A.n_max = K.n; A.m_max = K.m; A.t_max = K.t_max; A.dv_max = K.dv; A.dc_max = K.dc;
     A.placement = sp.placement;
+    A.smem_bytes = sp.smem;
     A.yslots = S->scratch;
     A.st_global = P.per_st ? reinterpret_cast<uint16_t*>(S->scratch + align256((size_t)P.grid * P.per_y)) : nullptr;
     host_gen_consts(S->seed, A.G);

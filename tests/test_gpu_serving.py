@@ -230,3 +230,38 @@ def test_requests_across_kernel_retirements(codes):
     assert stats["launches"] >= 3, stats
     for dc in dcs:
         dc.close()
+
+
+def test_mix_with_a_code_whose_state_is_off_chip(codes):
+    """A mix whose largest code (N = 8192) keeps its slot state in global memory: the resident
+    kernel decodes every request in a layout of its own code, so the smaller codes' requests keep
+    their state in shared memory in the same launch; every result equals the request decoded
+    alone, and a few equal the reference decoder."""
+    big_code = wl.peg_code(8192, 1639, 3, seed=1)
+    mix = [codes[0], codes[3], big_code]
+    dcs = [ngdbf.DeviceCode.from_code(c) for c in mix]
+    kws = [dict(w=0.75, theta=-0.9, eta=0.9, lam=0.99, y_max=2.5),
+           dict(w=0.1875, theta=-0.7, eta=0.65, lam=0.993, y_max=2.0),
+           dict(w=0.5, theta=-0.7, eta=0.8, lam=0.99, y_max=2.5)]
+    rng = np.random.default_rng(31)
+    reqs = []
+    for r in range(30):
+        c = 2 if r % 5 == 0 else int(rng.integers(2))      # the large code first, then every fifth
+        F = int(rng.integers(1, 200 if c < 2 else 48))
+        y, _, sig = wl.frames(mix[c], F, float(rng.uniform(3.5, 4.5)), seed=4000 + r)
+        kw = kws[c] | dict(t_max=int(rng.integers(60, 200)), smooth_window=64, variant=3)
+        reqs.append(dict(c=c, y=torch.from_numpy(y).pin_memory(), sigma=sig, kw=kw, off=5000 * r + 3))
+    alone = decode_alone(dcs, reqs[:1], seed=14)
+    assert ngdbf.ngdbf_last_launch()["state_in_smem"] == 0      # the large code's state is off chip
+    alone += decode_alone(dcs, reqs[1:], seed=14)
+    got, done, stats = serve(dcs, reqs, budget=4 << 30, inflight=4, max_jobs=64, seed=14)
+    assert len(done) == len(reqs) and all(st == 0 for _, _, st in done)
+    for g, a in zip(got, alone):
+        assert all((x == y).all() for x, y in zip(g, a)), "served result differs from the request alone"
+    O = oracle.load()
+    for q, g in [(q, g) for q, g in zip(reqs, got) if q["c"] < 2][:4]:
+        ob, oi, op = O.decode_f32(mix[q["c"]], q["y"].numpy(), q["sigma"], oracle.make_params(**q["kw"]), seed=14,
+                                  frame_offset=q["off"], threads=THREADS)
+        assert (g[0] == ob).all() and (g[1] == oi).all() and (g[2] == op).all()
+    for dc in dcs:
+        dc.close()
