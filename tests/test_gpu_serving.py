@@ -232,11 +232,13 @@ def test_requests_across_kernel_retirements(codes):
         dc.close()
 
 
-def test_mix_with_a_code_whose_state_is_off_chip(codes):
+@pytest.mark.parametrize("prec", [dict(), dict(precision=ngdbf.NGDBF_FP16), dict(precision=ngdbf.NGDBF_FIX, q_bits=8),
+                                  dict(precision=ngdbf.NGDBF_FIXACC, q_bits=8)], ids=["fp32", "fp16", "fix8", "fixacc8"])
+def test_mix_with_a_code_whose_state_is_off_chip(codes, prec):
     """A mix whose largest code (N = 8192) keeps its slot state in global memory: the resident
     kernel decodes every request in a layout of its own code, so the smaller codes' requests keep
     their state in shared memory in the same launch; every result equals the request decoded
-    alone, and a few equal the reference decoder."""
+    alone, and a few equal the reference decoder (in every held precision)."""
     big_code = wl.peg_code(8192, 1639, 3, seed=1)
     mix = [codes[0], codes[3], big_code]
     dcs = [ngdbf.DeviceCode.from_code(c) for c in mix]
@@ -249,7 +251,7 @@ def test_mix_with_a_code_whose_state_is_off_chip(codes):
         c = 2 if r % 5 == 0 else int(rng.integers(2))      # the large code first, then every fifth
         F = int(rng.integers(1, 200 if c < 2 else 48))
         y, _, sig = wl.frames(mix[c], F, float(rng.uniform(3.5, 4.5)), seed=4000 + r)
-        kw = kws[c] | dict(t_max=int(rng.integers(60, 200)), smooth_window=64, variant=3)
+        kw = kws[c] | dict(t_max=int(rng.integers(60, 200)), smooth_window=64, variant=3) | prec
         reqs.append(dict(c=c, y=torch.from_numpy(y).pin_memory(), sigma=sig, kw=kw, off=5000 * r + 3))
     alone = decode_alone(dcs, reqs[:1], seed=14)
     assert ngdbf.ngdbf_last_launch()["state_in_smem"] == 0      # the large code's state is off chip
