@@ -88,7 +88,7 @@ def mix_probe(ngdbf, stream, reps=5, warmup=2):
 # this workload at 2*10^4 frames per Eb/N0 point (samples 164 MB per launch, larger than L2):
 # 167.6 MB read + 8.0 MB written at 3.5 dB; traffic scales with frames, each frame's samples
 # being read once.  Set to None when the kernel changes without a new capture.
-DRAM_BYTES_PER_FRAME = 8_778
+DRAM_BYTES_PER_FRAME = 8_697
 
 
 def env_rank():
